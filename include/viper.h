@@ -1,0 +1,224 @@
+/*
+ * viper.h -- C ABI of the GB300 (sm_103a) VIPER rod solver.
+ *
+ * The library steps volume-invariant position-based elastic rods ("VIPER",
+ * Angles et al., arXiv 1906.05260) on one GPU.  Per substep it animates
+ * kinematic bones, predicts positions / orientations / scales (Sec. 6
+ * "Prediction step", App. B), projects stretch/shear, volume, cross-section
+ * scale, scale-gradient, bend/twist and volume-bending constraints with the
+ * generalised XPBD update (Sec. 5, Sec. 6 "Correction steps", App. C) over an
+ * even/odd colouring of each rod, detects and resolves pill-pill and
+ * half-plane contacts (Sec. 7.1, Sec. 7.2, App. D), updates velocities, and
+ * linear-blend-skins surface meshes (Sec. 7.4).
+ *
+ * Conventions shared by every entry point
+ *  - Rods are given as a vertex CSR `rod_offsets[n_rods+1]`; rod r owns
+ *    vertices rod_offsets[r] .. rod_offsets[r+1]-1 (at least 2).  Segment j of
+ *    rod r joins its local vertices j and j+1 and has the global index
+ *    rod_offsets[r] - r + j; nv = rod_offsets[n_rods], ns = nv - n_rods.
+ *  - Quaternions are (x, y, z, w), Hamilton product; the material frame's
+ *    third axis d3 = R(q) e_z is the rod tangent (Sec. 3).
+ *  - Each vertex carries a scale s (Sec. 3: D(z) = s(z) R(z)); its physical
+ *    radius is s times the rest radius.
+ *  - Units are SI.  Compliances are 1/modulus in 1/Pa; stiffness matrices are
+ *    the disc integrals of Sec. 5 times the element length (Sec. 6).
+ *  - All public arrays use the caller's vertex/segment numbering; the library
+ *    keeps its own (packed) order internally.
+ *  - Pointer arguments marked "host or device" accept either; the library
+ *    tells them apart through unified addressing.
+ *  - Every call returns VIPER_OK (0) or a negative VIPER_E* code; nothing
+ *    throws across the ABI.  Work is queued on the scene's CUDA stream; errors
+ *    raised by kernels (non-finite state, pair-buffer overflow) are reported by
+ *    the next viper_sync / viper_step / viper_get_state on that scene.
+ *  - A scene is used from one host thread at a time.
+ */
+#ifndef VIPER_H
+#define VIPER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIPER_OK 0
+#define VIPER_EINVAL -1      /* invalid argument                                  */
+#define VIPER_ENOMEM -2      /* device allocation failed                          */
+#define VIPER_ECUDA -3       /* a CUDA runtime call failed                        */
+#define VIPER_ENONFINITE -4  /* the state became NaN/Inf (scene is quarantined)   */
+#define VIPER_EOVERFLOW -5   /* more candidate pairs than the pair buffer holds   */
+#define VIPER_ETIMEOUT -6    /* a bounded device wait expired                     */
+#define VIPER_EBUDGET -7     /* admission refused: memory budget exceeded         */
+
+#define VIPER_FLAG_CONTACTS 1 /* pill-pill contacts (Sec. 7.1, 7.2)                */
+#define VIPER_FLAG_VOLUME 2   /* volume constraints (Sec. 5 "Volume potential")    */
+
+#define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
+#define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,
+                                  a frame replayed from a captured CUDA graph     */
+
+typedef struct viper_scene viper_scene;
+
+/*
+ * Scene description (Sec. 4: the rest pose is the initial pose; the
+ * variational implicit Euler problem is fixed by rest geometry, masses,
+ * stiffness and external forces).  All pointers are HOST pointers read during
+ * viper_scene_create only; the library copies what it needs.
+ */
+typedef struct viper_scene_desc {
+    int n_rods;
+    const int *rod_offsets;      /* [n_rods+1] vertex CSR                                */
+    const double *rest_pos;      /* [3 nv] rest centre-line positions c_bar              */
+    const double *rest_quat;     /* [4 ns] rest frames; d3 must follow the rest tangent  */
+    const double *radius;        /* [nv] rest disc radius r(z) (Sec. 3)                   */
+    const double *density;       /* [n_rods] mass per volume m (Sec. 4), > 0             */
+    const double *c_stretch;     /* [n_rods] stretch/shear + scale compliance, > 0       */
+    const double *c_bend;        /* [n_rods] bend/twist compliance, > 0                  */
+    const double *c_volume;      /* [n_rods] volume compliance, > 0; NULL: = c_stretch   */
+    const int *group;            /* [n_rods] collision group; NULL: rod index           */
+    double gravity[3];           /* uniform acceleration (m/s^2)                        */
+    int n_pins;                  /* kinematic vertices (position only)                  */
+    const int *pin_vertex;       /* [n_pins] vertex ids                                 */
+    const int *pin_bone;         /* [n_pins] bone id, or -1 for a point fixed in world  */
+    const double *pin_offset;    /* [3 n_pins] offset in the bone frame (world if -1)   */
+    int n_bones;
+    const double *bone_quat;     /* [4 n_bones] initial bone orientations               */
+    const double *bone_trans;    /* [3 n_bones] initial bone origins                    */
+    int n_planes;                /* kinematic half-planes (Sec. 7)                       */
+    const double *planes;        /* [4 n_planes] (n, d): keeps n.x - d - radius >= 0     */
+    double contact_compliance;   /* XPBD compliance of contact constraints (>= 0)       */
+    int flags;                   /* VIPER_FLAG_*                                        */
+    int max_pairs;               /* candidate-pair capacity; 0 selects 32 per segment   */
+    void *stream;                /* cudaStream_t for all work; NULL: a new stream      */
+} viper_scene_desc;
+
+/*
+ * Create a scene: validates the description, precomputes rest data (rest
+ * lengths, rest Darboux vectors, lumped inertias, compliances) in double
+ * precision, rounds them to FP32, packs rods into shared-memory work items and
+ * uploads everything.  The state starts at rest, with zero velocities.
+ * Returns VIPER_EINVAL for inconsistent sizes, a rod of fewer than 2 vertices,
+ * a pin index out of range or non-positive material parameters;
+ * VIPER_ENOMEM / VIPER_ECUDA on device failures.  On success *out owns all
+ * device memory until viper_scene_destroy.
+ */
+int viper_scene_create(const viper_scene_desc *desc, viper_scene **out);
+
+/* Release all device memory of the scene (waits for its stream first). */
+void viper_scene_destroy(viper_scene *scene);
+
+/* Number of rods, vertices and segments. */
+int viper_scene_counts(const viper_scene *scene, int *n_rods, int *n_verts, int *n_segs);
+
+/*
+ * Solver selection: VIPER_SOLVER_PLAIN (predict, one launch per colour and per
+ * iteration, velocity update; state read from and written to HBM each launch)
+ * or VIPER_SOLVER_BATCHED (one shared-memory-resident launch per substep for
+ * rods of at most `resident_max` vertices, longer rods on the plain path; a
+ * whole frame is captured once into a CUDA graph and replayed).  block_warps
+ * is the CTA size in warps for the batched kernel (1, 2, 4 or 8; larger rods
+ * raise it as needed).  Changing either drops cached graphs.
+ */
+int viper_set_solver(viper_scene *scene, int mode, int block_warps, int resident_max);
+
+/*
+ * Time the batched solver over candidate CTA sizes and residency thresholds
+ * on a scratch copy of the state (the scene state is restored afterwards) and
+ * keep the fastest.  *chosen receives block_warps * 1000 + resident_max.
+ */
+int viper_autotune(viper_scene *scene, float dt, int substeps, int iterations, int *chosen);
+
+/*
+ * Advance one frame: `substeps` substeps of h = dt / substeps, each with
+ * `iterations` sweeps of the four constraint colours (and, when contacts or
+ * half-planes exist, a Jacobi contact pass after every sweep).  Bones move from
+ * their previous pose to the pose last given to viper_set_bones.
+ * Asynchronous on the scene stream; returns an error latched by earlier work.
+ */
+int viper_step(viper_scene *scene, float dt, int substeps, int iterations);
+
+/* Bone poses to reach at the end of the next viper_step (host or device). */
+int viper_set_bones(viper_scene *scene, int n_bones, const float *quat, const float *trans);
+
+/*
+ * Linear blend skinning (Sec. 7.4) of n mesh vertices: out = sum_k w_k T_k
+ * Tbar_k^-1 rest with segment similarity frames T = [s_m R, c_m] (Eq.
+ * shapematch).  rest4 [4n] (x, y, z, unused), idx4 [4n] caller segment ids,
+ * w4 [4n], out4 [4n] (x, y, z, 0); all host or device.  Host output makes the
+ * call synchronous.
+ */
+int viper_skin(viper_scene *scene, int n, const float *rest4, const int *idx4, const float *w4,
+               float *out4);
+
+/*
+ * State in caller numbering, host or device, any pointer may be NULL:
+ *   x4 [4 nv] (x, y, z, radius)   v4 [4 nv] (vx, vy, vz, d radius / dt)
+ *   q4 [4 ns] (x, y, z, w)        w4 [4 ns] (angular velocity, 0)
+ * viper_get_state synchronises with the scene stream.
+ */
+int viper_get_state(viper_scene *scene, float *x4, float *v4, float *q4, float *w4);
+int viper_set_state(viper_scene *scene, const float *x4, const float *v4, const float *q4,
+                    const float *w4);
+
+/* Wait for the scene's queued work; returns and clears any latched error. */
+int viper_sync(viper_scene *scene);
+
+/*
+ * Candidate pairs of the last substep (Sec. 7.1), as caller segment ids a < b,
+ * sorted lexicographically into `pairs` [2 cap] (host).  *n_pairs receives the
+ * total count, which may exceed cap.  Synchronous.
+ */
+int viper_get_pairs(viper_scene *scene, int *pairs, int cap, int *n_pairs);
+
+/*
+ * Colour each constraint is projected in by the active solver, read back from
+ * the device schedule: seg_colour [ns] in {0, 1}; vtx_colour [nv] in {2, 3}
+ * for interior vertices and -1 at rod ends (host pointers).
+ */
+int viper_get_colouring(viper_scene *scene, int *seg_colour, int *vtx_colour);
+
+/* Predicted FP32 vertex state (x, y, z, scale) and rest radii of the last
+ * substep, as used by the broadphase (host pointers, caller numbering). */
+int viper_get_predicted(viper_scene *scene, float *x4, float *rbar);
+
+/*
+ * Device allocator hook for all later scene allocations (e.g. a framework's
+ * caching allocator).  alloc(bytes, ctx) returns device memory or NULL;
+ * release(ptr, ctx).  Passing NULL restores cudaMalloc/cudaFree.
+ */
+int viper_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*release)(void *ptr, void *ctx),
+                        void *ctx);
+
+/* Device memory (bytes) a scene with this description would hold. */
+size_t viper_scene_footprint(const viper_scene_desc *desc);
+
+/*
+ * Kernel timing for measurement.  viper_profile(scene, cls) brackets every
+ * launch of one kernel class with CUDA events (recorded as event nodes when a
+ * frame is captured into a graph; cached graphs are dropped).  cls:
+ *   VIPER_PROF_NONE, VIPER_PROF_ROD (rod kernels: shared-memory and per-colour),
+ *   VIPER_PROF_CONTACT (narrowphase + contact projection),
+ *   VIPER_PROF_BROADPHASE (every broadphase kernel),
+ *   VIPER_PROF_LBS (skinning gather), VIPER_PROF_ELEMENTWISE (predict, finish, apply).
+ * viper_profile_read synchronises and returns the summed device time (ms) and
+ * number of bracketed launches of the last frame plus any skinning calls since.
+ */
+#define VIPER_PROF_NONE 0
+#define VIPER_PROF_ROD 1
+#define VIPER_PROF_CONTACT 2
+#define VIPER_PROF_BROADPHASE 3
+#define VIPER_PROF_LBS 4
+#define VIPER_PROF_ELEMENTWISE 5
+int viper_profile(viper_scene *scene, int kernel_class);
+int viper_profile_read(viper_scene *scene, double *ms, int *launches);
+
+/* Number of kernel launches the scene enqueued since creation. */
+long long viper_launch_count(const viper_scene *scene);
+
+/* Static text for a VIPER_* code. */
+const char *viper_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

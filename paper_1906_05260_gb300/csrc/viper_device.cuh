@@ -1,0 +1,389 @@
+// viper_device.cuh -- device math of the VIPER rod solver (sm_103a).
+//
+// Closed-form XPBD projections of the rod constraints (Sec. 5, App. A) in the
+// generalised XPBD form of Sec. 6 / App. C, the pill-pill narrowphase
+// (Sec. 7.2, App. D) and the exactly rounded FP32 bounding-sphere predicate
+// used by the broadphase (Sec. 7.1).  Shared by every kernel of the library.
+//
+// State conventions: vertex float4 (x, y, z, s) with s the cross-section scale
+// (radius = s * rest radius); segment quaternion float4 (x, y, z, w), Hamilton
+// product, d3 = R(q) e_z the tangent; rotations are updated by a world-frame
+// increment dtheta as q <- normalize(q + 1/2 (dtheta, 0) q) (Sec. 7.5: the
+// small-angle quaternion [theta/2, 1]).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace viper {
+
+// ---------------------------------------------------------------- vectors
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 xyz(float4 a) { return {a.x, a.y, a.z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ void add_to(float4 &p, V3 d)
+{
+    p.x += d.x;
+    p.y += d.y;
+    p.z += d.z;
+}
+
+// ---------------------------------------------------------------- quaternions
+__device__ __forceinline__ float4 qmul(float4 a, float4 b)
+{
+    return make_float4(a.w * b.x + b.w * a.x + a.y * b.z - a.z * b.y,
+                       a.w * b.y + b.w * a.y + a.z * b.x - a.x * b.z,
+                       a.w * b.z + b.w * a.z + a.x * b.y - a.y * b.x,
+                       a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z);
+}
+__device__ __forceinline__ float4 qconj(float4 a) { return make_float4(-a.x, -a.y, -a.z, a.w); }
+__device__ __forceinline__ float4 qnormalize(float4 q)
+{
+    float r = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    return make_float4(q.x * r, q.y * r, q.z * r, q.w * r);
+}
+// d3 = R(q) e_z
+__device__ __forceinline__ V3 qd3(float4 q)
+{
+    return {2.f * (q.x * q.z + q.y * q.w), 2.f * (q.y * q.z - q.x * q.w), 1.f - 2.f * (q.x * q.x + q.y * q.y)};
+}
+// R(q) v for unit q
+__device__ __forceinline__ V3 qrot(float4 q, V3 v)
+{
+    V3 u = {q.x, q.y, q.z};
+    V3 t = 2.f * cross(u, v);
+    return v + q.w * t + cross(u, t);
+}
+// q <- normalize(q + 1/2 (d, 0) q)
+__device__ __forceinline__ void rotate_by(float4 &q, V3 d)
+{
+    float4 t = qmul(make_float4(d.x, d.y, d.z, 0.f), q);
+    q = qnormalize(make_float4(q.x + 0.5f * t.x, q.y + 0.5f * t.y, q.z + 0.5f * t.z, q.w + 0.5f * t.w));
+}
+
+// ---------------------------------------------------------------- rest data
+// RS0 = (lbar, 1/(M r_m^2), alpha_S, alpha_V), RS1 = (alpha_X, alpha_G) per segment;
+// RV0 = (Omega_bar, rbar), RV1 = (w | -(pin+1), w_s, alpha_B, alpha_Vb) per vertex.
+// Vertex inverse mass: RV1.x when >= 0, else the vertex is pinned (mass infinite).
+__device__ __forceinline__ float inv_mass(float4 rv1) { return fmaxf(rv1.x, 0.f); }
+
+// ---------------------------------------------------------------- segment constraints
+// Segment j between vertices a, b, frame q; per-constraint multipliers in lam
+// (S.xyz, V) and lam2 (X, G).  Order S, V, X, G, each evaluated at the state the
+// previous one left (Gauss-Seidel inside the element).
+//
+//  S  C = (xb - xa)/l - d3                (Eq. stretch_z, isotropic vector form)
+//     J_xa = -I/l, J_xb = I/l, J_theta = [d3]x; with the rotational inverse
+//     inertia I^-1 = R diag(a, a, a/2) R^T (a = 4 / (s_m^2 M r^2), App. B) the
+//     effective matrix is (w_a + w_b)/l^2 I + a (I - d3 d3^T): its inverse plus
+//     compliance splits into the d3 and orthogonal parts below.
+//  V  C = s_m^2 d3.(xb - xa)/l - 1        (determinant of grad p, App. A)
+//  X  C = s_m - 1                         (Eq. stretch_xy)
+//  G  C = (sb - sa)/l                     (Eq. surface_stretch)
+__device__ __forceinline__ void project_segment(float4 &xa, float4 &xb, float4 &q, float wa, float wb,
+                                                float wsa, float wsb, float4 rs0, float2 rs1,
+                                                float4 &lam, float2 &lam2, float inv_h2, bool volume)
+{
+    const float inv_l = 1.f / rs0.x;
+    // ---- S: stretch / shear
+    {
+        V3 d3 = qd3(q);
+        V3 C = (xyz(xb) - xyz(xa)) * inv_l - d3;
+        float sm = 0.5f * (xa.w + xb.w);
+        float a = 4.f * rs0.y / (sm * sm);
+        float wp = (wa + wb) * inv_l * inv_l;
+        float at = rs0.z * inv_h2;
+        V3 lm = {lam.x, lam.y, lam.z};
+        V3 rhs = -C - at * lm;
+        float dn = dot(rhs, d3);
+        V3 dl = (rhs - dn * d3) * (1.f / (wp + a + at)) + d3 * (dn / (wp + at));
+        lam.x += dl.x;
+        lam.y += dl.y;
+        lam.z += dl.z;
+        add_to(xa, (-wa * inv_l) * dl);
+        add_to(xb, (wb * inv_l) * dl);
+        rotate_by(q, a * cross(dl, d3));
+    }
+    // ---- V: volume (determinant form)
+    if (volume) {
+        V3 d3 = qd3(q);
+        V3 dx = xyz(xb) - xyz(xa);
+        float sm = 0.5f * (xa.w + xb.w);
+        float e = dot(d3, dx);
+        float C = sm * sm * e * inv_l - 1.f;
+        float jx = sm * sm * inv_l;  // J_xb = jx d3, J_xa = -jx d3
+        float js = sm * e * inv_l;   // J_sa = J_sb
+        V3 jt = (sm * sm * inv_l) * cross(d3, dx);  // J_theta (orthogonal to d3)
+        float a = 4.f * rs0.y / (sm * sm);
+        float at = rs0.w * inv_h2;
+        float den = (wa + wb) * jx * jx + (wsa + wsb) * js * js + a * dot(jt, jt) + at;
+        float dl = (-C - at * lam.w) / den;
+        lam.w += dl;
+        add_to(xa, (-wa * jx * dl) * d3);
+        add_to(xb, (wb * jx * dl) * d3);
+        xa.w += wsa * js * dl;
+        xb.w += wsb * js * dl;
+        rotate_by(q, (a * dl) * jt);
+    }
+    // ---- X: cross-section scale
+    {
+        float C = 0.5f * (xa.w + xb.w) - 1.f;
+        float at = rs1.x * inv_h2;
+        float dl = (-C - at * lam2.x) / (0.25f * (wsa + wsb) + at);
+        lam2.x += dl;
+        xa.w += 0.5f * wsa * dl;
+        xb.w += 0.5f * wsb * dl;
+    }
+    // ---- G: scale gradient
+    {
+        float C = (xb.w - xa.w) * inv_l;
+        float at = rs1.y * inv_h2;
+        float dl = (-C - at * lam2.y) / ((wsa + wsb) * inv_l * inv_l + at);
+        lam2.y += dl;
+        xa.w -= wsa * inv_l * dl;
+        xb.w += wsb * inv_l * dl;
+    }
+}
+
+// ---------------------------------------------------------------- vertex constraints
+// Relative rotation p = conj(q_a) q_b (flipped to p_w >= 0), Darboux vector
+// Omega = kappa Im(p), kappa = 4/(l_a + l_b) (Sec. 7.5).  A world rotation
+// dtheta_b changes Im(p) by 1/2 M R_a^T dtheta_b with M = p_w I - [p_v]x and
+// dtheta_a by the negative.  In the frame of segment a the inverse rotational
+// inertias are D_a = diag(da, da, da/2) and R(p) D_b R(p)^T, so
+//   J_theta I^-1 J_theta^T = s^2 (kappa/2)^2 M (D_a + R(p) D_b R(p)^T) M^T,
+// with M M^T = I - p_v p_v^T for unit p.
+struct RelFrame {
+    float4 p;
+    V3 om;         // Omega
+    float h2;      // kappa / 2
+    float da, db;  // perpendicular inverse inertias of segments a, b (body frame)
+    V3 e;          // d3 of p: segment b's tangent in segment a's frame
+    float N[6];    // M (D_a + R(p) D_b R(p)^T) M^T, symmetric (xx, yy, zz, xy, xz, yz)
+};
+
+__device__ __forceinline__ void rel_frame(RelFrame &f, float4 qa, float4 qb, float sma, float smb,
+                                          float kappa, float imr2a, float imr2b)
+{
+    float4 p = qmul(qconj(qa), qb);
+    if (p.w < 0.f) p = make_float4(-p.x, -p.y, -p.z, -p.w);
+    f.p = p;
+    f.om = kappa * v3(p.x, p.y, p.z);
+    f.h2 = 0.5f * kappa;
+    f.da = 4.f * imr2a / (sma * sma);
+    f.db = 4.f * imr2b / (smb * smb);
+    f.e = qd3(p);
+    V3 pv = {p.x, p.y, p.z};
+    // M ez and M e, with M v = p_w v - p_v x v
+    V3 ez = {0.f, 0.f, 1.f};
+    V3 m1 = p.w * ez - cross(pv, ez);
+    V3 m2 = p.w * f.e - cross(pv, f.e);
+    float c0 = f.da + f.db, c1 = -0.5f * f.da, c2 = -0.5f * f.db;
+    f.N[0] = c0 * (1.f - pv.x * pv.x) + c1 * m1.x * m1.x + c2 * m2.x * m2.x;
+    f.N[1] = c0 * (1.f - pv.y * pv.y) + c1 * m1.y * m1.y + c2 * m2.y * m2.y;
+    f.N[2] = c0 * (1.f - pv.z * pv.z) + c1 * m1.z * m1.z + c2 * m2.z * m2.z;
+    f.N[3] = -c0 * pv.x * pv.y + c1 * m1.x * m1.y + c2 * m2.x * m2.y;
+    f.N[4] = -c0 * pv.x * pv.z + c1 * m1.x * m1.z + c2 * m2.x * m2.z;
+    f.N[5] = -c0 * pv.y * pv.z + c1 * m1.y * m1.z + c2 * m2.y * m2.z;
+}
+
+// Apply dtheta_a = -c R_a D_a M^T dl, dtheta_b = c R_a R(p) D_b R(p)^T M^T dl.
+__device__ __forceinline__ void apply_rel(const RelFrame &f, float4 &qa, float4 &qb, V3 dl, float c)
+{
+    V3 pv = {f.p.x, f.p.y, f.p.z};
+    V3 u = f.p.w * dl + cross(pv, dl);  // M^T dl
+    V3 va = {f.da * u.x, f.da * u.y, 0.5f * f.da * u.z};
+    V3 vb = f.db * u + (-0.5f * f.db * dot(u, f.e)) * f.e;
+    V3 ta = qrot(qa, va);
+    V3 tb = qrot(qa, vb);
+    rotate_by(qa, (-c) * ta);
+    rotate_by(qb, c * tb);
+}
+
+// Solve the symmetric 3x3 system [a0 a3 a4; a3 a1 a5; a4 a5 a2] x = b by
+// cofactors after dividing A and b by the largest diagonal entry: for thin,
+// short segments the entries reach 1e13 and an unscaled FP32 determinant
+// (~A^3) would overflow.
+__device__ __forceinline__ V3 solve_sym3(const float *A_, V3 b)
+{
+    const float sc = 1.f / fmaxf(fmaxf(fabsf(A_[0]), fabsf(A_[1])), fmaxf(fabsf(A_[2]), 1e-30f));
+    float A[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A[k] = A_[k] * sc;
+    b = sc * b;
+    float c00 = A[1] * A[2] - A[5] * A[5];
+    float c01 = A[4] * A[5] - A[3] * A[2];
+    float c02 = A[3] * A[5] - A[4] * A[1];
+    float c11 = A[0] * A[2] - A[4] * A[4];
+    float c12 = A[3] * A[4] - A[0] * A[5];
+    float c22 = A[0] * A[1] - A[3] * A[3];
+    float det = A[0] * c00 + A[3] * c01 + A[4] * c02;
+    float id = 1.f / det;
+    return {(c00 * b.x + c01 * b.y + c02 * b.z) * id, (c01 * b.x + c11 * b.y + c12 * b.z) * id,
+            (c02 * b.x + c12 * b.y + c22 * b.z) * id};
+}
+
+// Interior vertex i with neighbours' scales s_prev, s_next; segments a = i-1
+// and b = i.  rv0 = (Omega_bar, rbar); aB = alpha_B base (the compliance is
+// aB * (4, 4, 2)); aVb = volume-bending compliance; lam = (B.xyz, Vb.u),
+// lam_v = Vb.v.  Order B, Vb.
+//  B   C = s Omega - Omega_bar            (Eq. bending_twist, s_bar = 1)
+//  Vb  C = s^3 Omega_uv - Omega_bar_uv    (Eq. vol, u and v rows)
+__device__ __forceinline__ void project_vertex(float4 &qa, float4 &qb, float &s, float s_prev, float s_next,
+                                               float la, float lb, float imr2a, float imr2b, float ws,
+                                               float4 rv0, float aB, float aVb, float4 &lam, float &lam_v,
+                                               float inv_h2, bool volume)
+{
+    const float kappa = 4.f / (la + lb);
+    // ---- B: bend / twist
+    {
+        RelFrame f;
+        rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
+        V3 C = s * f.om - v3(rv0.x, rv0.y, rv0.z);
+        float k = s * s * f.h2 * f.h2;
+        float atu = 4.f * aB * inv_h2, atw = 2.f * aB * inv_h2;
+        float A[6] = {k * f.N[0] + ws * f.om.x * f.om.x + atu, k * f.N[1] + ws * f.om.y * f.om.y + atu,
+                      k * f.N[2] + ws * f.om.z * f.om.z + atw, k * f.N[3] + ws * f.om.x * f.om.y,
+                      k * f.N[4] + ws * f.om.x * f.om.z,       k * f.N[5] + ws * f.om.y * f.om.z};
+        V3 rhs = {-C.x - atu * lam.x, -C.y - atu * lam.y, -C.z - atw * lam.z};
+        V3 dl = solve_sym3(A, rhs);
+        lam.x += dl.x;
+        lam.y += dl.y;
+        lam.z += dl.z;
+        float ds = ws * dot(f.om, dl);
+        apply_rel(f, qa, qb, dl, s * f.h2);
+        s += ds;
+    }
+    // ---- Vb: volume bending
+    if (volume) {
+        RelFrame f;
+        rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
+        float s2 = s * s, s3 = s2 * s;
+        float cu = s3 * f.om.x - rv0.x, cv = s3 * f.om.y - rv0.y;
+        float k = s3 * s3 * f.h2 * f.h2;
+        float js_u = 3.f * s2 * f.om.x, js_v = 3.f * s2 * f.om.y;
+        float at = aVb * inv_h2;
+        float a00 = k * f.N[0] + ws * js_u * js_u + at;
+        float a11 = k * f.N[1] + ws * js_v * js_v + at;
+        float a01 = k * f.N[3] + ws * js_u * js_v;
+        float r0 = -cu - at * lam.w, r1 = -cv - at * lam_v;
+        const float sc = 1.f / fmaxf(fmaxf(fabsf(a00), fabsf(a11)), 1e-30f);  // keep the determinant in range
+        a00 *= sc; a11 *= sc; a01 *= sc; r0 *= sc; r1 *= sc;
+        float id = 1.f / (a00 * a11 - a01 * a01);
+        float d0 = (a11 * r0 - a01 * r1) * id, d1 = (a00 * r1 - a01 * r0) * id;
+        lam.w += d0;
+        lam_v += d1;
+        float ds = ws * (js_u * d0 + js_v * d1);
+        apply_rel(f, qa, qb, v3(d0, d1, 0.f), s3 * f.h2);
+        s += ds;
+    }
+}
+
+// ---------------------------------------------------------------- pills
+// Closed-form closest sphere of a tapered capsule (App. D): t = (a - h tan th)/l
+// clamped, sin th = (r1 - r2)/l; one end sphere containing the other -> the
+// larger one; degenerate axis -> 0.
+__device__ __forceinline__ float pill_project(V3 c1, float r1, V3 c2, float r2, V3 x)
+{
+    V3 e = c2 - c1;
+    float l = sqrtf(dot(e, e));
+    if (l < 1e-12f) return 0.f;
+    V3 u = (1.f / l) * e;
+    V3 rel = x - c1;
+    float a = dot(rel, u);
+    V3 perp = rel - a * u;
+    float hh = sqrtf(dot(perp, perp));
+    float dr = r1 - r2;
+    if (fabsf(dr) >= l) return dr >= 0.f ? 0.f : 1.f;
+    float sn = dr / l;
+    float tn = sn * rsqrtf(1.f - sn * sn);
+    float t = (a - hh * tn) / l;
+    return fminf(fmaxf(t, 0.f), 1.f);
+}
+
+struct PillPair {
+    V3 a1, a2, b1, b2;
+    float ra1, ra2, rb1, rb2;
+};
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return (1.f - t) * a + t * b; }
+__device__ __forceinline__ V3 lerp3(V3 a, V3 b, float t) { return (1.f - t) * a + t * b; }
+
+// separation of sphere alpha of pill a and its closest sphere of pill b (Eq. collsearch)
+__device__ __forceinline__ float coll_f(const PillPair &P, float al, float &be)
+{
+    V3 pa = lerp3(P.a1, P.a2, al);
+    float ra = lerpf(P.ra1, P.ra2, al);
+    be = pill_project(P.b1, P.rb1, P.b2, P.rb2, pa);
+    V3 d = pa - lerp3(P.b1, P.b2, be);
+    return sqrtf(dot(d, d)) - ra - lerpf(P.rb1, P.rb2, be);
+}
+
+// Dichotomous search, 10 iterations (Sec. 7.2): probes mid -+ eps/2 with
+// eps = 1e-3 of the current bracket; keep the side of the smaller probe.
+__device__ __forceinline__ float dichotomous(const PillPair &P)
+{
+    float lo = 0.f, hi = 1.f, be;
+#pragma unroll 1
+    for (int it = 0; it < 10; ++it) {
+        float mid = 0.5f * (lo + hi);
+        float eps = 1e-3f * (hi - lo);
+        float x1 = mid - 0.5f * eps, x2 = mid + 0.5f * eps;
+        if (coll_f(P, x1, be) < coll_f(P, x2, be))
+            hi = x2;
+        else
+            lo = x1;
+    }
+    return 0.5f * (lo + hi);
+}
+
+// ---------------------------------------------------------------- broadphase predicate
+// Bounding sphere of a pill in IEEE single precision, every operation rounded
+// separately (no FMA contraction), fixed order:
+//   c = (x1 + x2) * 0.5, R = 0.5 * sqrt((dx*dx + dy*dy) + dz*dz) + max(s1 rb1, s2 rb2)
+__device__ __forceinline__ float4 pill_sphere(float4 x1, float rb1, float4 x2, float rb2)
+{
+    float dx = __fsub_rn(x2.x, x1.x), dy = __fsub_rn(x2.y, x1.y), dz = __fsub_rn(x2.z, x1.z);
+    float cx = __fmul_rn(__fadd_rn(x1.x, x2.x), 0.5f);
+    float cy = __fmul_rn(__fadd_rn(x1.y, x2.y), 0.5f);
+    float cz = __fmul_rn(__fadd_rn(x1.z, x2.z), 0.5f);
+    float l2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    float len = __fsqrt_rn(l2);
+    float r1 = __fmul_rn(x1.w, rb1), r2 = __fmul_rn(x2.w, rb2);
+    float R = __fadd_rn(__fmul_rn(0.5f, len), fmaxf(r1, r2));
+    return make_float4(cx, cy, cz, R);
+}
+
+// ((ex*ex + ey*ey) + ez*ez) <= (Ra + Rb)^2, each operation rounded separately
+__device__ __forceinline__ bool spheres_overlap(float4 a, float4 b)
+{
+    float ex = __fsub_rn(a.x, b.x), ey = __fsub_rn(a.y, b.y), ez = __fsub_rn(a.z, b.z);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+    float rs = __fadd_rn(a.w, b.w);
+    return d2 <= __fmul_rn(rs, rs);
+}
+
+// ---------------------------------------------------------------- fixed point
+// Contact corrections are summed as 64-bit fixed point (2^-40 units) so that the
+// per-vertex sums do not depend on the order of the atomic additions.
+constexpr float kFixScale = 1099511627776.0f;  // 2^40
+constexpr float kFixInv = 1.0f / 1099511627776.0f;
+__device__ __forceinline__ unsigned long long to_fix(float v)
+{
+    float c = fminf(fmaxf(v * kFixScale, -9.0e18f), 9.0e18f);
+    return (unsigned long long)__float2ll_rn(c);
+}
+__device__ __forceinline__ float from_fix(unsigned long long v) { return __ll2float_rn((long long)v) * kFixInv; }
+
+}  // namespace viper

@@ -1,0 +1,175 @@
+// viper_impl.h -- internal scene layout and kernel launchers of the VIPER library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/viper.h"
+
+namespace viper {
+
+enum : int { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
+
+// Work item of the shared-memory rod kernel: a packed group of whole rods.
+//   x = first internal vertex, y = vertex count, z = first internal segment, w = segment count
+// Slot descriptor per thread: x = local vertex base | N << 16, y = local segment base | p << 16,
+// or y = -1 for an idle thread.  Slot p of a rod owns segments 2p, 2p+1 and interior
+// vertices 2p+1, 2p+2 (when they exist).
+
+// Uniform grid of the broadphase, recomputed on the device every substep.
+struct Grid {
+    float lo[3];
+    float inv_cell;
+    int dim[3];
+    int pad;
+};
+
+// Kernel arguments shared by every kernel (passed by value).
+struct Params {
+    int nv, ns, n_rods;
+    int n_planes;
+    float h, inv_h, inv_h2, tau;
+    float gx, gy, gz;
+    int volume;
+    // state
+    float4 *X, *V, *Q, *W, *Xp, *Qp, *Xpred;
+    // rest
+    const float4 *RV0, *RV1, *RS0;
+    const float2 *RS1;
+    const int *seg_v0, *vtx_seg, *seg_group;
+    // Vertex positions are stored relative to a per-rod FP32 origin (the rod's
+    // rest centroid) so that differences along a rod keep full precision far
+    // from the world origin; world = local + rod_origin[rod_of_v[v]].
+    const float4 *rod_origin;
+    const int *rod_of_v;
+    const float4 *pins, *bq0, *bq1, *planes;
+    const float *bt0, *bt1;  // bone origins, 3 floats per bone
+    // plain-path multipliers
+    float4 *lamS, *lamB;
+    float2 *lamS2;
+    float *lamB2;
+    // shared-memory path
+    const int4 *items;
+    const int2 *slots;
+    float *slot_lam;
+    int slot_stride;
+    // contacts
+    float contact_alpha;
+    int max_pairs;
+    int2 *pairs;
+    int *npairs;
+    float *lam_pair, *lam_plane;
+    unsigned long long *acc;
+    int *cnt;
+    // broadphase
+    float4 *spheres;
+    unsigned int *bounds;
+    int *cell_of, *cell_count, *cell_start, *cell_pills;
+    int table;
+    Grid *grid;
+    int *err;
+};
+
+struct Alloc {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+
+}  // namespace viper
+
+struct viper_scene {
+    int n_rods = 0, nv = 0, ns = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t ls = nullptr;     // stream the launchers enqueue on (stream, or side during a fork)
+    cudaStream_t side = nullptr;   // second branch: the broadphase runs beside the first rod sweep
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool own_stream = false;
+    int flags = 0, n_pins = 0, n_bones = 0, n_planes = 0;
+    double gravity[3] = {0, 0, 0};
+    double contact_compliance = 0;
+    // permutations (internal <-> caller numbering)
+    std::vector<int> h_vperm, h_sperm, h_vinv, h_sinv, h_rod_perm;
+    std::vector<int> h_off;  // caller rod offsets
+    std::vector<int> h_int_off;  // internal rod offsets (internal rod order)
+    std::vector<int> h_rod_n;    // vertices per caller rod
+    // device arrays
+    viper::Params P{};
+    int *d_vperm = nullptr, *d_sperm = nullptr, *d_sinv = nullptr;
+    float4 *LQ = nullptr, *LC = nullptr;  // LBS rest quaternion / rest midpoint per internal segment
+    float4 *frames = nullptr;             // LBS frames, 3 float4 per caller segment
+    float4 *stage4 = nullptr;             // staging for get/set state (max(nv, ns) float4)
+    float *stage1 = nullptr;
+    int *col_list[4] = {nullptr, nullptr, nullptr, nullptr};
+    int col_n[4] = {0, 0, 0, 0};
+    int *d_scan_tmp = nullptr;
+    int scan_tmp_n = 0;
+    // batched schedule
+    int n_items = 0, block_threads = 0, smem_full = 0, smem_iter = 0;
+    int resident_nv = 0, resident_ns = 0;  // resident rods occupy internal [0, resident_nv)
+    std::vector<int> h_rod_len_int;        // vertex count per internal rod
+    std::vector<int4> h_items;
+    std::vector<int2> h_slots;
+    // options
+    int mode = VIPER_SOLVER_BATCHED;
+    int block_warps = 4;
+    int resident_max = 256;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    float g_dt = 0;
+    int g_sub = 0, g_it = 0;
+    long long g_launches = 0;
+    long long launches = 0;
+    int latched = 0;
+    // rest tables in caller order (FP64 precompute rounded to FP32), kept to rebuild the schedule
+    std::vector<float4> u_RV0, u_RV1, u_RS0, u_LQ, u_LC;
+    std::vector<float2> u_RS1;
+    std::vector<int> u_group;  // per caller rod
+    std::vector<float4> u_origin;  // per caller rod: FP32 rest centroid
+    // pinned host mirror of the device error word (read without a stream sync)
+    int *h_err = nullptr;
+    // scratch for host-pointer skinning
+    float4 *skin_buf = nullptr;
+    size_t skin_cap = 0;
+    size_t bytes = 0;
+    // kernel timing (viper_profile)
+    int prof_class = 0;
+    std::vector<cudaEvent_t> prof_ev;      // frame pool (start, end pairs)
+    int prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev_skin; // skinning pool
+    int prof_used_skin = 0;
+    bool prof_in_skin = false;
+    viper::Alloc alloc;
+    std::vector<void *> owned;
+};
+
+namespace viper {
+
+enum : int { PROF_NONE = 0, PROF_ROD = 1, PROF_CONTACT = 2, PROF_BROADPHASE = 3, PROF_LBS = 4, PROF_ELEM = 5 };
+
+// Brackets the launches issued during its lifetime with events when the scene
+// profiles kernel class `cls`.
+struct ProfScope {
+    viper_scene *s;
+    cudaEvent_t end = nullptr;
+    ProfScope(viper_scene *sc, int cls);
+    ~ProfScope();
+};
+
+// launchers (all enqueue on s->stream and count kernels in s->launches)
+void launch_predict(viper_scene *s, int v_begin, int v_end, int s_begin, int s_end, bool contact_path);
+void launch_finish(viper_scene *s, int v_begin, int v_end, int s_begin, int s_end, bool apply);
+void launch_colour(viper_scene *s, int colour, const int *list, int n);
+void launch_rod_full(viper_scene *s, int n_iter);
+void launch_rod_iter(viper_scene *s, bool first, bool apply);
+void launch_apply(viper_scene *s, int v_begin, int v_end);
+void launch_broadphase(viper_scene *s);
+void launch_contacts(viper_scene *s);
+void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
+void launch_state_out(viper_scene *s, int which, float4 *dst);
+void launch_state_in(viper_scene *s, int which, const float4 *src);
+void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);
+int configure_rod_kernels(int smem_bytes);
+
+}  // namespace viper

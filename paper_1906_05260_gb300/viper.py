@@ -1,0 +1,371 @@
+"""Thin Python binding of the VIPER C ABI (include/viper.h).
+
+Argument marshalling only: every step of the solver runs in libviper.so's CUDA
+kernels.  PyTorch supplies device memory (through the library's allocator
+hook, backed by torch's caching allocator) and CUDA streams.  There is no CPU
+fallback: if the compiled library is missing or no GPU is present, calls fail.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+import os
+import weakref
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libviper.so")
+
+OK = 0
+EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
+FLAG_CONTACTS, FLAG_VOLUME = 1, 2
+SOLVER_PLAIN, SOLVER_BATCHED = 0, 1
+PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE = 0, 1, 2, 3, 4, 5
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_fp = C.POINTER(C.c_float)
+
+
+class ViperError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} ({code})")
+
+
+class Desc(C.Structure):
+    """Mirror of viper_scene_desc."""
+    _fields_ = [
+        ("n_rods", C.c_int), ("rod_offsets", _ip), ("rest_pos", _dp), ("rest_quat", _dp),
+        ("radius", _dp), ("density", _dp), ("c_stretch", _dp), ("c_bend", _dp), ("c_volume", _dp),
+        ("group", _ip), ("gravity", C.c_double * 3), ("n_pins", C.c_int), ("pin_vertex", _ip),
+        ("pin_bone", _ip), ("pin_offset", _dp), ("n_bones", C.c_int), ("bone_quat", _dp),
+        ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
+        ("contact_compliance", C.c_double), ("flags", C.c_int), ("max_pairs", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+_lib = None
+_ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_torch_hooks = None
+_live = weakref.WeakSet()
+
+
+def lib():
+    """Load libviper.so (built by paper_1906_05260_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.viper_scene_create.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
+        L.viper_scene_destroy.argtypes = [vp]
+        L.viper_scene_destroy.restype = None
+        L.viper_scene_counts.argtypes = [vp, _ip, _ip, _ip]
+        L.viper_set_solver.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.viper_autotune.argtypes = [vp, C.c_float, C.c_int, C.c_int, _ip]
+        L.viper_step.argtypes = [vp, C.c_float, C.c_int, C.c_int]
+        L.viper_set_bones.argtypes = [vp, C.c_int, vp, vp]
+        L.viper_skin.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+        L.viper_get_state.argtypes = [vp, vp, vp, vp, vp]
+        L.viper_set_state.argtypes = [vp, vp, vp, vp, vp]
+        L.viper_sync.argtypes = [vp]
+        L.viper_get_pairs.argtypes = [vp, _ip, C.c_int, _ip]
+        L.viper_get_colouring.argtypes = [vp, _ip, _ip]
+        L.viper_get_predicted.argtypes = [vp, vp, vp]
+        L.viper_set_allocator.argtypes = [vp, vp, vp]
+        L.viper_scene_footprint.argtypes = [C.POINTER(Desc)]
+        L.viper_scene_footprint.restype = C.c_size_t
+        L.viper_profile.argtypes = [vp, C.c_int]
+        L.viper_profile_read.argtypes = [vp, _dp, _ip]
+        L.viper_launch_count.argtypes = [vp]
+        L.viper_launch_count.restype = C.c_longlong
+        L.viper_error_string.argtypes = [C.c_int]
+        L.viper_error_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    try:
+        return lib().viper_error_string(int(code)).decode()
+    except Exception:  # library not loadable: still report the number
+        return "error"
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise ViperError(rc, where)
+    return rc
+
+
+def use_torch_allocator():
+    """Route all later scene allocations through torch's CUDA caching allocator."""
+    global _torch_hooks
+    import torch
+    if _torch_hooks is not None:
+        return
+
+    def _alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    _torch_hooks = (_ALLOC_T(_alloc), _FREE_T(_free))
+    _check(lib().viper_set_allocator(C.cast(_torch_hooks[0], C.c_void_p), C.cast(_torch_hooks[1], C.c_void_p),
+                                     None), "viper_set_allocator")
+
+
+def _d(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32).reshape(-1)
+    return a, a.ctypes.data_as(_ip)
+
+
+def make_desc(scene, stream_handle=None, max_pairs=0):
+    """Marshal a scenes.Scene into a viper_scene_desc; returns (desc, keepalive)."""
+    keep = []
+
+    def d(a):
+        arr, p = _d(a)
+        keep.append(arr)
+        return p
+
+    def i(a):
+        arr, p = _i(a)
+        keep.append(arr)
+        return p
+
+    desc = Desc()
+    desc.n_rods = scene.n_rods
+    desc.rod_offsets = i(scene.rod_offsets)
+    desc.rest_pos = d(scene.rest_pos)
+    desc.rest_quat = d(scene.rest_quat)
+    desc.radius = d(scene.radius)
+    desc.density = d(scene.density)
+    desc.c_stretch = d(scene.c_stretch)
+    desc.c_bend = d(scene.c_bend)
+    desc.c_volume = d(scene.c_volume)
+    desc.group = i(scene.group)
+    for c in range(3):
+        desc.gravity[c] = float(scene.gravity[c])
+    n_pins = int(scene.pin_vertex.shape[0])
+    desc.n_pins = n_pins
+    desc.pin_vertex = i(scene.pin_vertex if n_pins else np.zeros(1))
+    desc.pin_bone = i(scene.pin_bone if n_pins else np.zeros(1))
+    desc.pin_offset = d(scene.pin_offset if n_pins else np.zeros(3))
+    nb = 0 if scene.bones is None else scene.bones.n
+    desc.n_bones = nb
+    q0, t0 = scene.bone_pose(0.0) if nb else (np.zeros(4), np.zeros(3))
+    desc.bone_quat = d(q0)
+    desc.bone_trans = d(t0)
+    n_planes = int(scene.planes.shape[0])
+    desc.n_planes = n_planes
+    desc.planes = d(scene.planes if n_planes else np.zeros(4))
+    desc.contact_compliance = float(scene.contact_compliance)
+    desc.flags = (FLAG_CONTACTS if scene.contacts else 0) | (FLAG_VOLUME if scene.volume else 0)
+    desc.max_pairs = int(max_pairs)
+    desc.stream = stream_handle
+    return desc, keep
+
+
+def footprint(scene, max_pairs=0) -> int:
+    desc, keep = make_desc(scene, None, max_pairs)
+    return int(lib().viper_scene_footprint(C.byref(desc)))
+
+
+class Mesh:
+    """Skinning mesh staged on the device as 128-bit-aligned float4/int4 rows."""
+
+    def __init__(self, mesh, device="cuda"):
+        import torch
+        m = mesh.n
+        rest = np.zeros((m, 4), np.float32)
+        rest[:, :3] = mesh.rest
+        self.n = m
+        self.rest = torch.from_numpy(rest).to(device)
+        self.idx = torch.from_numpy(np.ascontiguousarray(mesh.idx, np.int32)).to(device)
+        self.w = torch.from_numpy(np.ascontiguousarray(mesh.w, np.float32)).to(device)
+        self.out = torch.empty((m, 4), dtype=torch.float32, device=device)
+
+
+class Scene:
+    """A device-resident VIPER scene (one viper_scene handle)."""
+
+    def __init__(self, scene, stream=None, solver=SOLVER_BATCHED, block_warps=4, resident_max=256,
+                 max_pairs=0, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required")
+        L = lib()
+        if torch_allocator:
+            use_torch_allocator()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        desc, keep = make_desc(scene, C.c_void_p(self.stream.cuda_stream), max_pairs)
+        h = C.c_void_p()
+        with torch.cuda.stream(self.stream):
+            _check(L.viper_scene_create(C.byref(desc), C.byref(h)), "viper_scene_create")
+        self._h = h
+        self.scene = scene
+        self.n_rods, self.nv, self.ns = scene.n_rods, scene.nv, scene.ns
+        self.t = 0.0
+        _live.add(self)
+        self.set_solver(solver, block_warps, resident_max)
+        if scene.init_pos is not None or scene.init_quat is not None:
+            x4 = self.get_state()["x4"]
+            q4 = None
+            if scene.init_pos is not None:
+                x4[:, :3] = scene.init_pos
+            if scene.init_quat is not None:
+                q4 = np.ascontiguousarray(scene.init_quat, np.float32)
+            self.set_state(x4=x4, q4=q4)
+
+    # -- lifecycle
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().viper_scene_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- solver
+    def set_solver(self, mode=SOLVER_BATCHED, block_warps=4, resident_max=256):
+        _check(lib().viper_set_solver(self._h, int(mode), int(block_warps), int(resident_max)), "viper_set_solver")
+
+    def autotune(self, dt=None, substeps=None, iterations=None):
+        sc = self.scene
+        out = C.c_int()
+        _check(lib().viper_autotune(self._h, float(dt or sc.dt), int(substeps or sc.substeps),
+                                    int(iterations if iterations is not None else sc.iterations),
+                                    C.byref(out)), "viper_autotune")
+        return divmod(out.value, 1000)
+
+    # -- stepping
+    def step(self, dt=None, substeps=None, iterations=None, check=True):
+        sc = self.scene
+        rc = lib().viper_step(self._h, float(dt if dt is not None else sc.dt),
+                              int(substeps if substeps is not None else sc.substeps),
+                              int(iterations if iterations is not None else sc.iterations))
+        self.t += float(dt if dt is not None else sc.dt)
+        if check:
+            _check(rc, "viper_step")
+        return rc
+
+    def set_bones(self, quat, trans):
+        """quat [nb,4], trans [nb,3]: numpy (host) or torch CUDA tensors."""
+        q, t = _ptr_f32(quat), _ptr_f32(trans)
+        _check(lib().viper_set_bones(self._h, int(self.scene.bones.n), q[1], t[1]), "viper_set_bones")
+
+    def frame(self):
+        """One frame of the scene's schedule with bones set to their pose at the frame end."""
+        sc = self.scene
+        if sc.bones is not None:
+            self.set_bones(*sc.bone_pose(self.t + sc.dt))
+        return self.step()
+
+    def skin(self, mesh: Mesh):
+        _check(lib().viper_skin(self._h, mesh.n, C.c_void_p(mesh.rest.data_ptr()), C.c_void_p(mesh.idx.data_ptr()),
+                                C.c_void_p(mesh.w.data_ptr()), C.c_void_p(mesh.out.data_ptr())), "viper_skin")
+        return mesh.out
+
+    def skin_host(self, rest4, idx4, w4, out4):
+        """Skinning with host (numpy) operands; synchronous."""
+        args = [np.ascontiguousarray(a) for a in (rest4, idx4, w4)]
+        _check(lib().viper_skin(self._h, int(args[0].shape[0]), *[C.c_void_p(a.ctypes.data) for a in args],
+                                C.c_void_p(out4.ctypes.data)), "viper_skin")
+        return out4
+
+    def sync(self):
+        return lib().viper_sync(self._h)
+
+    # -- state
+    def get_state(self):
+        x4 = np.zeros((self.nv, 4), np.float32); v4 = np.zeros((self.nv, 4), np.float32)
+        q4 = np.zeros((self.ns, 4), np.float32); w4 = np.zeros((self.ns, 4), np.float32)
+        rc = lib().viper_get_state(self._h, *[C.c_void_p(a.ctypes.data) for a in (x4, v4, q4, w4)])
+        return {"x4": x4, "v4": v4, "q4": q4, "w4": w4, "rc": rc}
+
+    def set_state(self, x4=None, v4=None, q4=None, w4=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float32) for a in (x4, v4, q4, w4)]
+        _check(lib().viper_set_state(self._h, *[None if a is None else C.c_void_p(a.ctypes.data) for a in arrs]),
+               "viper_set_state")
+
+    # -- introspection
+    def pairs(self):
+        n = C.c_int()
+        _check(lib().viper_get_pairs(self._h, None, 0, C.byref(n)), "viper_get_pairs")
+        out = np.zeros((max(n.value, 1), 2), np.int32)
+        _check(lib().viper_get_pairs(self._h, out.ctypes.data_as(_ip), n.value, C.byref(n)), "viper_get_pairs")
+        return out[: n.value]
+
+    def colouring(self):
+        sc = np.zeros(self.ns, np.int32); vc = np.zeros(self.nv, np.int32)
+        rc = lib().viper_get_colouring(self._h, sc.ctypes.data_as(_ip), vc.ctypes.data_as(_ip))
+        _check(rc, "viper_get_colouring")
+        return sc, vc
+
+    def predicted(self):
+        x4 = np.zeros((self.nv, 4), np.float32); rb = np.zeros(self.nv, np.float32)
+        _check(lib().viper_get_predicted(self._h, C.c_void_p(x4.ctypes.data), C.c_void_p(rb.ctypes.data)),
+               "viper_get_predicted")
+        return x4, rb
+
+    def profile(self, kernel_class: int):
+        """Bracket one kernel class with CUDA events (drops cached graphs)."""
+        _check(lib().viper_profile(self._h, int(kernel_class)), "viper_profile")
+
+    def profile_read(self):
+        """(device ms, launches) of the profiled class in the last frame + skin calls."""
+        ms = C.c_double(); n = C.c_int()
+        _check(lib().viper_profile_read(self._h, C.byref(ms), C.byref(n)), "viper_profile_read")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(lib().viper_launch_count(self._h))
+
+
+def _ptr_f32(a):
+    """(keepalive, pointer) for a float32 numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            t = a.contiguous().float()
+            return t, C.c_void_p(t.data_ptr())
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, np.float32)
+    return arr, C.c_void_p(arr.ctypes.data)
+
+
+@atexit.register
+def _close_all():
+    for s in list(_live):
+        try:
+            s.close()
+        except Exception:
+            pass

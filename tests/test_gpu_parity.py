@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every test runs both sides on the same seeded synthetic scene.  Float results
+are compared with the tolerances stated in parity_util; the candidate-pair set
+and the colouring are compared bit for bit (the pair set is recomputed by the
+oracle's FP32 predicate on the GPU's own predicted positions, since the two
+trajectories legitimately differ at threshold pairs).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_05260_gb300 import scenes as S
+from parity_util import ANG_TOL, POS_TOL_1, POS_TOL_100, RAD_TOL, assert_parity, errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1906_05260_gb300 import build
+    build.build()
+    from paper_1906_05260_gb300 import viper
+    return viper
+
+
+def _pair(V, scene, solver, **kw):
+    return V.Scene(scene, solver=solver, **kw), oracle.OracleScene(scene)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_plain_small_one_frame(V, solver):
+    sc = S.plain_small()
+    g, o = _pair(V, sc, solver)
+    g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="plain_small 1 frame")
+    print("plain_small 1 frame errors vs FP64:", e)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_plain_small_100_frames(V, solver):
+    sc = S.plain_small()
+    g, o = _pair(V, sc, solver)
+    for _ in range(100):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_100, rad_tol=1e-4, ang_tol=1e-3,
+                      what="plain_small 100 frames")
+    print("plain_small 100 frames errors vs FP64:", e)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_colouring_bit_exact(V, solver):
+    sc = S.batching(n_rods=300)
+    g, o = _pair(V, sc, solver, resident_max=128)
+    gs, gv = g.colouring()
+    os_, ov = o.colouring()
+    np.testing.assert_array_equal(gs, os_)
+    np.testing.assert_array_equal(gv, ov)
+
+
+def _ragged_scene():
+    """Rods of 2..9 vertices, around the warp / CTA boundaries, and long rods."""
+    lens = [2, 3, 4, 5, 6, 7, 8, 9, 31, 32, 33, 63, 64, 65, 66, 127, 128, 129, 255, 256, 257, 300]
+    base = S.batching(n_rods=len(lens))
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    nv = int(off[-1])
+    rng = np.random.default_rng(9)
+    pos = np.zeros((nv, 3))
+    ipos = np.zeros((nv, 3))
+    iq = []
+    for r, n in enumerate(lens):
+        root = np.array([0.0, 0.3 * r, 0.0])
+        pos[off[r]:off[r + 1]] = root + np.arange(n)[:, None] * np.array([0.01, 0, 0])
+        ang = np.radians(rng.uniform(-30, 30, n - 1))
+        phi = rng.uniform(0, 2 * np.pi, n - 1)
+        axis = np.stack([np.zeros(n - 1), np.cos(phi), np.sin(phi)], 1)
+        qr = S.quat_from_z(np.array([1.0, 0, 0]))
+        qs = S.quat_mul(S.axis_angle_quat(axis * ang[:, None]), np.tile(qr, (n - 1, 1)))
+        d3 = S.quat_rotate(qs, np.tile([0, 0, 1.0], (n - 1, 1)))
+        ipos[off[r]] = root
+        ipos[off[r] + 1:off[r + 1]] = root + np.cumsum(0.01 * d3, axis=0)
+        iq.append(qs)
+    nr = len(lens)
+    return dataclasses.replace(
+        base, rod_offsets=off, rest_pos=pos, rest_quat=np.tile(S.quat_from_z(np.array([1.0, 0, 0])), (nv - nr, 1)),
+        radius=np.repeat(rng.uniform(0.004, 0.02, nr), lens), density=np.full(nr, 1000.0),
+        c_stretch=np.exp(rng.uniform(np.log(1e-8), np.log(1e-5), nr)),
+        c_bend=np.exp(rng.uniform(np.log(1e-8), np.log(1e-5), nr)), c_volume=np.full(nr, 1e-7),
+        group=np.arange(nr, dtype=np.int32), pin_vertex=off[:-1].copy(), pin_bone=np.full(nr, -1, np.int32),
+        pin_offset=pos[off[:-1]].copy(), init_pos=ipos, init_quat=np.concatenate(iq), substeps=10, iterations=4)
+
+
+@pytest.mark.parametrize("solver,warps,resident", [(0, 4, 256), (1, 1, 64), (1, 4, 256), (1, 8, 512)],
+                         ids=["plain", "b1w-res64", "b4w-res256", "b8w-res512"])
+def test_ragged_rod_lengths(V, solver, warps, resident):
+    sc = _ragged_scene()
+    g = V.Scene(sc, solver=solver, block_warps=warps, resident_max=resident)
+    o = oracle.OracleScene(sc)
+    for _ in range(3):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="ragged")
+    gs, gv = g.colouring()
+    os_, ov = o.colouring()
+    np.testing.assert_array_equal(gs, os_)
+    np.testing.assert_array_equal(gv, ov)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_muscle_rig_one_frame_with_contacts_and_skinning(V, solver):
+    sc = S.muscle_rig()
+    g, o = _pair(V, sc, solver)
+    for _ in range(2):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    gst, ost = g.get_state(), o.get_state()
+    e = assert_parity(sc, gst, ost, POS_TOL_1, what="muscle_rig")
+    print("muscle_rig 2 frames errors vs FP64:", e)
+    # skinning: GPU LBS of the GPU state against the oracle's LBS of the same
+    # FP32 state (tight), and against the oracle's LBS of its own state
+    mesh = V.Mesh(sc.mesh)
+    out = g.skin(mesh).cpu().numpy()[:, :3].astype(np.float64)
+    o2 = oracle.OracleScene(sc)
+    o2.set_state(x=gst["x4"][:, :3], s=gst["x4"][:, 3] / sc.radius, q=gst["q4"])
+    ref_same = o2.skin()
+    scale = np.abs(sc.mesh.rest).max()
+    assert np.abs(out - ref_same).max() < 2e-6 * scale
+    ref_own = o.skin()
+    assert np.abs(out - ref_own).max() < POS_TOL_1 * 0.3 * 3  # rods are ~0.22 m; frames move by pos error
+
+
+def test_muscle_rig_pairs_bit_exact(V):
+    sc = S.muscle_rig(mesh_verts=0)
+    g = V.Scene(sc)
+    total = 0
+    for f in range(5):
+        g.frame()
+        x4, rb = g.predicted()
+        ref = oracle.broadphase_f32(sc.rod_offsets, sc.group, x4, rb)
+        got = g.pairs()
+        np.testing.assert_array_equal(got, ref)
+        total += len(ref)
+    assert g.sync() == 0
+
+
+def test_hair_pairs_bit_exact_first_five_frames(V):
+    sc = S.hair()
+    g = V.Scene(sc)
+    counts = []
+    for f in range(5):
+        g.frame()
+        x4, rb = g.predicted()
+        ref = oracle.broadphase_f32(sc.rod_offsets, sc.group, x4, rb)
+        got = g.pairs()
+        assert got.shape == ref.shape, (got.shape, ref.shape)
+        np.testing.assert_array_equal(got, ref)
+        counts.append(len(ref))
+    assert g.sync() == 0
+    print("hair candidate pairs per substep (last substep of frames 0-4):", counts)
+    assert min(counts) > 100_000
+
+
+def test_hair_small_one_frame(V):
+    sc = S.hair(n_rods=400)
+    g, o = _pair(V, sc, 1)
+    g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="hair-400")
+    print("hair (400 rods) 1 frame errors vs FP64:", e)
+
+
+def test_batching_full_size_sampled_rods(V):
+    sc = S.batching()
+    g = V.Scene(sc)
+    sample = np.unique(np.concatenate([np.argsort(sc.rod_lengths())[[0, 1, -1, -2]],
+                                       np.random.default_rng(0).choice(sc.n_rods, 12, replace=False)]))
+    sub = sc.subset(sample)
+    o = oracle.OracleScene(sub)
+    g.frame(); o.frame()
+    assert g.sync() == 0
+    gst = g.get_state()
+    off = sc.rod_offsets
+    vsel = np.concatenate([np.arange(off[r], off[r + 1]) for r in sample])
+    ssel = np.concatenate([np.arange(off[r] - r, off[r + 1] - r - 1) for r in sample])
+    gsub = {"x4": gst["x4"][vsel], "q4": gst["q4"][ssel]}
+    e = assert_parity(sub, gsub, o.get_state(), POS_TOL_1, what="batching sample")
+    print("batching (20x8, sampled rods) 1 frame errors vs FP64:", e)
+
+
+def test_plain_and_batched_agree_on_batching(V):
+    sc = S.batching(n_rods=512)
+    a = V.Scene(sc, solver=0)
+    b = V.Scene(sc, solver=1)
+    for _ in range(3):
+        a.frame(); b.frame()
+    sa, sb = a.get_state(), b.get_state()
+    assert np.abs(sa["x4"] - sb["x4"]).max() < 1e-4
+    qa, qb = sa["q4"].astype(np.float64), sb["q4"].astype(np.float64)
+    ang = 2 * np.arccos(np.clip(np.abs((qa * qb).sum(1)) / np.linalg.norm(qa, axis=1) / np.linalg.norm(qb, axis=1), 0, 1))
+    print("plain vs batched (two FP32 schedules), 3 frames of 20x8: max angle", ang.max(),
+          "max |dx|", np.abs(sa["x4"] - sb["x4"]).max())
+
+
+def test_deterministic_replay(V):
+    sc = S.muscle_rig(mesh_verts=0)
+    a, b = V.Scene(sc), V.Scene(sc)
+    for _ in range(3):
+        a.frame(); b.frame()
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("x4", "v4", "q4", "w4"):
+        np.testing.assert_array_equal(sa[k], sb[k])
+
+
+def test_zero_iterations_is_pure_prediction(V):
+    sc = dataclasses.replace(S.plain_small(n_rods=2), pin_vertex=np.zeros(0, np.int32),
+                             pin_bone=np.zeros(0, np.int32), pin_offset=np.zeros((0, 3)))
+    g, o = _pair(V, sc, 1)
+    g.step(iterations=0); o.step(iterations=0)
+    assert_parity(sc, g.get_state(), o.get_state(), 1e-6, what="iterations=0")
+
+
+def test_nonfinite_state_is_quarantined(V):
+    sc = S.plain_small(n_rods=4)
+    g = V.Scene(sc)
+    st = g.get_state()
+    x4 = st["x4"].copy()
+    x4[5, 1] = np.nan
+    g.set_state(x4=x4)
+    g.step(check=False)
+    assert g.sync() == V.ENONFINITE
+    assert g.step(check=False) == V.ENONFINITE
+    g.set_state(x4=st["x4"], v4=np.zeros_like(st["v4"]), q4=st["q4"], w4=np.zeros_like(st["w4"]))
+    assert g.step(check=False) == 0
+    assert g.sync() == 0
+
+
+def test_state_roundtrip_and_host_skinning(V):
+    sc = S.muscle_rig(n_rods=20, mesh_verts=3000)
+    g = V.Scene(sc)
+    g.frame()
+    st = g.get_state()
+    g.set_state(**{k: st[k] for k in ("x4", "v4", "q4", "w4")})
+    st2 = g.get_state()
+    for k in ("x4", "v4", "w4"):
+        np.testing.assert_allclose(st2[k], st[k], rtol=2e-7, atol=1e-7)
+    mesh = V.Mesh(sc.mesh)
+    dev = g.skin(mesh).cpu().numpy()
+    rest4 = np.zeros((sc.mesh.n, 4), np.float32); rest4[:, :3] = sc.mesh.rest
+    host = np.zeros((sc.mesh.n, 4), np.float32)
+    g.skin_host(rest4, sc.mesh.idx.astype(np.int32), sc.mesh.w.astype(np.float32), host)
+    np.testing.assert_array_equal(dev, host)
+
+
+def test_autotune_keeps_results(V):
+    sc = S.batching(n_rods=256)
+    g = V.Scene(sc)
+    bw, res = g.autotune()
+    assert bw in (1, 2, 4, 8) and res in (64, 128, 256, 512)
+    o = oracle.OracleScene(sc)
+    g.frame(); o.frame()
+    assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="after autotune")
