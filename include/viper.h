@@ -177,6 +177,26 @@ int viper_get_pairs(viper_scene *scene, int *pairs, int cap, int *n_pairs);
  */
 int viper_get_colouring(viper_scene *scene, int *seg_colour, int *vtx_colour);
 
+/*
+ * Stand-alone broadphase (Sec. 7.1) for rods whose state the caller holds on
+ * the device, without a scene: the candidate pairs (a, b), a < b, of segments
+ * ("pills") of different collision groups whose FP32 bounding spheres overlap,
+ * with the same exactly rounded predicate as viper_step.
+ *   rod_offsets [n_rods+1], group [n_rods] (NULL: rod index), x4 [4 n_verts]
+ *   (x, y, z, scale; 16-byte aligned), rbar [n_verts] rest radii (radius =
+ *   scale * rbar): device pointers, read only.
+ *   pairs [2 max_pairs] (device, 8-byte aligned) receives the pairs in no
+ *   particular order; *n_pairs (device int) receives the total count, which
+ *   may exceed max_pairs (then only max_pairs are written).
+ * Work and scratch (about 40 bytes per segment plus an 8-byte-per-cell grid)
+ * are stream-ordered on `stream` (cudaStream_t); the scratch is allocated with
+ * cudaMallocAsync and freed before return, so results are ready when the
+ * stream reaches this point.  VIPER_EINVAL for bad sizes, pointers or
+ * alignment, VIPER_ENOMEM if the scratch cannot be allocated.
+ */
+int viper_broadphase(int n_rods, int n_verts, const int *rod_offsets, const int *group, const float *x4,
+                     const float *rbar, int *pairs, int max_pairs, int *n_pairs, void *stream);
+
 /* Predicted FP32 vertex state (x, y, z, scale) and rest radii of the last
  * substep, as used by the broadphase (host pointers, caller numbering). */
 int viper_get_predicted(viper_scene *scene, float *x4, float *rbar);

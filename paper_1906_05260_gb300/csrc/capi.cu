@@ -252,6 +252,7 @@ int rebuild(viper_scene *s, bool keep_state)
     Params &P = s->P;
     int rc;
     if ((rc = upload(s, const_cast<float4 *>(P.RV0), RV0))) return rc;
+    P.bp_rbar = reinterpret_cast<const float *>(P.RV0) + 3;  // RV0[v].w = rest radius
     if ((rc = upload(s, const_cast<float4 *>(P.RV1), RV1))) return rc;
     if ((rc = upload(s, const_cast<float4 *>(P.RS0), RS0))) return rc;
     if ((rc = upload(s, const_cast<float2 *>(P.RS1), RS1))) return rc;
@@ -662,6 +663,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.gz = (float)d->gravity[2];
     P.volume = (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
+    P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0;
     const bool pills = (d->flags & VIPER_FLAG_CONTACTS) != 0;
 #define A(ptr, n)                                  \

@@ -40,7 +40,8 @@ __global__ void bp_bounds_kernel(Params P)
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
         int a = P.seg_v0[g];
-        float4 sp = pill_sphere(P.Xpred[a], P.RV0[a].w, P.Xpred[a + 1], P.RV0[a + 1].w);
+        const float ra = P.bp_rbar[(size_t)a * P.bp_rbar_stride], rb = P.bp_rbar[(size_t)(a + 1) * P.bp_rbar_stride];
+        float4 sp = pill_sphere(P.Xpred[a], ra, P.Xpred[a + 1], rb);
         P.spheres[g] = sp;
         mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
         mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) bp_emit_kernel(Params P)
                     const int idx = out + __popc(m & ((1u << lane) - 1u));
                     if (idx < P.max_pairs) {
                         P.pairs[idx] = make_int2(a, b);
-                        P.lam_pair[idx] = 0.f;
+                        if (P.lam_pair) P.lam_pair[idx] = 0.f;
                     }
                 }
             }
@@ -323,29 +324,29 @@ __global__ void __launch_bounds__(kScanThreads) scan_small_kernel(const int *in,
     if (threadIdx.x == 0) out[n] = tot;
 }
 
-static void scan(viper_scene *s, const int *in, int n, int *out, int *total)
+static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n, int *out)
 {
-    if (n <= kScanThreads * kSmallPer && !total) {
+    if (n <= kScanThreads * kSmallPer) {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_small_kernel<<<1, kScanThreads, 0, s->ls>>>(in, n, out);
-        s->launches += 1;
+        scan_small_kernel<<<1, kScanThreads, 0, st>>>(in, n, out);
+        if (s) s->launches += 1;
         return;
     }
     int tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles < 1) tiles = 1;
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_tiles_kernel<<<tiles, kScanThreads, 0, s->ls>>>(in, n, s->d_scan_tmp);
+        scan_tiles_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_sums_kernel<<<1, kScanThreads, 0, s->ls>>>(s->d_scan_tmp, tiles, total);
+        scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tmp, tiles, nullptr);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_apply_kernel<<<tiles, kScanThreads, 0, s->ls>>>(in, n, s->d_scan_tmp, out);
+        scan_apply_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp, out);
     }
-    s->launches += 3;
+    if (s) s->launches += 3;
 }
 
 static int sm_count()
@@ -360,34 +361,34 @@ static int sm_count()
     return n;
 }
 
-void launch_broadphase(viper_scene *s)
+void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s)
 {
-    const Params &P = s->P;
     const int grid = (P.ns + 255) / 256 < 4 * sm_count() ? (P.ns + 255) / 256 + 1 : 4 * sm_count();
-    cudaMemsetAsync(P.bounds, 0, 8 * sizeof(unsigned int), s->ls);
+    cudaMemsetAsync(P.bounds, 0, 8 * sizeof(unsigned int), st);
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_bounds_kernel<<<grid, 256, 0, s->ls>>>(P);
+        bp_bounds_kernel<<<grid, 256, 0, st>>>(P);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_count_kernel<<<grid, 256, 0, s->ls>>>(P);
+        bp_count_kernel<<<grid, 256, 0, st>>>(P);
     }
-    s->launches += 2;
-    scan(s, P.cell_count, P.table, P.cell_start, nullptr);
+    scan(s, st, scan_tmp, P.cell_count, P.table, P.cell_start);
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_scatter_kernel<<<grid, 256, 0, s->ls>>>(P);
+        bp_scatter_kernel<<<grid, 256, 0, st>>>(P);
     }
     {
         int eg = (P.ns + kEmitWarps - 1) / kEmitWarps;
         if (eg > 8 * sm_count()) eg = 8 * sm_count();
         if (eg < 1) eg = 1;
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_emit_kernel<<<eg, 32 * kEmitWarps, 0, s->ls>>>(P);
+        bp_emit_kernel<<<eg, 32 * kEmitWarps, 0, st>>>(P);
     }
-    s->launches += 2;
+    if (s) s->launches += 4;
 }
+
+void launch_broadphase(viper_scene *s) { broadphase_enqueue(s->P, s->ls, s->d_scan_tmp, s); }
 
 // ---------------------------------------------------------------- contact pass
 __device__ __forceinline__ void acc_add(const Params &P, int v, V3 d, float ds)

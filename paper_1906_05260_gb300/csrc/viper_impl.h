@@ -62,7 +62,9 @@ struct Params {
     float *lam_pair, *lam_plane;
     unsigned long long *acc;
     int *cnt;
-    // broadphase
+    // broadphase: rest radius of vertex v is bp_rbar[v * bp_rbar_stride]
+    const float *bp_rbar;
+    int bp_rbar_stride;
     float4 *spheres;
     unsigned int *bounds;
     int *cell_of, *cell_count, *cell_start, *cell_pills;
@@ -165,6 +167,9 @@ void launch_rod_full(viper_scene *s, int n_iter);
 void launch_rod_iter(viper_scene *s, bool first, bool apply);
 void launch_apply(viper_scene *s, int v_begin, int v_end);
 void launch_broadphase(viper_scene *s);
+// Enqueue the broadphase on `st` for the pills described by P (Xpred, bp_rbar,
+// seg_v0, seg_group, grid buffers, pairs, npairs); `s` may be null (no scene).
+void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s);
 void launch_contacts(viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
 void launch_state_out(viper_scene *s, int which, float4 *dst);

@@ -83,6 +83,7 @@ def lib():
         L.viper_scene_footprint.restype = C.c_size_t
         L.viper_profile.argtypes = [vp, C.c_int]
         L.viper_profile_read.argtypes = [vp, _dp, _ip]
+        L.viper_broadphase.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp, vp]
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
         L.viper_error_string.argtypes = [C.c_int]
@@ -347,6 +348,28 @@ class Scene:
 
     def launch_count(self) -> int:
         return int(lib().viper_launch_count(self._h))
+
+
+def broadphase(rod_offsets, group, x4, rbar, max_pairs, stream=None):
+    """Stand-alone broadphase on device tensors (torch): returns (pairs[n,2] sorted, total count).
+
+    rod_offsets/group int32, x4 float32 [nv,4] (x, y, z, scale), rbar float32 [nv]."""
+    import torch
+    dev = x4.device
+    n_rods = int(rod_offsets.numel() - 1)
+    pairs = torch.empty((max(int(max_pairs), 1), 2), dtype=torch.int32, device=dev)
+    n = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().viper_broadphase(n_rods, int(x4.shape[0]), C.c_void_p(rod_offsets.data_ptr()),
+                                  None if group is None else C.c_void_p(group.data_ptr()),
+                                  C.c_void_p(x4.data_ptr()), C.c_void_p(rbar.data_ptr()),
+                                  C.c_void_p(pairs.data_ptr()), int(max_pairs), C.c_void_p(n.data_ptr()),
+                                  C.c_void_p(st.cuda_stream)), "viper_broadphase")
+    st.synchronize()
+    total = int(n.item())
+    got = pairs[: min(total, int(max_pairs))].cpu().numpy()
+    order = np.lexsort((got[:, 1], got[:, 0])) if got.size else np.zeros(0, np.int64)
+    return got[order], total
 
 
 def _ptr_f32(a):
