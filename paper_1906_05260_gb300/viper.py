@@ -84,6 +84,7 @@ def lib():
         L.viper_profile.argtypes = [vp, C.c_int]
         L.viper_profile_read.argtypes = [vp, _dp, _ip]
         L.viper_broadphase.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp, vp]
+        L.viper_broadphase_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp, vp]
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
         L.viper_error_string.argtypes = [C.c_int]
