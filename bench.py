@@ -204,6 +204,61 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- our arm
 
+def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, frames):
+    """4096 independent rods (log-uniform 4..256 vertices), 20 substeps x 8 iterations."""
+    from paper_1906_05260_gb300 import scenes as S
+    sc = S.batching()
+    out = {"workload": "batching: 4096 rods, log-uniform 4-256 vertices (250,612 total), "
+                       "random initial bends, 20 substeps x 8 iterations, no contacts"}
+    units = sc.nv * sc.substeps
+    for mode, name in ((V.SOLVER_BATCHED, "batched"), (V.SOLVER_PLAIN, "plain")):
+        g = V.Scene(sc, solver=mode)
+        st = g.stream
+        for _ in range(3):
+            g.step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for i in range(frames):
+            with torch.cuda.stream(st):
+                flush.fill_(i & 0xFF)
+                e0.record(st)
+                g.step()
+                e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = reduce_max(dist, sum(ts) / len(ts))
+        out[name] = {"value": reduce_sum(dist, units) / (ms * 1e-3), "unit": "rod-vertex substeps/s",
+                     "ms_per_frame": ms, "p50_ms": float(np.percentile(ts, 50)),
+                     "p99_ms": float(np.percentile(ts, 99))}
+        if mode == V.SOLVER_BATCHED:
+            g.profile(V.PROF_ROD)
+            g.step()
+            g.profile_read()
+            tot, nl = 0.0, 0
+            for i in range(min(frames, 10)):
+                with torch.cuda.stream(st):
+                    flush.fill_(i & 0xFF)
+                g.step()
+                ms_k, n = g.profile_read()
+                tot += ms_k
+                nl += n
+            us = 1e3 * tot / max(nl, 1)
+            flops = sc.nv * sc.iterations * 1030.0
+            bytes_ = sc.nv * 140.0
+            out["rod_kernel"] = {
+                "us_per_launch": us, "launches_per_frame": nl / min(frames, 10),
+                "alu": {"achieved": flops / (us * 1e-6) / 1e12, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                        "frac": flops / (us * 1e-6) / 1e12 / fp32_peak_tflops},
+                "hbm": {"achieved": bytes_ / (us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": bytes_ / (us * 1e-6) / 1e9 / peaks["hbm_gbs"], "peak_kind": peak_kind},
+            }
+            g.profile(V.PROF_NONE)
+        g.close()
+    out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,6 +267,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--serving", type=float, default=10.0,
+                    help="seconds of the real-time serving load (0 disables)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -399,6 +457,31 @@ def main():
                  "p99_ms": float(np.percentile(tp, 99)), "solver": "plain: one launch per constraint colour"}
         g.set_solver(V.SOLVER_BATCHED)
 
+    # ---- batching workload (4096 rods, 20 x 8, no contacts): batched vs plain and
+    # the shared-memory rod kernel's roofline
+    batching = None
+    if not args.no_batching:
+        batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
+
+    # ---- serving: Poisson stream of muscle-rig scenes, 60 Hz frame requests each
+    serving = None
+    if args.serving > 0:
+        from paper_1906_05260_gb300 import serving as SV
+        g.close()
+        temps = SV.scene_templates(seed=4 + rank)
+        conc = SV.run_load(duration=args.serving, rate=6.4, mean_life=10.0, budget=150 << 30, max_inflight=256,
+                           seed=4 + rank, templates=temps, warm_scenes=64)
+        ser = SV.run_load(duration=max(3.0, args.serving / 2), rate=6.4, mean_life=10.0, budget=150 << 30,
+                          max_inflight=1, seed=4 + rank, templates=temps, warm_scenes=64)
+        serving = {
+            "workload": "Poisson arrivals 6.4/s, lifetimes Exp(10 s), 64 scenes live at start (mean 64 "
+                        "concurrent); muscle rigs of log-uniform 50-500 rods and 10k-300k mesh vertices; "
+                        "60 Hz frame requests per scene, dt=1/60 s, 10 substeps x 4 iterations + LBS; "
+                        "HBM budget 150 GB",
+            "continuous_batching": conc, "serial_per_scene": ser,
+            "throughput_over_serial": conc["rod_vertex_substeps_per_s"] / max(ser["rod_vertex_substeps_per_s"], 1e-9),
+        }
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -417,6 +500,8 @@ def main():
         "skinned_vertices_per_s": reduce_sum(dist, sc.mesh.n) / (mean_ms_max * 1e-3),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         "plain": plain,
+        "batching": batching,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -137,6 +137,13 @@ int viper_autotune(viper_scene *scene, float dt, int substeps, int iterations, i
  */
 int viper_step(viper_scene *scene, float dt, int substeps, int iterations);
 
+/*
+ * Build (capture and instantiate) the frame graph viper_step will replay for
+ * this (dt, substeps, iterations) without running it, so that the first step
+ * does not pay for the capture.  No effect on the plain solver.
+ */
+int viper_prepare(viper_scene *scene, float dt, int substeps, int iterations);
+
 /* Bone poses to reach at the end of the next viper_step (host or device). */
 int viper_set_bones(viper_scene *scene, int n_bones, const float *quat, const float *trans);
 
@@ -255,6 +262,60 @@ int viper_profile_read(viper_scene *scene, double *ms, int *launches);
 
 /* Number of kernel launches the scene enqueued since creation. */
 long long viper_launch_count(const viper_scene *scene);
+
+/* ------------------------------------------------------------------------
+ * Serving: many independent scenes stepped as frame requests arrive.
+ * (The paper steps one scene per frame; this runtime applies its per-substep
+ * solve to a request stream, as its Sec. 7 engine applies it to 100 octopuses.)
+ *
+ * A server keeps every admitted scene resident on the device and admits new
+ * scenes only while the sum of their footprints stays within budget_bytes.
+ * A dispatcher thread keeps up to max_inflight frames on the GPU: whenever a
+ * slot frees up it starts the oldest waiting request of every scene without a
+ * frame in flight, each on the scene's own stream, so frames of different
+ * scenes overlap on the device (continuous batching at frame granularity).
+ * Frames of one scene run in submission order.  Per-scene results do not
+ * depend on what else runs (no shared state; deterministic kernels).
+ * ------------------------------------------------------------------------ */
+typedef struct viper_server viper_server;
+
+typedef struct viper_server_stats {
+    long long frames;            /* completed frame requests                    */
+    long long failed;            /* requests completed with an error            */
+    double rod_vertex_substeps;  /* sum over completed frames of nv x substeps  */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> completion latency    */
+    int scenes, inflight, queued;
+    size_t used_bytes;           /* admitted footprint                          */
+} viper_server_stats;
+
+int viper_server_create(size_t budget_bytes, int max_inflight, viper_server **out);
+/* Drops queued requests, waits for frames in flight, releases every scene. */
+void viper_server_destroy(viper_server *server);
+/*
+ * Admit a scene (desc as for viper_scene_create; desc->stream is ignored) with
+ * an optional skinning mesh (host or device rest4/idx4/w4 [4 n_mesh], copied).
+ * (dt, substeps, iterations) is the frame schedule the scene will be stepped
+ * with: its graph is built here so that its first frame starts at once.
+ * VIPER_EBUDGET if its footprint does not fit the remaining budget now.
+ */
+int viper_server_admit(viper_server *server, const viper_scene_desc *desc, int n_mesh, const float *rest4,
+                       const int *idx4, const float *w4, int solver_mode, float dt, int substeps,
+                       int iterations, int *scene_id);
+/* Queue one frame (host bone poses [4 nb], [3 nb], copied); returns a ticket. */
+int viper_server_submit(viper_server *server, int scene_id, const float *bone_quat, const float *bone_trans,
+                        float dt, int substeps, int iterations, long long *ticket);
+/* Wait for a ticket (VIPER_ETIMEOUT after timeout_ms); status is the frame's VIPER_* code. */
+int viper_server_wait(viper_server *server, long long ticket, double timeout_ms, int *status, double *latency_ms);
+/* Wait until no request is queued or in flight. */
+int viper_server_idle(viper_server *server, double timeout_ms);
+/* Finish the scene's queued frames, then free it and its budget. */
+int viper_server_release(viper_server *server, int scene_id);
+/* The scene handle (for viper_get_state etc.; use only while it is idle). */
+viper_scene *viper_server_scene(viper_server *server, int scene_id);
+/* Copy the skinned mesh of the scene's last completed frame (host or device out4 [4 n_mesh]). */
+int viper_server_mesh_out(viper_server *server, int scene_id, float *out4);
+int viper_server_get_stats(viper_server *server, viper_server_stats *stats);
+int viper_server_reset_stats(viper_server *server);
 
 /* Static text for a VIPER_* code. */
 const char *viper_error_string(int code);

@@ -801,6 +801,42 @@ int viper_set_solver(viper_scene *s, int mode, int block_warps, int resident_max
     return rebuild(s, true);
 }
 
+// Capture and instantiate the frame graph for (dt, substeps, iterations) if the
+// cached one differs.  Called with no other work in flight on the stream.
+static int ensure_graph(viper_scene *s, float dt, int substeps, int iterations)
+{
+    if (s->gexec && s->g_dt == dt && s->g_sub == substeps && s->g_it == iterations) return VIPER_OK;
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    long long before = s->launches;
+    VCHECK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_frame(s, dt, substeps, iterations);
+    cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
+    if (ce != cudaSuccess) return VIPER_ECUDA;
+    ce = cudaGraphInstantiate(&s->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    s->g_launches = s->launches - before;  // kernels per replay (counted while capturing)
+    s->launches = before;
+    if (ce != cudaSuccess) {
+        s->gexec = nullptr;
+        return VIPER_ECUDA;
+    }
+    s->g_dt = dt;
+    s->g_sub = substeps;
+    s->g_it = iterations;
+    return VIPER_OK;
+}
+
+int viper_prepare(viper_scene *s, float dt, int substeps, int iterations)
+{
+    if (!s || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
+    if (s->mode == VIPER_SOLVER_PLAIN) return VIPER_OK;
+    return ensure_graph(s, dt, substeps, iterations);
+}
+
 int viper_step(viper_scene *s, float dt, int substeps, int iterations)
 {
     if (!s || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
@@ -809,29 +845,8 @@ int viper_step(viper_scene *s, float dt, int substeps, int iterations)
     if (s->mode == VIPER_SOLVER_PLAIN) {
         enqueue_frame(s, dt, substeps, iterations);
     } else {
-        if (!s->gexec || s->g_dt != dt || s->g_sub != substeps || s->g_it != iterations) {
-            if (s->gexec) {
-                cudaGraphExecDestroy(s->gexec);
-                s->gexec = nullptr;
-            }
-            cudaGraph_t graph = nullptr;
-            long long before = s->launches;
-            VCHECK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-            enqueue_frame(s, dt, substeps, iterations);
-            cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
-            if (ce != cudaSuccess) return VIPER_ECUDA;
-            ce = cudaGraphInstantiate(&s->gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ce != cudaSuccess) {
-                s->gexec = nullptr;
-                return VIPER_ECUDA;
-            }
-            s->g_launches = s->launches - before;
-            s->launches = before;
-            s->g_dt = dt;
-            s->g_sub = substeps;
-            s->g_it = iterations;
-        }
+        int rc = ensure_graph(s, dt, substeps, iterations);
+        if (rc) return rc;
         VCHECK(cudaGraphLaunch(s->gexec, s->stream));
         s->launches += s->g_launches;
     }

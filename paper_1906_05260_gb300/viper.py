@@ -47,6 +47,13 @@ class Desc(C.Structure):
     ]
 
 
+class ServerStats(C.Structure):
+    """Mirror of viper_server_stats."""
+    _fields_ = [("frames", C.c_longlong), ("failed", C.c_longlong), ("rod_vertex_substeps", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("scenes", C.c_int), ("inflight", C.c_int), ("queued", C.c_int), ("used_bytes", C.c_size_t)]
+
+
 _lib = None
 _ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -85,6 +92,22 @@ def lib():
         L.viper_profile_read.argtypes = [vp, _dp, _ip]
         L.viper_broadphase.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp, vp]
         L.viper_broadphase_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp, vp]
+        L.viper_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+        L.viper_server_destroy.argtypes = [vp]
+        L.viper_server_destroy.restype = None
+        L.viper_server_admit.argtypes = [vp, C.POINTER(Desc), C.c_int, vp, vp, vp, C.c_int, C.c_float, C.c_int,
+                                         C.c_int, _ip]
+        L.viper_prepare.argtypes = [vp, C.c_float, C.c_int, C.c_int]
+        L.viper_server_submit.argtypes = [vp, C.c_int, vp, vp, C.c_float, C.c_int, C.c_int,
+                                          C.POINTER(C.c_longlong)]
+        L.viper_server_wait.argtypes = [vp, C.c_longlong, C.c_double, _ip, _dp]
+        L.viper_server_idle.argtypes = [vp, C.c_double]
+        L.viper_server_release.argtypes = [vp, C.c_int]
+        L.viper_server_scene.argtypes = [vp, C.c_int]
+        L.viper_server_scene.restype = vp
+        L.viper_server_mesh_out.argtypes = [vp, C.c_int, vp]
+        L.viper_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.viper_server_reset_stats.argtypes = [vp]
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
         L.viper_error_string.argtypes = [C.c_int]
