@@ -30,6 +30,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Serving runs one stream per scene; give the driver more hardware work queues
+# than the default 8 so that frames of different scenes overlap (read once, at
+# context creation; a process setting, not a GPU setting).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOAD_DESC = ("muscle_rig: 200 tapered rods of 8-64 vertices pinned to 20 animated bones, "
                  "pill-pill contacts, volume on, dt=1/60 s, 10 substeps x 4 iterations, "
@@ -211,8 +215,8 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
     out = {"workload": "batching: 4096 rods, log-uniform 4-256 vertices (250,612 total), "
                        "random initial bends, 20 substeps x 8 iterations, no contacts"}
     units = sc.nv * sc.substeps
-    for mode, name in ((V.SOLVER_BATCHED, "batched"), (V.SOLVER_PLAIN, "plain")):
-        g = V.Scene(sc, solver=mode)
+    for mode, name in ((V.SOLVER_FRAME, "frame"), (V.SOLVER_BATCHED, "batched"), (V.SOLVER_PLAIN, "plain")):
+        g = V.Scene(sc, solver=mode, resident_max=256)
         st = g.stream
         for _ in range(3):
             g.step()
@@ -231,7 +235,7 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
         out[name] = {"value": reduce_sum(dist, units) / (ms * 1e-3), "unit": "rod-vertex substeps/s",
                      "ms_per_frame": ms, "p50_ms": float(np.percentile(ts, 50)),
                      "p99_ms": float(np.percentile(ts, 99))}
-        if mode == V.SOLVER_BATCHED:
+        if mode in (V.SOLVER_BATCHED, V.SOLVER_FRAME):
             g.profile(V.PROF_ROD)
             g.step()
             g.profile_read()
@@ -244,9 +248,10 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
                 tot += ms_k
                 nl += n
             us = 1e3 * tot / max(nl, 1)
-            flops = sc.nv * sc.iterations * 1030.0
-            bytes_ = sc.nv * 140.0
-            out["rod_kernel"] = {
+            per_launch = sc.substeps if mode == V.SOLVER_FRAME else 1  # substeps per launch
+            flops = sc.nv * sc.iterations * 1030.0 * per_launch
+            bytes_ = sc.nv * 140.0 * (1 if mode == V.SOLVER_FRAME else 1)  # state in/out + rest once per launch
+            out["rod_kernel" if mode == V.SOLVER_BATCHED else "frame_kernel"] = {
                 "us_per_launch": us, "launches_per_frame": nl / min(frames, 10),
                 "alu": {"achieved": flops / (us * 1e-6) / 1e12, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                         "frac": flops / (us * 1e-6) / 1e12 / fp32_peak_tflops},
@@ -256,6 +261,7 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
             g.profile(V.PROF_NONE)
         g.close()
     out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    out["frame_over_plain"] = out["frame"]["value"] / out["plain"]["value"]
     return out
 
 
@@ -292,7 +298,7 @@ def main():
     K, W = args.steps, args.warmup
 
     # per-frame bone poses: the inputs, generated before timing
-    total_frames = 4 * (W + K) + 64
+    total_frames = 10 * (W + K) + 400
     poses_q = np.zeros((total_frames, nb, 4), np.float32)
     poses_t = np.zeros((total_frames, nb, 3), np.float32)
     for f in range(total_frames):
@@ -408,6 +414,8 @@ def main():
             ms, n = g.profile_read()
             tot += ms
             nl += n
+        if nl == 0:
+            continue  # class not launched by this solver (the frame kernel fuses it)
         per_class[name] = {"ms_per_frame": tot / prof_frames, "launches_per_frame": nl / prof_frames,
                            "us_per_launch": 1e3 * tot / max(nl, 1)}
     g.profile(V.PROF_NONE)
@@ -420,7 +428,15 @@ def main():
     nv, ns = sc.nv, sc.ns
     d = per_class[dominant]
     # algorithmic work per launch of each class (derivation in the design doc)
-    if dominant == "rod":
+    pairs_last = g.pairs().shape[0]
+    if dominant == "rod" and g.solver == V.SOLVER_FRAME:
+        # the whole frame: colour sweeps (1030 flop per vertex per sweep) + contact passes
+        # (1500 flop per candidate pair per pass, pair count of the frame's last substep)
+        flops = sc.substeps * sc.iterations * (nv * 1030.0 + pairs_last * 1500.0)
+        roof = {"bound": "alu", "achieved": flops / (d["us_per_launch"] * 1e-6) / 1e12, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "peak_kind": f"FP32 SIMT 152x128x2x{sm_max:.0f} MHz ({peak_kind} clock)",
+                "kernel_name": "frame_kernel<true,true>", "pairs": pairs_last}
+    elif dominant == "rod":
         flops = nv * 1030.0  # FP32 flop per vertex per colour sweep (segment + vertex constraints)
         roof = {"bound": "alu", "achieved": flops / (d["us_per_launch"] * 1e-6) / 1e12, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "peak_kind": f"FP32 SIMT 152x128x2x{sm_max:.0f} MHz ({peak_kind} clock)"}
@@ -445,17 +461,28 @@ def main():
     roof["traffic"] = None
     roof["per_class"] = per_class
 
-    # ---- plain (one launch per colour) path for comparison
+    # ---- the other solvers on the same scene: graph-replayed launches and plain per-colour launches
+    main_solver = g.solver
     plain = None
+    graph = None
     if not args.no_plain:
-        g.set_solver(V.SOLVER_PLAIN)
-        for _ in range(3):
-            device_frame()
-        tp = timed(max(10, K // 2), device_frame)
-        pm = reduce_max(dist, sum(tp) / len(tp))
-        plain = {"value": units / (pm * 1e-3), "ms_per_step": pm, "p50_ms": float(np.percentile(tp, 50)),
-                 "p99_ms": float(np.percentile(tp, 99)), "solver": "plain: one launch per constraint colour"}
-        g.set_solver(V.SOLVER_BATCHED)
+        for mode, label in ((V.SOLVER_BATCHED, "batched: one shared-memory rod launch per iteration, broadphase and "
+                                               "contact launches, frame replayed as a CUDA graph"),
+                            (V.SOLVER_PLAIN, "plain: one launch per constraint colour")):
+            if mode == main_solver:
+                continue
+            g.set_solver(mode)
+            for _ in range(3):
+                device_frame()
+            tp = timed(max(10, K // 2), device_frame)
+            pm = reduce_max(dist, sum(tp) / len(tp))
+            res = {"value": units / (pm * 1e-3), "ms_per_step": pm, "p50_ms": float(np.percentile(tp, 50)),
+                   "p99_ms": float(np.percentile(tp, 99)), "solver": label}
+            if mode == V.SOLVER_PLAIN:
+                plain = res
+            else:
+                graph = res
+        g.set_solver(main_solver)
 
     # ---- batching workload (4096 rods, 20 x 8, no contacts): batched vs plain and
     # the shared-memory rod kernel's roofline
@@ -493,13 +520,17 @@ def main():
         "steps": K, "warmup": W, "ms_per_step": mean_ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "rods": sc.n_rods, "vertices": sc.nv, "mesh_vertices": sc.mesh.n,
-                   "solver": "batched: shared-memory rod kernel, frame replayed as a CUDA graph",
+                   "solver": ("frame: one persistent cooperative launch per frame, rods resident in shared memory, "
+                              "grid barriers between broadphase / sweep / contact phases")
+                             if main_solver == V.SOLVER_FRAME else
+                             "batched: shared-memory rod kernel, frame replayed as a CUDA graph",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{ws} (independent seeded scenes)"},
         "latency_ms": {"p50": p50, "p99": p99},
         "skinned_vertices_per_s": reduce_sum(dist, sc.mesh.n) / (mean_ms_max * 1e-3),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         "plain": plain,
+        "graph_batched": graph,
         "batching": batching,
         "serving": serving,
     }

@@ -56,6 +56,9 @@ extern "C" {
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
 #define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,
                                   a frame replayed from a captured CUDA graph     */
+#define VIPER_SOLVER_FRAME 2   /* one persistent launch per frame: rods stay in
+                                  shared memory across substeps; contact scenes
+                                  synchronise CTAs with bounded grid barriers    */
 
 typedef struct viper_scene viper_scene;
 
@@ -115,9 +118,13 @@ int viper_scene_counts(const viper_scene *scene, int *n_rods, int *n_verts, int 
  * iteration, velocity update; state read from and written to HBM each launch)
  * or VIPER_SOLVER_BATCHED (one shared-memory-resident launch per substep for
  * rods of at most `resident_max` vertices, longer rods on the plain path; a
- * whole frame is captured once into a CUDA graph and replayed).  block_warps
- * is the CTA size in warps for the batched kernel (1, 2, 4 or 8; larger rods
- * raise it as needed).  Changing either drops cached graphs.
+ * whole frame is captured once into a CUDA graph and replayed) or
+ * VIPER_SOLVER_FRAME (one launch steps the whole frame; needs every rod
+ * resident and, for scenes with contacts or half-planes, all work items
+ * co-resident on the GPU -- otherwise VIPER_EINVAL and the solver is left
+ * unchanged).  block_warps is the CTA size in warps for the shared-memory
+ * kernels (1, 2, 4 or 8; larger rods raise it as needed).  Changing either
+ * drops cached graphs.
  */
 int viper_set_solver(viper_scene *scene, int mode, int block_warps, int resident_max);
 
@@ -259,6 +266,9 @@ size_t viper_scene_footprint(const viper_scene_desc *desc);
 #define VIPER_PROF_ELEMENTWISE 5
 int viper_profile(viper_scene *scene, int kernel_class);
 int viper_profile_read(viper_scene *scene, double *ms, int *launches);
+
+/* cudaError_t of the scene's last failed CUDA call behind a VIPER_ECUDA (0 if none). */
+int viper_cuda_error(const viper_scene *scene);
 
 /* Number of kernel launches the scene enqueued since creation. */
 long long viper_launch_count(const viper_scene *scene);

@@ -214,6 +214,7 @@ int rebuild(viper_scene *s, bool keep_state)
         }
     }
     s->n_items = (int)S.items.size();
+    s->P.n_items = s->n_items;
     s->block_threads = S.block_threads;
     s->smem_full = std::max(S.smem_full, 16);
     s->smem_iter = std::max(S.smem_iter, 16);
@@ -308,6 +309,9 @@ int rebuild(viper_scene *s, bool keep_state)
     return VIPER_OK;
 }
 
+// The whole frame in one persistent launch (frame.cu).
+void substeps_frame(viper_scene *s, int substeps, int iterations) { launch_frame(s, substeps, iterations); }
+
 bool contact_path(const viper_scene *s) { return (s->flags & VIPER_FLAG_CONTACTS) || s->n_planes > 0; }
 
 // Enqueue one frame on s->stream.
@@ -322,7 +326,8 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
     const bool cp = contact_path(s);
     const bool pills = (s->flags & VIPER_FLAG_CONTACTS) != 0;
     const int nv = s->nv, ns = s->ns;
-    for (int k = 0; k < substeps; ++k) {
+    if (s->mode == VIPER_SOLVER_FRAME) substeps_frame(s, substeps, iterations);
+    for (int k = 0; k < substeps && s->mode != VIPER_SOLVER_FRAME; ++k) {
         P.tau = (float)((double)(k + 1) / substeps);
         if (s->mode == VIPER_SOLVER_PLAIN) {
             launch_predict(s, 0, nv, 0, ns, cp);
@@ -694,6 +699,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(P.cell_of, pills ? ns : 1); A(P.cell_pills, pills ? ns : 1);
     A(P.cell_count, P.table); A(P.cell_start, P.table + 1);
     A(s->d_scan_tmp, 4096);
+    A(P.bar, 4); A(P.tile_sums, 1024);
 #undef A
 #undef AC
     cudaMemsetAsync(P.err, 0, sizeof(int), s->stream);
@@ -790,15 +796,29 @@ int viper_scene_counts(const viper_scene *s, int *n_rods, int *n_verts, int *n_s
 
 long long viper_launch_count(const viper_scene *s) { return s ? s->launches : 0; }
 
+int viper_cuda_error(const viper_scene *s) { return s ? s->last_cuda : 0; }
+
 int viper_set_solver(viper_scene *s, int mode, int block_warps, int resident_max)
 {
-    if (!s || (mode != VIPER_SOLVER_PLAIN && mode != VIPER_SOLVER_BATCHED)) return VIPER_EINVAL;
+    if (!s || (mode != VIPER_SOLVER_PLAIN && mode != VIPER_SOLVER_BATCHED && mode != VIPER_SOLVER_FRAME))
+        return VIPER_EINVAL;
     if (block_warps != 1 && block_warps != 2 && block_warps != 4 && block_warps != 8) return VIPER_EINVAL;
     if (resident_max < 2 || resident_max > 512) return VIPER_EINVAL;
+    const int old_mode = s->mode, old_bw = s->block_warps, old_rm = s->resident_max;
     s->mode = mode;
     s->block_warps = block_warps;
     s->resident_max = resident_max;
-    return rebuild(s, true);
+    int rc = rebuild(s, true);
+    if (rc == VIPER_OK && mode == VIPER_SOLVER_FRAME) rc = frame_configure(s);
+    if (rc != VIPER_OK) {
+        s->mode = old_mode;
+        s->block_warps = old_bw;
+        s->resident_max = old_rm;
+        int r2 = rebuild(s, true);
+        if (r2 == VIPER_OK && old_mode == VIPER_SOLVER_FRAME) frame_configure(s);
+        return rc;
+    }
+    return VIPER_OK;
 }
 
 // Capture and instantiate the frame graph for (dt, substeps, iterations) if the
@@ -833,7 +853,7 @@ static int ensure_graph(viper_scene *s, float dt, int substeps, int iterations)
 int viper_prepare(viper_scene *s, float dt, int substeps, int iterations)
 {
     if (!s || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
-    if (s->mode == VIPER_SOLVER_PLAIN) return VIPER_OK;
+    if (s->mode != VIPER_SOLVER_BATCHED) return VIPER_OK;
     return ensure_graph(s, dt, substeps, iterations);
 }
 
@@ -842,7 +862,7 @@ int viper_step(viper_scene *s, float dt, int substeps, int iterations)
     if (!s || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
     int e = poll_latched(s);
     if (e == VIPER_ENONFINITE) return e;
-    if (s->mode == VIPER_SOLVER_PLAIN) {
+    if (s->mode != VIPER_SOLVER_BATCHED) {
         enqueue_frame(s, dt, substeps, iterations);
     } else {
         int rc = ensure_graph(s, dt, substeps, iterations);
@@ -850,7 +870,11 @@ int viper_step(viper_scene *s, float dt, int substeps, int iterations)
         VCHECK(cudaGraphLaunch(s->gexec, s->stream));
         s->launches += s->g_launches;
     }
-    if (cudaGetLastError() != cudaSuccess) return VIPER_ECUDA;
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        s->last_cuda = (int)ce;
+        return VIPER_ECUDA;
+    }
     return e;
 }
 
@@ -984,7 +1008,7 @@ int viper_get_colouring(viper_scene *s, int *seg_colour, int *vtx_colour)
         if (arr[i] != -1) bad = 1;
         arr[i] = c;
     };
-    if (s->mode == VIPER_SOLVER_BATCHED && s->n_items > 0) {
+    if (s->mode != VIPER_SOLVER_PLAIN && s->n_items > 0) {
         std::vector<int4> items(s->n_items);
         std::vector<int2> slots((size_t)s->n_items * s->block_threads);
         VCHECK(cudaMemcpy(items.data(), s->P.items, sizeof(int4) * items.size(), cudaMemcpyDeviceToHost));

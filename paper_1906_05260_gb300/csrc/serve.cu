@@ -234,7 +234,14 @@ int viper_server_admit(viper_server *S, const viper_scene_desc *desc, int n_mesh
     viper_scene_desc d = *desc;
     d.stream = nullptr;  // every scene runs on its own stream
     int rc = viper_scene_create(&d, &sl->sc);
-    if (rc == VIPER_OK && solver_mode != VIPER_SOLVER_BATCHED) rc = viper_set_solver(sl->sc, solver_mode, 4, 256);
+    if (rc == VIPER_OK && solver_mode == VIPER_SOLVER_FRAME) {
+        // the frame kernel when the scene fits it, on as few CTAs as it has work
+        // items so that many scenes' frames share the GPU; else the graph path
+        sl->sc->frame_min_grid = 0;
+        if (viper_set_solver(sl->sc, VIPER_SOLVER_FRAME, 4, 512) != VIPER_OK) solver_mode = VIPER_SOLVER_BATCHED;
+    } else if (rc == VIPER_OK && solver_mode != VIPER_SOLVER_BATCHED) {
+        rc = viper_set_solver(sl->sc, solver_mode, 4, 256);
+    }
     if (rc == VIPER_OK && dt > 0 && substeps > 0 && iterations >= 0) rc = viper_prepare(sl->sc, dt, substeps, iterations);
     if (rc == VIPER_OK && n_mesh > 0) {
         const size_t nb = sizeof(float4) * (size_t)n_mesh;

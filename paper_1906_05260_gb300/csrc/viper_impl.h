@@ -52,6 +52,10 @@ struct Params {
     // shared-memory path
     const int4 *items;
     const int2 *slots;
+    int n_items;
+    // persistent frame kernel: grid barrier words and per-tile sums of the cell scan
+    unsigned int *bar;
+    int *tile_sums;
     float *slot_lam;
     int slot_stride;
     // contacts
@@ -109,6 +113,7 @@ struct viper_scene {
     int scan_tmp_n = 0;
     // batched schedule
     int n_items = 0, block_threads = 0, smem_full = 0, smem_iter = 0;
+    int frame_grid = 0, frame_smem = 0, frame_min_grid = 64;  // persistent frame kernel
     int resident_nv = 0, resident_ns = 0;  // resident rods occupy internal [0, resident_nv)
     std::vector<int> h_rod_len_int;        // vertex count per internal rod
     std::vector<int4> h_items;
@@ -123,6 +128,7 @@ struct viper_scene {
     int g_sub = 0, g_it = 0;
     long long g_launches = 0;
     long long launches = 0;
+    int last_cuda = 0;  // cudaError_t of the last failed CUDA call (viper_cuda_error)
     int latched = 0;
     // rest tables in caller order (FP64 precompute rounded to FP32), kept to rebuild the schedule
     std::vector<float4> u_RV0, u_RV1, u_RS0, u_LQ, u_LC;
@@ -176,5 +182,7 @@ void launch_state_out(viper_scene *s, int which, float4 *dst);
 void launch_state_in(viper_scene *s, int which, const float4 *src);
 void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);
 int configure_rod_kernels(int smem_bytes);
+int frame_configure(viper_scene *s);
+void launch_frame(viper_scene *s, int substeps, int iterations);
 
 }  // namespace viper

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "libviper.so")
 OK = 0
 EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
 FLAG_CONTACTS, FLAG_VOLUME = 1, 2
-SOLVER_PLAIN, SOLVER_BATCHED = 0, 1
+SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
+SOLVER_AUTO = -1
 PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE = 0, 1, 2, 3, 4, 5
 
 _dp = C.POINTER(C.c_double)
@@ -233,7 +234,7 @@ class Mesh:
 class Scene:
     """A device-resident VIPER scene (one viper_scene handle)."""
 
-    def __init__(self, scene, stream=None, solver=SOLVER_BATCHED, block_warps=4, resident_max=256,
+    def __init__(self, scene, stream=None, solver=SOLVER_AUTO, block_warps=4, resident_max=256,
                  max_pairs=0, torch_allocator=True):
         import torch
         if not torch.cuda.is_available():
@@ -251,7 +252,9 @@ class Scene:
         self.n_rods, self.nv, self.ns = scene.n_rods, scene.nv, scene.ns
         self.t = 0.0
         _live.add(self)
-        self.set_solver(solver, block_warps, resident_max)
+        # auto: the graph-replayed shared-memory path (measured fastest on contact scenes;
+        # the persistent frame kernel is an explicit option)
+        self.set_solver(SOLVER_BATCHED if solver == SOLVER_AUTO else solver, block_warps, resident_max)
         if scene.init_pos is not None or scene.init_quat is not None:
             x4 = self.get_state()["x4"]
             q4 = None
@@ -281,6 +284,7 @@ class Scene:
     # -- solver
     def set_solver(self, mode=SOLVER_BATCHED, block_warps=4, resident_max=256):
         _check(lib().viper_set_solver(self._h, int(mode), int(block_warps), int(resident_max)), "viper_set_solver")
+        self.solver = mode
 
     def autotune(self, dt=None, substeps=None, iterations=None):
         sc = self.scene
