@@ -218,7 +218,7 @@ int viper_broadphase(int n_rods, int n_verts, const int *rod_offsets, const int 
  * captured, real-time loops that must not wait on an allocator, hosts whose
  * device memory is owned by another allocator.  Same arguments, results and
  * alignment rules as viper_broadphase, but the scratch is one fixed
- * file-scope device array (about 3 MiB, held on every GPU that loads the
+ * file-scope device array (about 4.3 MiB, held on every GPU that loads the
  * library until the process exits), so the call never allocates or frees.
  * Limits: at most VIPER_NOALLOC_MAX_SEGMENTS segments (n_verts - n_rods);
  * larger queries return VIPER_EINVAL without doing any work.
@@ -272,6 +272,66 @@ int viper_cuda_error(const viper_scene *scene);
 
 /* Number of kernel launches the scene enqueued since creation. */
 long long viper_launch_count(const viper_scene *scene);
+
+/* ------------------------------------------------------------------------
+ * Multi-scene step: one frame of many scenes with one launch sequence.
+ * (The paper steps one scene at a time; this applies the same per-substep
+ * solve -- Sec. 6 prediction, the Sec. 5 constraint colours, the Sec. 7
+ * contacts, Sec. 7.4 skinning -- to many scenes at once.)
+ *
+ * Every kernel of the frame covers all scenes of the call: its grid is the
+ * concatenation of the scenes' grids, so a frame of S substeps and I
+ * iterations costs S (7 + 2 I) + 2 launches however many scenes it carries.
+ * Scenes with contacts or half-planes whose rods all fit the shared-memory
+ * kernel (every scene whose rods are at most resident_max long) run the
+ * contact-path sequence; such scenes without contacts run one launch per
+ * substep; the rest are stepped one by one as viper_step would.  Each scene
+ * computes what viper_step computes for it (to FP32 rounding: the same
+ * device code), and its result does not depend on the other scenes of the
+ * call.
+ * ------------------------------------------------------------------------ */
+typedef struct viper_batch viper_batch;
+
+/* One scene of a multi-scene frame. */
+typedef struct viper_batch_item {
+    viper_scene *scene;
+    const float *bone_quat;   /* host [4 n_bones]: pose to reach at the end of the frame, or NULL
+                                 (keep the pose last given)                                       */
+    const float *bone_trans;  /* host [3 n_bones], NULL with bone_quat                            */
+    int n_mesh;               /* mesh vertices to skin after the frame (0: none)                  */
+    const float *rest4;       /* device [4 n_mesh] as for viper_skin                              */
+    const int *idx4;          /* device [4 n_mesh]                                                */
+    const float *w4;          /* device [4 n_mesh]                                                */
+    float *out4;              /* device [4 n_mesh]                                                */
+} viper_batch_item;
+
+/*
+ * A batch context: a stream (`stream`, or a new one when NULL) and
+ * double-buffered pinned/device staging for the per-call scene table.
+ */
+int viper_batch_create(void *stream, viper_batch **out);
+/* Waits for the context's stream and frees it. */
+void viper_batch_destroy(viper_batch *batch);
+
+/*
+ * Advance every item's scene by one frame (dt, substeps, iterations as for
+ * viper_step), bones moving to the item's pose, then skin the item's mesh.
+ * Work is queued on the batch stream, ordered after work already queued on
+ * each scene's stream (and that stream after the batch).  A scene may appear
+ * once per call.  status (optional, n entries) receives each scene's latched
+ * error from earlier frames, as viper_step returns it; a quarantined scene
+ * (VIPER_ENONFINITE) is not stepped.  Errors raised by this frame latch in the
+ * scene (viper_sync, or the next call's status).  Returns VIPER_EINVAL for bad
+ * arguments (nothing queued), VIPER_ENOMEM / VIPER_ECUDA on failures.
+ */
+int viper_batch_step(viper_batch *batch, const viper_batch_item *items, int n, float dt, int substeps,
+                     int iterations, int *status);
+
+/* Stream of the batch context (cudaStream_t). */
+void *viper_batch_stream(const viper_batch *batch);
+
+/* Number of kernel launches the batch context enqueued since creation. */
+long long viper_batch_launch_count(const viper_batch *batch);
 
 /* ------------------------------------------------------------------------
  * Serving: many independent scenes stepped as frame requests arrive.

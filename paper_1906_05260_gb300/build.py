@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libviper.so")
-SOURCES = ["capi.cu", "rod.cu", "contact.cu", "io.cu", "query.cu", "noalloc.cu", "serve.cu", "frame.cu"]
+SOURCES = ["capi.cu", "rod.cu", "contact.cu", "io.cu", "query.cu", "noalloc.cu", "serve.cu", "frame.cu", "batch.cu"]
 HEADERS = ["viper_device.cuh", "viper_impl.h", "phases.cuh", os.path.join("..", "..", "include", "viper.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -1,0 +1,573 @@
+// batch.cu -- multi-scene frame step of the VIPER library (sm_103a).
+//
+// viper_batch_step advances many scenes by one frame with one launch sequence
+// for all of them.  Each kernel's grid is the concatenation of the scenes'
+// grids for that kernel kind; a CTA finds its scene with one barrier count
+// over the kind's block offsets and stages the scene's parameters (the same
+// Params the one-scene kernels take by value) in shared memory.  The
+// per-element work is the one-scene kernels' device code (phases.cuh), so a
+// scene computes the same thing alone and in a batch.
+//
+// Per substep, contact path (pills and/or half-planes):
+//   predict | bounds | count | scan | scatter | emit | {rod sweep | contact} x I | finish
+// without contacts: one full shared-memory rod launch.  After the substeps
+// one launch builds the skinning frames, hands the bone pose on and mirrors
+// the error word to the host; one more skins every mesh.
+//
+// The per-call table (scene parameters, block offsets, bone poses) is written
+// into pinned staging and uploaded with one copy; two staging buffers let the
+// host fill the next call's table while the previous call runs.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "phases.cuh"
+
+namespace viper {
+
+enum BatchKind : int { K_ELEM = 0, K_PILL, K_EMIT, K_SCAN, K_ROD, K_CONTACT, K_END, K_MESH, K_KINDS };
+
+// One scene of a batched frame, as the device sees it.
+struct BatchScene {
+    Params P;  // h, inv_h, inv_h2 of this frame; bq1 / bt1 point at the frame's target pose
+    const float4 *LQ, *LC;
+    const int *sperm;
+    float4 *frames;
+    const float4 *rest;
+    const int4 *idx;
+    const float4 *w;
+    float4 *out;
+    float4 *bq0, *bq1_own;  // the scene's previous / target pose buffers
+    float *bt0, *bt1_own;
+    int *herr;              // device address of the scene's mapped error mirror
+    int n_mesh, n_bones, pills, pad;
+};
+
+struct BatchArgs {
+    const BatchScene *sc;
+    const int *off;  // K_KINDS rows of n + 1 block offsets
+    int n;
+};
+
+constexpr int kElemThreads = 256, kEmitWarpsB = 8, kScanThreadsB = 1024, kScanPerB = 16;
+
+// Scene of this CTA for `kind` (the last scene whose first block is <= blockIdx.x),
+// staged in shared memory; local = block index within the scene, nblk = its block count.
+__device__ __forceinline__ void batch_enter(const BatchArgs &A, int kind, BatchScene &sb, int &local, int &nblk)
+{
+    __shared__ int s_lo, s_hi;
+    const int *o = A.off + kind * (A.n + 1);
+    const int b = blockIdx.x;
+    int cnt = 0;
+    for (int base = 0; base < A.n; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        cnt += __syncthreads_count(t < A.n && o[t] <= b);
+    }
+    const int s = cnt - 1;  // o[0] = 0 <= b, so 0 <= s < n
+    if (threadIdx.x == 0) {
+        s_lo = o[s];
+        s_hi = o[s + 1];
+    }
+    const int *src = reinterpret_cast<const int *>(A.sc + s);
+    int *dst = reinterpret_cast<int *>(&sb);
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchScene) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    local = b - s_lo;
+    nblk = s_hi - s_lo;
+}
+
+// ---------------------------------------------------------------- substep kernels
+// Prediction (Sec. 6) of every vertex and segment; clears the scene's
+// broadphase bounds for this substep's merge.
+__global__ void __launch_bounds__(kElemThreads) batch_predict_kernel(BatchArgs A, float tau)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_ELEM, sb, local, nblk);
+    const Params &P = sb.P;
+    if (sb.pills && local == 0 && threadIdx.x < 8) P.bounds[threadIdx.x] = 0u;
+    const int i = local * blockDim.x + threadIdx.x;
+    if (i < P.nv)
+        predict_vertex_at(P, i, tau, sb.pills != 0, false);
+    else if (i < P.nv + P.ns)
+        predict_segment_at(P, i - P.nv, false);
+}
+
+__global__ void __launch_bounds__(kElemThreads) batch_bounds_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_PILL, sb, local, nblk);
+    const Params &P = sb.P;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
+    const int g = local * blockDim.x + threadIdx.x;
+    if (g < P.ns) bound_pill(P, g, mn, mx, mr);
+    merge_bounds(P, mn, mx, mr);
+}
+
+__global__ void __launch_bounds__(kElemThreads) batch_count_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_PILL, sb, local, nblk);
+    const Params &P = sb.P;
+    bool ok;
+    const Grid G = make_grid(P, ok);
+    if (local == 0 && threadIdx.x == 0) {
+        *P.grid = G;
+        *P.npairs = 0;
+        if (!ok) atomicOr(P.err, ERR_NONFINITE);
+    }
+    const int g = local * blockDim.x + threadIdx.x;
+    if (g < P.ns) count_pill(P, G, g);
+}
+
+// Exclusive scan of the scene's cell counts over the cells its grid spans, by
+// one CTA, 16 cells per thread per round; cell_start[cells] = number of pills.
+__global__ void __launch_bounds__(kScanThreadsB) batch_scan_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    __shared__ int ws[33];
+    int local, nblk;
+    batch_enter(A, K_SCAN, sb, local, nblk);
+    const int n = grid_cells(sb.P.grid, sb.P.table);
+    const int *cc = sb.P.cell_count;
+    int *cs = sb.P.cell_start;
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanThreadsB * kScanPerB) {
+        const int b0 = base + threadIdx.x * kScanPerB;
+        int v[kScanPerB], s = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPerB; ++k) {
+            v[k] = (b0 + k < n) ? cc[b0 + k] : 0;
+            s += v[k];
+        }
+        int tot;
+        int off = block_excl_scan(s, ws, &tot) + carry;
+#pragma unroll
+        for (int k = 0; k < kScanPerB; ++k) {
+            if (b0 + k < n) cs[b0 + k] = off;
+            off += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) cs[n] = carry;
+}
+
+__global__ void __launch_bounds__(kElemThreads) batch_scatter_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_PILL, sb, local, nblk);
+    const Params &P = sb.P;
+    const int g = local * blockDim.x + threadIdx.x;
+    if (g < P.ns) {
+        const int cell = P.cell_of[g];
+        scatter_pill(P, g, cell, P.cell_start[cell]);
+    }
+}
+
+// Candidate pairs, one warp per work unit of a grid cell (see emit_cell).
+__global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_EMIT, sb, local, nblk);
+    const Params &P = sb.P;
+    const Grid G = *P.grid;
+    if (G.pad) return;  // no valid grid: no candidates (uniform over the CTA)
+    const int wib = threadIdx.x >> 5;
+    const int cells = grid_cells(P.grid, P.table);
+    const int *cs = P.cell_start;
+    auto start = [cs](int c) { return cs[c]; };
+    for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
+        emit_cell(P, G, u, start);
+}
+
+// One colour sweep of every work item (contact path): FULL = false, or the
+// whole substep with all iterations (no contacts): FULL = true.
+template <bool FULL>
+__global__ void __launch_bounds__(256) batch_rod_kernel(BatchArgs A, int n_iter, int first, int apply, float tau)
+{
+    __shared__ BatchScene sb;
+    extern __shared__ float4 smem[];
+    int local, nblk;
+    batch_enter(A, K_ROD, sb, local, nblk);
+    rod_item<FULL>(sb.P, local, n_iter, first != 0, apply != 0, tau, smem);
+}
+
+// Jacobi contact pass (Sec. 7.2): pairs, then half-plane vertices, over the scene's CTAs.
+__global__ void __launch_bounds__(kElemThreads) batch_contact_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_CONTACT, sb, local, nblk);
+    const Params &P = sb.P;
+    const int np_all = sb.pills ? *P.npairs : 0;
+    const int np = min(np_all, P.max_pairs);
+    if (local == 0 && threadIdx.x == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
+    const int total = np + (P.n_planes > 0 ? P.nv : 0);
+    const float at = P.contact_alpha * P.inv_h2;
+    for (int i = local * blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
+        if (i < np)
+            contact_pair(P, i, at);
+        else
+            contact_planes(P, i - np, at);
+    }
+}
+
+// Velocity update after the last contact pass.
+__global__ void __launch_bounds__(kElemThreads) batch_finish_kernel(BatchArgs A, int apply)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_ELEM, sb, local, nblk);
+    const Params &P = sb.P;
+    const int i = local * blockDim.x + threadIdx.x;
+    if (i < P.nv)
+        finish_vertex_at(P, i, apply != 0);
+    else if (i < P.nv + P.ns)
+        finish_segment_at(P, i - P.nv);
+}
+
+// ---------------------------------------------------------------- end of frame
+// Skinning frames (scenes with a mesh), the bone pose handed on (previous :=
+// target, and the frame's target kept as the scene's own), and the error word
+// mirrored to the host.
+__global__ void __launch_bounds__(kElemThreads) batch_end_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_END, sb, local, nblk);
+    const Params &P = sb.P;
+    const int g = local * blockDim.x + threadIdx.x;
+    if (sb.n_mesh > 0 && g < P.ns) lbs_frame_at(P, sb.LQ, sb.LC, sb.sperm, sb.frames, g);
+    if (local == 0) {
+        for (int b = threadIdx.x; b < sb.n_bones; b += blockDim.x) {
+            const float4 q = P.bq1[b];
+            const float t0 = P.bt1[3 * b], t1 = P.bt1[3 * b + 1], t2 = P.bt1[3 * b + 2];
+            sb.bq0[b] = q;
+            sb.bt0[3 * b] = t0;
+            sb.bt0[3 * b + 1] = t1;
+            sb.bt0[3 * b + 2] = t2;
+            if (P.bq1 != sb.bq1_own) {
+                sb.bq1_own[b] = q;
+                sb.bt1_own[3 * b] = t0;
+                sb.bt1_own[3 * b + 1] = t1;
+                sb.bt1_own[3 * b + 2] = t2;
+            }
+        }
+        if (threadIdx.x == 0) *(volatile int *)sb.herr = *(volatile int *)P.err;
+    }
+}
+
+__global__ void __launch_bounds__(kElemThreads) batch_skin_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_MESH, sb, local, nblk);
+    for (int i = local * blockDim.x + threadIdx.x; i < sb.n_mesh; i += nblk * blockDim.x)
+        lbs_vertex_at(i, sb.P.ns, sb.rest, sb.idx, sb.w, sb.frames, sb.out, sb.P.err);
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+constexpr int kEmitPillsPerWarp = 8;
+constexpr int kMeshPerThread = 4;
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+}  // namespace viper
+
+struct viper_batch {
+    struct Stage {
+        char *h = nullptr;  // pinned
+        char *d = nullptr;  // device
+        size_t cap = 0;
+        cudaEvent_t done = nullptr;  // the last call that used this stage has finished on the device
+        bool used = false;
+    };
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Stage stage[2];
+    int cur = 0;
+    std::vector<cudaEvent_t> ev;  // ordering after the scenes' streams
+    cudaEvent_t ev_after = nullptr;
+    long long launches = 0;
+};
+
+namespace viper {
+namespace {
+
+int stage_reserve(viper_batch::Stage &S, size_t bytes)
+{
+    if (S.used && cudaEventSynchronize(S.done) != cudaSuccess) return VIPER_ECUDA;
+    if (S.cap >= bytes) return VIPER_OK;
+    size_t cap = std::max(bytes, 2 * S.cap);
+    if (S.h) cudaFreeHost(S.h);
+    if (S.d) cudaFree(S.d);
+    S.h = nullptr;
+    S.d = nullptr;
+    S.cap = 0;
+    if (cudaHostAlloc((void **)&S.h, cap, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        S.h = nullptr;
+        return VIPER_ENOMEM;
+    }
+    if (cudaMalloc((void **)&S.d, cap) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(S.h);
+        S.h = nullptr;
+        S.d = nullptr;
+        return VIPER_ENOMEM;
+    }
+    S.cap = cap;
+    return VIPER_OK;
+}
+
+// One launch sequence for the scenes idx (same CTA size; contact path or not).
+int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<int> &idx, float dt, int substeps,
+              int iterations, bool cp)
+{
+    const int n = (int)idx.size();
+    size_t nb_total = 0;
+    for (int i : idx)
+        if (items[i].bone_quat) nb_total += (size_t)items[i].scene->n_bones;
+    const size_t o_off = align16(sizeof(BatchScene) * n);
+    const size_t o_bq = align16(o_off + sizeof(int) * K_KINDS * (size_t)(n + 1));
+    const size_t o_bt = o_bq + sizeof(float4) * nb_total;
+    const size_t bytes = o_bt + sizeof(float) * 3 * nb_total;
+    viper_batch::Stage &S = B->stage[B->cur];
+    B->cur ^= 1;
+    int rc = stage_reserve(S, bytes);
+    if (rc) return rc;
+
+    BatchScene *hs = reinterpret_cast<BatchScene *>(S.h);
+    int *off = reinterpret_cast<int *>(S.h + o_off);
+    float4 *hbq = reinterpret_cast<float4 *>(S.h + o_bq);
+    float *hbt = reinterpret_cast<float *>(S.h + o_bt);
+    const float4 *dbq = reinterpret_cast<const float4 *>(S.d + o_bq);
+    const float *dbt = reinterpret_cast<const float *>(S.d + o_bt);
+    const double h = (double)dt / substeps;
+    size_t bcur = 0;
+    int smem = 16, threads = 0;
+    for (int k = 0; k <= n; ++k)
+        for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k] = 0;
+    for (int k = 0; k < n; ++k) {
+        const viper_batch_item &it = items[idx[k]];
+        viper_scene *s = it.scene;
+        BatchScene &b = hs[k];
+        memset(&b, 0, sizeof(b));
+        b.P = s->P;
+        b.P.h = (float)h;
+        b.P.inv_h = (float)(1.0 / h);
+        b.P.inv_h2 = (float)(1.0 / (h * h));
+        if (it.bone_quat && s->n_bones > 0) {
+            memcpy(hbq + bcur, it.bone_quat, sizeof(float4) * s->n_bones);
+            memcpy(hbt + 3 * bcur, it.bone_trans, sizeof(float) * 3 * s->n_bones);
+            b.P.bq1 = dbq + bcur;
+            b.P.bt1 = dbt + 3 * bcur;
+            bcur += (size_t)s->n_bones;
+        }
+        b.LQ = s->LQ;
+        b.LC = s->LC;
+        b.sperm = s->d_sperm;
+        b.frames = s->frames;
+        b.rest = reinterpret_cast<const float4 *>(it.rest4);
+        b.idx = reinterpret_cast<const int4 *>(it.idx4);
+        b.w = reinterpret_cast<const float4 *>(it.w4);
+        b.out = reinterpret_cast<float4 *>(it.out4);
+        b.n_mesh = it.n_mesh;
+        b.bq0 = const_cast<float4 *>(s->P.bq0);
+        b.bq1_own = const_cast<float4 *>(s->P.bq1);
+        b.bt0 = const_cast<float *>(s->P.bt0);
+        b.bt1_own = const_cast<float *>(s->P.bt1);
+        b.herr = s->d_herr;
+        b.n_bones = s->n_bones;
+        b.pills = (s->flags & VIPER_FLAG_CONTACTS) ? 1 : 0;
+        const int nv = s->nv, ns = s->ns;
+        int cnt[K_KINDS];
+        cnt[K_ELEM] = cdiv(nv + ns, kElemThreads);
+        cnt[K_PILL] = b.pills ? cdiv(ns, kElemThreads) : 0;
+        cnt[K_EMIT] = b.pills ? cdiv(ns, kEmitWarpsB * kEmitPillsPerWarp) : 0;  // a few work units per warp
+        cnt[K_SCAN] = b.pills ? 1 : 0;
+        cnt[K_ROD] = s->n_items;
+        cnt[K_CONTACT] = cp ? std::min(64, std::max(1, cdiv(ns + (s->n_planes > 0 ? nv : 0), kElemThreads))) : 0;
+        cnt[K_END] = it.n_mesh > 0 ? std::max(1, cdiv(ns, kElemThreads)) : 1;
+        cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
+        for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k + 1] = off[c * (n + 1) + k] + cnt[c];
+        smem = std::max(smem, cp ? s->smem_iter : s->smem_full);
+        threads = s->block_threads;
+    }
+    int tot[K_KINDS];
+    for (int c = 0; c < K_KINDS; ++c) tot[c] = off[c * (n + 1) + n];
+
+    cudaStream_t st = B->stream;
+    if (cudaMemcpyAsync(S.d, S.h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return VIPER_ECUDA;
+    BatchArgs A{reinterpret_cast<const BatchScene *>(S.d), reinterpret_cast<const int *>(S.d + o_off), n};
+    const void *rod_fn = cp ? reinterpret_cast<const void *>(batch_rod_kernel<false>)
+                            : reinterpret_cast<const void *>(batch_rod_kernel<true>);
+    if (raise_smem_limit(rod_fn, smem) != 0) return VIPER_EINVAL;
+    long long L = 0;
+    for (int k = 0; k < substeps; ++k) {
+        const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
+        if (!cp) {
+            batch_rod_kernel<true><<<tot[K_ROD], threads, smem, st>>>(A, iterations, 1, 0, tau);
+            ++L;
+            continue;
+        }
+        batch_predict_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, tau);
+        ++L;
+        if (tot[K_PILL] > 0) {
+            batch_bounds_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+            batch_count_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+            batch_scan_kernel<<<tot[K_SCAN], kScanThreadsB, 0, st>>>(A);
+            batch_scatter_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+            batch_emit_kernel<<<tot[K_EMIT], 32 * kEmitWarpsB, 0, st>>>(A);
+            L += 5;
+        }
+        for (int i = 0; i < iterations; ++i) {
+            batch_rod_kernel<false><<<tot[K_ROD], threads, smem, st>>>(A, 1, i == 0 ? 1 : 0, i > 0 ? 1 : 0, tau);
+            batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
+            L += 2;
+        }
+        batch_finish_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, iterations > 0 ? 1 : 0);
+        ++L;
+    }
+    batch_end_kernel<<<tot[K_END], kElemThreads, 0, st>>>(A);
+    ++L;
+    if (tot[K_MESH] > 0) {
+        batch_skin_kernel<<<tot[K_MESH], kElemThreads, 0, st>>>(A);
+        ++L;
+    }
+    B->launches += L;
+    if (cudaEventRecord(S.done, st) != cudaSuccess) return VIPER_ECUDA;
+    S.used = true;
+    return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;
+}
+
+}  // namespace
+}  // namespace viper
+
+using namespace viper;
+
+extern "C" {
+
+int viper_batch_create(void *stream, viper_batch **out)
+{
+    if (!out) return VIPER_EINVAL;
+    viper_batch *B = new viper_batch();
+    bool ok = true;
+    if (stream) {
+        B->stream = (cudaStream_t)stream;
+    } else {
+        ok = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) == cudaSuccess;
+        B->own_stream = ok;
+    }
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = cudaEventCreateWithFlags(&B->stage[i].done, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&B->ev_after, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        viper_batch_destroy(B);
+        return VIPER_ECUDA;
+    }
+    *out = B;
+    return VIPER_OK;
+}
+
+void viper_batch_destroy(viper_batch *B)
+{
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    for (auto &S : B->stage) {
+        if (S.h) cudaFreeHost(S.h);
+        if (S.d) cudaFree(S.d);
+        if (S.done) cudaEventDestroy(S.done);
+    }
+    for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+    if (B->ev_after) cudaEventDestroy(B->ev_after);
+    if (B->own_stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+void *viper_batch_stream(const viper_batch *B) { return B ? (void *)B->stream : nullptr; }
+
+long long viper_batch_launch_count(const viper_batch *B) { return B ? B->launches : 0; }
+
+int viper_batch_step(viper_batch *B, const viper_batch_item *items, int n, float dt, int substeps, int iterations,
+                     int *status)
+{
+    if (!B || n < 0 || (n > 0 && !items) || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
+    std::vector<viper_scene *> seen(n);
+    for (int i = 0; i < n; ++i) {
+        const viper_batch_item &it = items[i];
+        if (!it.scene || (!it.bone_quat) != (!it.bone_trans) || it.n_mesh < 0) return VIPER_EINVAL;
+        if (it.n_mesh > 0 && (!it.rest4 || !it.idx4 || !it.w4 || !it.out4)) return VIPER_EINVAL;
+        seen[i] = it.scene;
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return VIPER_EINVAL;
+
+    // latched errors; groups of scenes that share one launch sequence
+    std::vector<int> st(n, VIPER_OK), single;
+    std::map<std::pair<int, int>, std::vector<int>> groups;  // (contact path, CTA size) -> items
+    for (int i = 0; i < n; ++i) {
+        viper_scene *s = items[i].scene;
+        st[i] = scene_poll_latched(s);
+        if (st[i] == VIPER_ENONFINITE) continue;
+        if (s->resident_nv == s->nv && s->n_items > 0)
+            groups[{scene_contact_path(s) ? 1 : 0, s->block_threads}].push_back(i);
+        else
+            single.push_back(i);
+    }
+    // the batch stream runs after work already queued on the scenes' streams
+    if ((int)B->ev.size() < n) {
+        for (int i = (int)B->ev.size(); i < n; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return VIPER_ECUDA;
+            B->ev.push_back(e);
+        }
+    }
+    for (auto &g : groups)
+        for (int i : g.second) {
+            viper_scene *s = items[i].scene;
+            if (s->stream == B->stream) continue;
+            if (cudaEventRecord(B->ev[i], s->stream) != cudaSuccess) return VIPER_ECUDA;
+            if (cudaStreamWaitEvent(B->stream, B->ev[i], 0) != cudaSuccess) return VIPER_ECUDA;
+        }
+    for (auto &g : groups) {
+        int rc = run_group(B, items, g.second, dt, substeps, iterations, g.first.first != 0);
+        if (rc) return rc;
+    }
+    if (!groups.empty()) {
+        if (cudaEventRecord(B->ev_after, B->stream) != cudaSuccess) return VIPER_ECUDA;
+        for (auto &g : groups)
+            for (int i : g.second) {
+                viper_scene *s = items[i].scene;
+                if (s->stream != B->stream && cudaStreamWaitEvent(s->stream, B->ev_after, 0) != cudaSuccess)
+                    return VIPER_ECUDA;
+            }
+    }
+    // scenes outside the shared-memory kernels: one by one on their own streams
+    for (int i : single) {
+        const viper_batch_item &it = items[i];
+        viper_scene *s = it.scene;
+        int rc = VIPER_OK;
+        if (it.bone_quat && s->n_bones > 0) rc = viper_set_bones(s, s->n_bones, it.bone_quat, it.bone_trans);
+        if (rc == VIPER_OK) rc = viper_step(s, dt, substeps, iterations);
+        if ((rc == VIPER_OK || rc == VIPER_EOVERFLOW) && it.n_mesh > 0)
+            rc = viper_skin(s, it.n_mesh, it.rest4, it.idx4, it.w4, it.out4);
+        if (rc != VIPER_OK && rc != VIPER_EOVERFLOW) st[i] = rc;
+    }
+    if (status)
+        for (int i = 0; i < n; ++i) status[i] = st[i];
+    return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;
+}
+
+}  // extern "C"

@@ -406,6 +406,10 @@ int poll_latched(viper_scene *s)
 
 namespace viper {
 
+int scene_poll_latched(viper_scene *s) { return poll_latched(s); }
+bool scene_contact_path(const viper_scene *s) { return contact_path(s); }
+int scene_decode_err(int e) { return decode_err(e); }
+
 static void prof_record(viper_scene *s, cudaEvent_t ev)
 {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -572,8 +576,10 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) return fail(VIPER_ECUDA);
     if (cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(VIPER_ECUDA);
     if (cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) return fail(VIPER_ECUDA);
-    if (cudaHostAlloc((void **)&s->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return fail(VIPER_ECUDA);
+    // mapped, so that the multi-scene step can write it from the device
+    if (cudaHostAlloc((void **)&s->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fail(VIPER_ECUDA);
     *s->h_err = 0;
+    if (cudaHostGetDevicePointer((void **)&s->d_herr, s->h_err, 0) != cudaSuccess) return fail(VIPER_ECUDA);
 
     // ---- rest data in FP64, caller order (Sec. 4 discretisation, App. A/B integrals)
     std::vector<int> rod_of_v(nv), pin_of_v(nv, -1);
@@ -697,6 +703,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(P.pairs, pills ? P.max_pairs : 1); A(P.lam_pair, pills ? P.max_pairs : 1); A(P.npairs, 1);
     A(P.spheres, pills ? ns : 1); A(P.bounds, 8); A(P.grid, 1);
     A(P.cell_of, pills ? ns : 1); A(P.cell_pills, pills ? ns : 1);
+    A(P.cell_sph, pills ? ns : 1); A(P.cell_grp, pills ? ns : 1);
     A(P.cell_count, P.table); A(P.cell_start, P.table + 1);
     A(s->d_scan_tmp, 4096);
     A(P.bar, 4); A(P.tile_sums, 1024);

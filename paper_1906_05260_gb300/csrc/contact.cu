@@ -4,13 +4,15 @@
 // centres are binned into a uniform grid whose cell width is the diameter of
 // the largest bounding sphere (slightly enlarged so rounding cannot separate
 // an overlapping pair by more than one cell).  The grid is built with a
-// count / exclusive-scan / scatter pass.  Candidate pairs are then built in
-// parallel (the paper's extension of Green's particle grid): one warp per
-// pill lays the 27 neighbouring cells' occupants out as one flattened list
-// (a warp-shuffle scan of the cell counts), tests 32 candidates per round,
-// compacts the hits with __ballot_sync / __popc and reserves output slots
-// with one atomic per warp and round.  The pair order inside the list is
-// not fixed, the pair set is; every consumer is order independent.
+// count / exclusive-scan / scatter pass that also copies each pill's sphere
+// and group into cell order.  Candidate pairs are then built in parallel (the
+// paper's extension of Green's particle grid): one warp per cell holds the
+// cell's pills one per lane and tests them against the pills of the cell
+// itself and of its 13 forward neighbours (each neighbouring pair of cells
+// is visited once), staged 32 at a time in shared memory; hits are compacted
+// with __ballot_sync / __popc and output slots reserved with one atomic per
+// step.  The pair order inside the list is not fixed, the pair set is; every
+// consumer is order independent.
 //
 // Contact handling (Sec. 7, Sec. 7.2): each candidate pair runs the
 // dichotomous narrowphase and, if the pills interpenetrate, one XPBD update of
@@ -22,32 +24,13 @@
 
 namespace viper {
 
-// bounds[0..2] = enc(-min c), bounds[3..5] = enc(max c), bounds[6] = enc(max R); zeroed before
+// bounds zeroed before (see merge_bounds)
 __global__ void bp_bounds_kernel(Params P)
 {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
-        float4 sp = bp_sphere(P, g);
-        P.spheres[g] = sp;
-        mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
-        mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
-        mr = fmaxf(mr, sp.w);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int c = 0; c < 3; ++c) {
-            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
-            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
-        }
-        mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        for (int c = 0; c < 3; ++c) {
-            atomicMax(P.bounds + c, ord_enc(-mn[c]));
-            atomicMax(P.bounds + 3 + c, ord_enc(mx[c]));
-        }
-        atomicMax(P.bounds + 6, ord_enc(mr));
-    }
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x)
+        bound_pill(P, g, mn, mx, mr);
+    merge_bounds(P, mn, mx, mr);
 }
 
 __global__ void bp_count_kernel(Params P)
@@ -59,45 +42,44 @@ __global__ void bp_count_kernel(Params P)
         *P.npairs = 0;  // pair cursor of bp_emit_kernel
         if (!ok) atomicOr(P.err, ERR_NONFINITE);
     }
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
-        int cell = bp_cell(G, P.spheres[g]);
-        P.cell_of[g] = cell;
-        atomicAdd(P.cell_count + cell, 1);
-    }
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) count_pill(P, G, g);
 }
 
 // cell_count is returned to zero here (each pill takes one slot), ready for the next substep
 __global__ void bp_scatter_kernel(Params P)
 {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
-        int cell = P.cell_of[g];
-        int k = atomicSub(P.cell_count + cell, 1) - 1;
-        P.cell_pills[P.cell_start[cell] + k] = g;
+        const int cell = P.cell_of[g];
+        scatter_pill(P, g, cell, P.cell_start[cell]);
     }
 }
 
 constexpr int kEmitWarps = 8;
 __global__ void __launch_bounds__(32 * kEmitWarps) bp_emit_kernel(Params P)
 {
-    __shared__ int s_start[kEmitWarps][32], s_off[kEmitWarps][32];
     const Grid G = *P.grid;
     if (G.pad) return;  // no valid grid: no candidates
     const int wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kEmitWarps;
+    const int cells = grid_cells(P.grid, P.table);
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
-    for (int a = blockIdx.x * kEmitWarps + wib; a < P.ns; a += nwarps) emit_pill(P, G, a, s_start[wib], s_off[wib], start);
+    for (int u = blockIdx.x * kEmitWarps + wib; u < kEmitUnits * cells; u += nwarps)
+        emit_cell(P, G, u, start);
 }
 
 // ---------------------------------------------------------------- exclusive scan
-// Three passes over 4096-element tiles (1024 threads x 4): tile sums, a scan of
-// the tile sums in one CTA, then the tile scans plus offsets.  In-block scans
-// use __shfl_up_sync warp scans.
+// Exclusive scan of the cell counts over the cells the grid uses (at most the
+// table): three passes over 4096-element tiles (1024 threads x 4): tile sums,
+// a scan of the tile sums in one CTA, then the tile scans plus offsets; or one
+// CTA for tables of up to 16384 cells.  In-block scans use __shfl_up_sync warp
+// scans.  out[cells] = total.
 constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
 
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *in, int n, int *tile_sums)
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *in, int n, int *tile_sums, const Grid *g)
 {
     __shared__ int ws[33];
+    n = grid_cells(g, n);
     int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
     int s = 0;
 #pragma unroll
@@ -108,7 +90,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const int *in,
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int *tile_sums, int n_tiles, int *total_out)
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int *tile_sums, int n_tiles, int *out, int n,
+                                                                 const Grid *g)
 {
     __shared__ int ws[33];
     int base = threadIdx.x * kScanPer;
@@ -125,13 +108,15 @@ __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int *tile_sums,
         if (base + k < n_tiles) tile_sums[base + k] = off;
         off += v[k];
     }
-    if (threadIdx.x == 0 && total_out) *total_out = tot;
+    if (threadIdx.x == 0) out[grid_cells(g, n)] = tot;
 }
 
-// out[i] = sum in[0..i-1]; out[n] = total
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in, int n, const int *tile_sums, int *out)
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in, int n, const int *tile_sums, int *out,
+                                                                  const Grid *g)
 {
     __shared__ int ws[33];
+    n = grid_cells(g, n);
+    if (blockIdx.x * kScanTile >= n) return;  // uniform over the CTA
     int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
     int v[kScanPer], s = 0;
 #pragma unroll
@@ -146,14 +131,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in,
         if (base + k < n) out[base + k] = off;
         off += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = off;
 }
 
-// Single-CTA scan for n <= 16384 (16 elements per thread); out[n] = total.
 constexpr int kSmallPer = 16;
-__global__ void __launch_bounds__(kScanThreads) scan_small_kernel(const int *in, int n, int *out)
+__global__ void __launch_bounds__(kScanThreads) scan_small_kernel(const int *in, int n, int *out, const Grid *g)
 {
     __shared__ int ws[33];
+    n = grid_cells(g, n);
     const int base = threadIdx.x * kSmallPer;
     int v[kSmallPer], s = 0;
 #pragma unroll
@@ -171,11 +155,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_small_kernel(const int *in,
     if (threadIdx.x == 0) out[n] = tot;
 }
 
-static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n, int *out)
+static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n, int *out, const Grid *g)
 {
     if (n <= kScanThreads * kSmallPer) {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_small_kernel<<<1, kScanThreads, 0, st>>>(in, n, out);
+        scan_small_kernel<<<1, kScanThreads, 0, st>>>(in, n, out, g);
         if (s) s->launches += 1;
         return;
     }
@@ -183,15 +167,15 @@ static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n
     if (tiles < 1) tiles = 1;
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_tiles_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp);
+        scan_tiles_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp, g);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tmp, tiles, nullptr);
+        scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tmp, tiles, out, n, g);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        scan_apply_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp, out);
+        scan_apply_kernel<<<tiles, kScanThreads, 0, st>>>(in, n, tmp, out, g);
     }
     if (s) s->launches += 3;
 }
@@ -220,13 +204,13 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
         ProfScope ps(s, PROF_BROADPHASE);
         bp_count_kernel<<<grid, 256, 0, st>>>(P);
     }
-    scan(s, st, scan_tmp, P.cell_count, P.table, P.cell_start);
+    scan(s, st, scan_tmp, P.cell_count, P.table, P.cell_start, P.grid);
     {
         ProfScope ps(s, PROF_BROADPHASE);
         bp_scatter_kernel<<<grid, 256, 0, st>>>(P);
     }
     {
-        int eg = (P.ns + kEmitWarps - 1) / kEmitWarps;
+        int eg = (P.ns + 8 * kEmitWarps - 1) / (8 * kEmitWarps);  // a warp per 8 pills: a few units each
         if (eg > 8 * sm_count()) eg = 8 * sm_count();
         if (eg < 1) eg = 1;
         ProfScope ps(s, PROF_BROADPHASE);

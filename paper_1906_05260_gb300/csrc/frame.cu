@@ -71,26 +71,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int nbl
     return s_ok != 0;
 }
 
-// Block-wide min/max of the sphere bounds, merged into P.bounds (see bp_bounds_kernel).
-__device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float mx[3], float mr)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int c = 0; c < 3; ++c) {
-            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
-            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
-        }
-        mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
-    }
-    if ((threadIdx.x & 31) == 0 && mr > 0.f) {
-        for (int c = 0; c < 3; ++c) {
-            atomicMax(P.bounds + c, ord_enc(-mn[c]));
-            atomicMax(P.bounds + 3 + c, ord_enc(mx[c]));
-        }
-        atomicMax(P.bounds + 6, ord_enc(mr));
-    }
-}
-
 // Exclusive scan of one tile of cell counts (blockDim x 16 cells) into
 // P.cell_start (tile-local prefixes) and its total into P.tile_sums[t].
 __device__ __forceinline__ void scan_tile(const Params &P, int t, int *ws)
@@ -132,12 +112,17 @@ __device__ __forceinline__ void tile_offsets(const Params &P, int ntiles, int *t
     __syncthreads();
 }
 
+// First entry of cell c in cell order: tile-local prefix plus tile offset.
+struct FrameStart {
+    const int *cs, *toff;
+    int table, T, ntiles;
+    __device__ int operator()(int c) const { return c >= table ? toff[ntiles] : cs[c] + toff[c / T]; }
+};
 // BARRIERS: grid-wide phases present (contacts or half-planes); PILLS: pill-pill contacts.
 template <bool BARRIERS, bool PILLS>
 __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int substeps, int iters)
 {
     extern __shared__ float4 smem[];
-    __shared__ int s_start[kFrameWarps][32], s_off[kFrameWarps][32];
     __shared__ int s_ws[33];
     __shared__ int s_toff[kMaxTiles + 1];
     const bool owner = blockIdx.x < P.n_items;
@@ -194,14 +179,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
         if (PILLS) {
             __syncthreads();
             float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
-            for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
-                const int g = item.z + j;
-                const float4 sp = bp_sphere(P, g);
-                P.spheres[g] = sp;
-                mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
-                mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
-                mr = fmaxf(mr, sp.w);
-            }
+            for (int j = threadIdx.x; j < item.w; j += blockDim.x) bound_pill(P, item.z + j, mn, mx, mr);
             merge_bounds(P, mn, mx, mr);
             if (!grid_barrier(P.bar, nb, P.err)) return;
         }
@@ -215,11 +193,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
                 if (!ok) atomicOr(P.err, ERR_NONFINITE);
             }
             if (!G.pad)
-                for (int g = gtid; g < P.ns; g += gthreads) {
-                    const int cell = bp_cell(G, P.spheres[g]);
-                    P.cell_of[g] = cell;
-                    atomicAdd(P.cell_count + cell, 1);
-                }
+                for (int g = gtid; g < P.ns; g += gthreads) count_pill(P, G, g);
         }
         if (iters > 0 && owner) {
             __syncthreads();
@@ -239,13 +213,16 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
             if (!G.pad)
                 for (int g = gtid; g < P.ns; g += gthreads) {
                     const int cell = P.cell_of[g];
-                    const int slot = atomicSub(P.cell_count + cell, 1) - 1;
-                    P.cell_pills[start(cell) + slot] = g;
+                    scatter_pill(P, g, cell, start(cell));
                 }
             if (!grid_barrier(P.bar, nb, P.err)) return;
-            // ---- candidate pairs (warp per pill)
-            if (!G.pad)
-                for (int a = gwarp; a < P.ns; a += gwarps) emit_pill(P, G, a, s_start[wib], s_off[wib], start);
+            // ---- candidate pairs (warp per grid cell)
+            if (!G.pad) {
+                const int cells = (int)min((long long)G.dim[0] * G.dim[1] * G.dim[2], (long long)P.table);
+                const FrameStart fs{cs, toff, table, T, ntiles};
+                for (int u = gwarp; u < kEmitUnits * cells; u += gwarps)
+                    emit_cell(P, G, u, fs);
+            }
             if (!grid_barrier(P.bar, nb, P.err)) return;
         } else if (BARRIERS && iters > 0) {
             if (!grid_barrier(P.bar, nb, P.err)) return;  // published positions before the first contact pass

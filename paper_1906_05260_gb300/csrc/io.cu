@@ -6,60 +6,23 @@
 // by the caller's segment id; a second kernel gathers four frames per mesh
 // vertex with 128-bit loads of the rest position, frame ids and weights and a
 // 128-bit store of the result.
-#include "viper_device.cuh"
-#include "viper_impl.h"
+#include "phases.cuh"
 
 namespace viper {
 
 __global__ void lbs_frames_kernel(Params P, const float4 *__restrict__ LQ, const float4 *__restrict__ LC,
                                   const int *__restrict__ sperm, float4 *__restrict__ frames)
 {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.ns) return;
-    int a = P.seg_v0[g];
-    float4 xa = P.X[a], xb = P.X[a + 1];
-    float sm = 0.5f * (xa.w + xb.w);
-    float4 q = P.Q[g], qb = LQ[g];
-    float4 r = qmul(q, qconj(qb));  // R_j Rbar_j^T
-    V3 c0 = qrot(r, v3(1.f, 0.f, 0.f)), c1 = qrot(r, v3(0.f, 1.f, 0.f)), c2 = qrot(r, v3(0.f, 0.f, 1.f));
-    c0 = sm * c0;
-    c1 = sm * c1;
-    c2 = sm * c2;
-    float4 cb = LC[g];
-    V3 cm = 0.5f * (xyz(xa) + xyz(xb)) + xyz(P.rod_origin[P.rod_of_v[a]]);
-    V3 t = cm - (cb.x * c0 + cb.y * c1 + cb.z * c2);
-    float4 *f = frames + 3 * (size_t)sperm[g];
-    f[0] = make_float4(c0.x, c1.x, c2.x, t.x);
-    f[1] = make_float4(c0.y, c1.y, c2.y, t.y);
-    f[2] = make_float4(c0.z, c1.z, c2.z, t.z);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < P.ns) lbs_frame_at(P, LQ, LC, sperm, frames, g);
 }
 
-// Frame ids outside [0, ns) contribute nothing and raise the error word.
 __global__ void lbs_gather_kernel(int n, int ns, const float4 *__restrict__ rest, const int4 *__restrict__ idx,
                                   const float4 *__restrict__ w, const float4 *__restrict__ frames,
                                   float4 *__restrict__ out, int *err)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 p = __ldcs(rest + i);
-        const int4 id = __ldcs(idx + i);
-        const float4 ww = __ldcs(w + i);
-        const int ids[4] = {id.x, id.y, id.z, id.w};
-        const float wv[4] = {ww.x, ww.y, ww.z, ww.w};
-        float ox = 0.f, oy = 0.f, oz = 0.f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if ((unsigned)ids[k] >= (unsigned)ns) {
-                atomicOr(err, ERR_OVERFLOW);
-                continue;
-            }
-            const float4 *f = frames + 3 * (size_t)ids[k];
-            const float4 r0 = __ldg(f), r1 = __ldg(f + 1), r2 = __ldg(f + 2);
-            ox += wv[k] * (r0.x * p.x + r0.y * p.y + r0.z * p.z + r0.w);
-            oy += wv[k] * (r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w);
-            oz += wv[k] * (r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
-        }
-        __stcs(out + i, make_float4(ox, oy, oz, 0.f));
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        lbs_vertex_at(i, ns, rest, idx, w, frames, out, err);
 }
 
 static int sms()

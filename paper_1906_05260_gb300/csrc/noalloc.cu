@@ -16,9 +16,9 @@
 
 namespace viper {
 
-size_t broadphase_scratch_layout(int ns, int table, size_t off[9]);
+size_t broadphase_scratch_layout(int ns, int table, size_t off[kBpSections]);
 int broadphase_table_size(int ns);
-void broadphase_params(Params &P, char *base, const size_t off[9], int n_rods, int nv, const float *x4,
+void broadphase_params(Params &P, char *base, const size_t off[kBpSections], int n_rods, int nv, const float *x4,
                        const float *rbar, int *pairs, int max_pairs, int *n_pairs, int table);
 int broadphase_check_args(int n_rods, int n_verts, const int *rod_offsets, const float *x4, const float *rbar,
                           int *pairs, int max_pairs, int *n_pairs);
@@ -31,11 +31,11 @@ namespace {
 constexpr int kMaxSegments = VIPER_NOALLOC_MAX_SEGMENTS;
 constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kTable = 131072;
-constexpr size_t kScratchBytes = round256(16 * (size_t)kMaxSegments) + 4 * round256(4 * (size_t)kMaxSegments) +
+constexpr size_t kScratchBytes = 2 * round256(16 * (size_t)kMaxSegments) + 5 * round256(4 * (size_t)kMaxSegments) +
                                  round256(4 * kTable) + round256(4 * (kTable + 1)) + round256(4 * 4096) +
                                  round256(sizeof(unsigned int) * 8 + sizeof(Grid) + 4 * sizeof(int));
 
-// The scratch itself: every GPU that loads this library holds these ~3 MiB
+// The scratch itself: every GPU that loads this library holds these ~4.3 MiB
 // until the process exits.  In host code the symbol is only a host-side
 // handle, never a device address; the address comes from
 // cudaGetSymbolAddress below.
@@ -79,7 +79,7 @@ extern "C" int viper_broadphase_noalloc(int n_rods, int n_verts, const int *rod_
     const int ns = n_verts - n_rods;
     if (ns > kMaxSegments) return VIPER_EINVAL;  // larger than the fixed scratch
     const int table = broadphase_table_size(ns);
-    size_t off[9];
+    size_t off[kBpSections];
     if (broadphase_scratch_layout(ns, table, off) > kScratchBytes) return VIPER_EINVAL;
     void *base = nullptr;
     if ((rc = scratch_address(&base))) return rc;

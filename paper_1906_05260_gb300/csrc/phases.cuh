@@ -124,6 +124,56 @@ __device__ __forceinline__ float4 apply_pending(const Params &P, int v, float4 x
     return x;
 }
 
+// ---------------------------------------------------------------- element phases
+// Prediction of vertex v at substep fraction tau (Sec. 6): keeps the substep's
+// start in Xp, writes the predicted world position for the broadphase when
+// `world`, clears the half-plane multipliers and, when `plain_lam`, the
+// per-constraint multipliers of the launch-per-colour kernels.
+__device__ __forceinline__ void predict_vertex_at(const Params &P, int v, float tau, bool world, bool plain_lam)
+{
+    float4 x = P.X[v];
+    P.Xp[v] = x;
+    x = predict_vertex(P, x, P.V[v], P.RV1[v], tau);
+    P.X[v] = x;
+    if (world) P.Xpred[v] = to_world(P, v, x);
+    if (plain_lam) {
+        P.lamB[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.lamB2[v] = 0.f;
+    }
+    for (int k = 0; k < P.n_planes; ++k) P.lam_plane[(size_t)v * P.n_planes + k] = 0.f;
+}
+
+__device__ __forceinline__ void predict_segment_at(const Params &P, int g, bool plain_lam)
+{
+    float4 q = P.Q[g];
+    P.Qp[g] = q;
+    P.Q[g] = predict_quat(P, q, P.W[g]);
+    if (plain_lam) {
+        P.lamS[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P.lamS2[g] = make_float2(0.f, 0.f);
+    }
+}
+
+// Velocity update of vertex v (after the pending contact corrections when `apply`).
+__device__ __forceinline__ void finish_vertex_at(const Params &P, int v, bool apply)
+{
+    float4 x = P.X[v];
+    if (apply) x = apply_pending(P, v, x);
+    const float4 xp = P.Xp[v];
+    const float4 vel = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
+                                   (x.w - xp.w) * P.inv_h);
+    check_finite(P, x);
+    P.X[v] = x;
+    P.V[v] = vel;
+}
+
+__device__ __forceinline__ void finish_segment_at(const Params &P, int g)
+{
+    const float4 q = P.Q[g];
+    check_finite(P, q);
+    P.W[g] = omega_of(P, q, P.Qp[g]);
+}
+
 // Multipliers of one slot kept across launches (contact path): 22 floats.
 struct SlotLam {
     float4 s0, s1, b1, b2;
@@ -275,6 +325,80 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
     __syncthreads();
 }
 
+// One work item of the shared-memory rod solve: a CTA stages the item's float4
+// state in shared memory with coalesced loads (FULL: predicting it first; else
+// adding the pending contact corrections when `apply`), runs n_iter colour
+// sweeps with each thread's constraints held in registers, and writes the
+// state back (FULL: with the velocity update).  Item b's slot descriptors and
+// multipliers are entries b * blockDim.x + threadIdx.x.  Every thread of the
+// CTA must call it.
+template <bool FULL>
+__device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, bool first, bool apply, float tau,
+                                         float4 *smem)
+{
+    const int4 item = P.items[b];
+    float4 *sX = smem;
+    float4 *sQ = smem + item.y;
+    float4 *sXp = sQ + item.w;
+    float4 *sQp = sXp + item.y;
+
+    for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
+        const int v = item.x + i;
+        float4 x = P.X[v];
+        if (FULL) {
+            sXp[i] = x;
+            x = predict_vertex(P, x, P.V[v], P.RV1[v], tau);
+        } else if (apply) {
+            x = apply_pending(P, v, x);
+        }
+        sX[i] = x;
+    }
+    for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
+        const int g = item.z + j;
+        float4 q = P.Q[g];
+        if (FULL) {
+            sQp[j] = q;
+            q = predict_quat(P, q, P.W[g]);
+        }
+        sQ[j] = q;
+    }
+
+    const int slot = b * blockDim.x + threadIdx.x;
+    SlotRest R;
+    load_slot(P, item, P.slots[slot], R);
+    SlotLam L;
+    if (FULL || first)
+        zero_lam(L);
+    else
+        lam_load(P, slot, L);
+    __syncthreads();
+    const bool vol = P.volume != 0;
+#pragma unroll 1
+    for (int k = 0; k < n_iter; ++k) sweep(sX, sQ, R, L, P.inv_h2, vol);
+    if (!FULL && R.active) lam_store(P, slot, L);
+
+    for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
+        const int v = item.x + i;
+        float4 x = sX[i];
+        if (FULL) {
+            float4 xp = sXp[i];
+            P.V[v] = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
+                                 (x.w - xp.w) * P.inv_h);
+            check_finite(P, x);
+        }
+        P.X[v] = x;
+    }
+    for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
+        const int g = item.z + j;
+        float4 q = sQ[j];
+        if (FULL) {
+            P.W[g] = omega_of(P, q, sQp[j]);
+            check_finite(P, q);
+        }
+        P.Q[g] = q;
+    }
+}
+
 // ================================================================ broadphase helpers
 // ---------------------------------------------------------------- ordered float encoding
 __device__ __forceinline__ unsigned int ord_enc(float f)
@@ -335,6 +459,13 @@ __device__ __forceinline__ Grid make_grid(const Params &P, bool &ok)
     return G;
 }
 
+// Cells the grid spans (at most n, the table size); cells beyond stay empty.
+__device__ __forceinline__ int grid_cells(const Grid *g, int n)
+{
+    const long long t = (long long)g->dim[0] * g->dim[1] * g->dim[2];
+    return t < n ? (int)t : n;
+}
+
 __device__ __forceinline__ int cell_coord(float x, float lo, float inv_cell, int dim)
 {
     int i = (int)floorf((x - lo) * inv_cell);
@@ -389,64 +520,136 @@ __device__ __forceinline__ int bp_cell(const Grid &G, float4 sp)
     return ix + G.dim[0] * (iy + G.dim[1] * iz);
 }
 
-// Candidate pairs of pill a, by one warp: lanes 0..26 own the neighbouring
-// cells, a warp scan of their occupancies flattens the candidates, 32
-// candidates are tested per round, hits are compacted with a ballot and their
-// output slots reserved with one atomic per round.  start(c) is the first
-// entry of cell c in cell_pills (start(c + 1) its end).  s_start / s_off are
-// this warp's 32-entry shared-memory rows.
+// Bounding sphere of pill g into P.spheres, folded into this thread's running bounds.
+__device__ __forceinline__ void bound_pill(const Params &P, int g, float mn[3], float mx[3], float &mr)
+{
+    const float4 sp = bp_sphere(P, g);
+    P.spheres[g] = sp;
+    mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
+    mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
+    mr = fmaxf(mr, sp.w);
+}
+
+// Warp-wide min/max of the running bounds, merged into P.bounds by lane 0:
+// bounds[0..2] = enc(-min c), bounds[3..5] = enc(max c), bounds[6] = enc(max R),
+// all zero before the first merge.  Every lane of the warp must call it.
+__device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float mx[3], float mr)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+        mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    }
+    if ((threadIdx.x & 31) == 0 && mr > 0.f) {
+        for (int c = 0; c < 3; ++c) {
+            atomicMax(P.bounds + c, ord_enc(-mn[c]));
+            atomicMax(P.bounds + 3 + c, ord_enc(mx[c]));
+        }
+        atomicMax(P.bounds + 6, ord_enc(mr));
+    }
+}
+
+__device__ __forceinline__ void count_pill(const Params &P, const Grid &G, int g)
+{
+    const int cell = bp_cell(G, P.spheres[g]);
+    P.cell_of[g] = cell;
+    atomicAdd(P.cell_count + cell, 1);
+}
+
+// Places pill g in its cell (entries from `first`, the cell's start), with a
+// copy of its bounding sphere and group in cell order for the pair search,
+// and returns the cell's count towards zero, ready for the next substep.
+__device__ __forceinline__ void scatter_pill(const Params &P, int g, int cell, int first)
+{
+    const int pos = first + atomicSub(P.cell_count + cell, 1) - 1;
+    P.cell_pills[pos] = g;
+    P.cell_sph[pos] = P.spheres[g];
+    P.cell_grp[pos] = P.seg_group[g];
+}
+
+// Candidate pairs between one grid cell and one of its neighbours, by one
+// warp.  Every pair of pills whose cells are neighbours is visited exactly
+// once: from the lower cell of the 13 "forward" neighbour offsets (dz = 1;
+// dz = 0, dy = 1; dz = dy = 0, dx = 1), and inside one cell from the pill at
+// the lower position.  Work unit u = 14 c + k pairs cell c with its forward
+// neighbour k < 13, or with itself (k = 13), so that the work of a crowded
+// neighbourhood is spread over 14 warps.  The cell's pills sit one per lane
+// (32 at a time); the neighbour's pills are loaded 32 at a time from the
+// cell-order sphere / group copies (coalesced) and broadcast to all lanes,
+// so each step tests up to 32 pairs.  Hits are compacted with a ballot and
+// their output slots reserved with one atomic per step; pairs are written as
+// (lower id, higher id).  start(c) is the first entry of cell c in cell
+// order (start(c + 1) its end).
+constexpr int kEmitUnits = 14;
+
 template <class StartFn>
-__device__ __forceinline__ void emit_pill(const Params &P, const Grid &G, int a, int *s_start, int *s_off,
-                                          StartFn start)
+__device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u, StartFn start)
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const float4 sa = P.spheres[a];
-    const int ga = P.seg_group[a];
-    const int ca = P.cell_of[a];
-    const int ix = ca % G.dim[0], iy = (ca / G.dim[0]) % G.dim[1], iz = ca / (G.dim[0] * G.dim[1]);
-    int cnt = 0, st = 0;
-    if (lane < 27) {
-        const int x = ix + lane % 3 - 1, y = iy + (lane / 3) % 3 - 1, z = iz + lane / 9 - 1;
-        if (x >= 0 && x < G.dim[0] && y >= 0 && y < G.dim[1] && z >= 0 && z < G.dim[2]) {
-            const int c = x + G.dim[0] * (y + G.dim[1] * z);
-            st = start(c);
-            cnt = start(c + 1) - st;
+    const int c = u / kEmitUnits, k = u % kEmitUnits;
+    const int c0 = start(c), c1 = start(c + 1);
+    if (c0 >= c1) return;  // empty cell (uniform over the warp)
+    int d = c;
+    if (k < 13) {
+        int dx, dy, dz;
+        if (k < 9) {
+            dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
+        } else if (k < 12) {
+            dx = k - 10; dy = 1; dz = 0;
+        } else {
+            dx = 1; dy = 0; dz = 0;
         }
+        const int ix = c % G.dim[0], iy = (c / G.dim[0]) % G.dim[1], iz = c / (G.dim[0] * G.dim[1]);
+        const int x = ix + dx, y = iy + dy, z = iz + dz;
+        if (x < 0 || x >= G.dim[0] || y < 0 || y >= G.dim[1] || z >= G.dim[2]) return;
+        d = x + G.dim[0] * (y + G.dim[1] * z);
     }
-    const int inc = warp_incl_scan(cnt);
-    const int total = __shfl_sync(full, inc, 31);
-    s_start[lane] = st;
-    s_off[lane] = inc - cnt;
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-        const int i = base + lane;
-        bool hit = false;
-        int b = 0;
-        if (i < total) {
-            int lo = 0, hi = 26;  // last cell whose offset is <= i
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= i) lo = mid; else hi = mid - 1;
+    const int d0 = start(d), d1 = start(d + 1);
+    if (d0 >= d1) return;
+    for (int ob = c0; ob < c1; ob += 32) {
+        const int pa = ob + lane;
+        const bool own = pa < c1;
+        const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ga = own ? P.cell_grp[pa] : 0;
+        // inside the own cell only pairs with pb > pa: candidates from this chunk on
+        for (int cb = (k == 13 ? ob : d0); cb < d1; cb += 32) {
+            const int q = cb + lane;
+            float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+            int cg = 0;
+            if (q < d1) {
+                cs = P.cell_sph[q];
+                cg = P.cell_grp[q];
             }
-            b = P.cell_pills[s_start[lo] + (i - s_off[lo])];
-            hit = b > a && P.seg_group[b] != ga && spheres_overlap(sa, P.spheres[b]);
-        }
-        const unsigned m = __ballot_sync(full, hit);
-        if (m) {
-            int out = 0;
-            if (lane == 0) out = atomicAdd(P.npairs, __popc(m));
-            out = __shfl_sync(full, out, 0);
-            if (hit) {
-                const int idx = out + __popc(m & ((1u << lane) - 1u));
-                if (idx < P.max_pairs) {
-                    P.pairs[idx] = make_int2(a, b);
-                    if (P.lam_pair) P.lam_pair[idx] = 0.f;
+            const int m = min(32, d1 - cb);
+            for (int j = 0; j < m; ++j) {
+                float4 sj;
+                sj.x = __shfl_sync(full, cs.x, j);
+                sj.y = __shfl_sync(full, cs.y, j);
+                sj.z = __shfl_sync(full, cs.z, j);
+                sj.w = __shfl_sync(full, cs.w, j);
+                const int gj = __shfl_sync(full, cg, j);
+                const bool hit = own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
+                const unsigned hm = __ballot_sync(full, hit);
+                if (hm) {
+                    int out = 0;
+                    if (lane == 0) out = atomicAdd(P.npairs, __popc(hm));
+                    out = __shfl_sync(full, out, 0);
+                    if (hit) {
+                        const int idx = out + __popc(hm & ((1u << lane) - 1u));
+                        if (idx < P.max_pairs) {
+                            const int a = P.cell_pills[pa], b = P.cell_pills[cb + j];
+                            P.pairs[idx] = make_int2(min(a, b), max(a, b));
+                            if (P.lam_pair) P.lam_pair[idx] = 0.f;
+                        }
+                    }
                 }
             }
         }
     }
-    __syncwarp();
 }
 
 // ================================================================ contacts
@@ -518,6 +721,60 @@ __device__ __forceinline__ void contact_planes(const Params &P, int v, float at)
         *lp += dl;
         acc_add(P, v, (w * dl) * v3(pl.x, pl.y, pl.z), -m.y * rbar * dl);
     }
+}
+
+// ================================================================ skinning
+// LBS frame of segment g (Sec. 7.4): the 3x4 similarity T_j Tbar_j^-1 =
+// [s_m R_j Rbar_j^T | c_m - s_m R_j Rbar_j^T cbar_m] in world coordinates,
+// stored as three float4 rows at the caller's segment id sperm[g].
+__device__ __forceinline__ void lbs_frame_at(const Params &P, const float4 *__restrict__ LQ,
+                                             const float4 *__restrict__ LC, const int *__restrict__ sperm,
+                                             float4 *__restrict__ frames, int g)
+{
+    const int a = P.seg_v0[g];
+    const float4 xa = P.X[a], xb = P.X[a + 1];
+    const float sm = 0.5f * (xa.w + xb.w);
+    const float4 q = P.Q[g], qb = LQ[g];
+    const float4 r = qmul(q, qconj(qb));  // R_j Rbar_j^T
+    V3 c0 = qrot(r, v3(1.f, 0.f, 0.f)), c1 = qrot(r, v3(0.f, 1.f, 0.f)), c2 = qrot(r, v3(0.f, 0.f, 1.f));
+    c0 = sm * c0;
+    c1 = sm * c1;
+    c2 = sm * c2;
+    const float4 cb = LC[g];
+    const V3 cm = 0.5f * (xyz(xa) + xyz(xb)) + xyz(P.rod_origin[P.rod_of_v[a]]);
+    const V3 t = cm - (cb.x * c0 + cb.y * c1 + cb.z * c2);
+    float4 *f = frames + 3 * (size_t)sperm[g];
+    f[0] = make_float4(c0.x, c1.x, c2.x, t.x);
+    f[1] = make_float4(c0.y, c1.y, c2.y, t.y);
+    f[2] = make_float4(c0.z, c1.z, c2.z, t.z);
+}
+
+// Skinned position of mesh vertex i: sum_k w_k T_k Tbar_k^-1 rest_i over its
+// four frames.  Frame ids outside [0, ns) contribute nothing and raise the
+// error word.  Streaming loads / stores: the mesh is touched once per frame.
+__device__ __forceinline__ void lbs_vertex_at(int i, int ns, const float4 *__restrict__ rest,
+                                              const int4 *__restrict__ idx, const float4 *__restrict__ w,
+                                              const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
+{
+    const float4 p = __ldcs(rest + i);
+    const int4 id = __ldcs(idx + i);
+    const float4 ww = __ldcs(w + i);
+    const int ids[4] = {id.x, id.y, id.z, id.w};
+    const float wv[4] = {ww.x, ww.y, ww.z, ww.w};
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if ((unsigned)ids[k] >= (unsigned)ns) {
+            atomicOr(err, ERR_OVERFLOW);
+            continue;
+        }
+        const float4 *f = frames + 3 * (size_t)ids[k];
+        const float4 r0 = __ldg(f), r1 = __ldg(f + 1), r2 = __ldg(f + 2);
+        ox += wv[k] * (r0.x * p.x + r0.y * p.y + r0.z * p.z + r0.w);
+        oy += wv[k] * (r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w);
+        oz += wv[k] * (r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
+    }
+    __stcs(out + i, make_float4(ox, oy, oz, 0.f));
 }
 
 }  // namespace viper

@@ -32,19 +32,21 @@ __global__ void seg_tables_kernel(const int *__restrict__ rod_offsets, int n_rod
 
 // Byte layout of the broadphase scratch for ns pills and a grid table; every
 // section starts on a 256-byte boundary.  Returns the total size.
-size_t broadphase_scratch_layout(int ns, int table, size_t off[9])
+size_t broadphase_scratch_layout(int ns, int table, size_t off[kBpSections])
 {
-    const size_t sz[9] = {16 * (size_t)ns,           // spheres
-                          4 * (size_t)ns,            // cell_of
-                          4 * (size_t)ns,            // cell_pills
-                          4 * (size_t)ns,            // seg_v0
-                          4 * (size_t)ns,            // seg_group
-                          4 * (size_t)table,         // cell_count (zero between calls)
-                          4 * ((size_t)table + 1),   // cell_start
-                          4 * 4096,                  // scan tile sums
-                          sizeof(unsigned int) * 8 + sizeof(Grid) + 4 * sizeof(int)};  // bounds, grid, err
+    const size_t sz[kBpSections] = {16 * (size_t)ns,           // spheres
+                                    4 * (size_t)ns,            // cell_of
+                                    4 * (size_t)ns,            // cell_pills
+                                    4 * (size_t)ns,            // seg_v0
+                                    4 * (size_t)ns,            // seg_group
+                                    4 * (size_t)table,         // cell_count (zero between calls)
+                                    4 * ((size_t)table + 1),   // cell_start
+                                    4 * 4096,                  // scan tile sums
+                                    sizeof(unsigned int) * 8 + sizeof(Grid) + 4 * sizeof(int),  // bounds, grid, err
+                                    16 * (size_t)ns,           // spheres in cell order
+                                    4 * (size_t)ns};           // groups in cell order
     size_t o = 0;
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < kBpSections; ++k) {
         off[k] = o;
         o += (sz[k] + 255) & ~(size_t)255;
     }
@@ -60,7 +62,7 @@ int broadphase_table_size(int ns)
 }
 
 // Point the broadphase arguments at a scratch block laid out as above.
-void broadphase_params(Params &P, char *base, const size_t off[9], int n_rods, int nv, const float *x4,
+void broadphase_params(Params &P, char *base, const size_t off[kBpSections], int n_rods, int nv, const float *x4,
                        const float *rbar, int *pairs, int max_pairs, int *n_pairs, int table)
 {
     P = Params{};
@@ -80,6 +82,8 @@ void broadphase_params(Params &P, char *base, const size_t off[9], int n_rods, i
     P.bounds = reinterpret_cast<unsigned int *>(base + off[8]);
     P.grid = reinterpret_cast<Grid *>(base + off[8] + 32);
     P.err = reinterpret_cast<int *>(base + off[8] + 32 + sizeof(Grid));
+    P.cell_sph = reinterpret_cast<float4 *>(base + off[9]);
+    P.cell_grp = reinterpret_cast<int *>(base + off[10]);
     P.table = table;
     P.pairs = reinterpret_cast<int2 *>(pairs);
     P.max_pairs = max_pairs;
@@ -120,7 +124,7 @@ extern "C" int viper_broadphase(int n_rods, int n_verts, const int *rod_offsets,
     cudaStream_t st = (cudaStream_t)stream;
     const int ns = n_verts - n_rods;
     const int table = broadphase_table_size(ns);
-    size_t off[9];
+    size_t off[kBpSections];
     const size_t bytes = broadphase_scratch_layout(ns, table, off);
     void *base = nullptr;
     if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {

@@ -21,24 +21,10 @@ __global__ void predict_kernel(Params P, int v0, int v1, int s0, int s1, int con
 {
     const int nvr = v1 - v0, total = nvr + (s1 - s0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        if (i < nvr) {
-            int v = v0 + i;
-            float4 x = P.X[v];
-            P.Xp[v] = x;
-            x = predict_vertex(P, x, P.V[v], P.RV1[v], P.tau);
-            P.X[v] = x;
-            if (contact_path) P.Xpred[v] = to_world(P, v, x);
-            P.lamB[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-            P.lamB2[v] = 0.f;
-            for (int k = 0; k < P.n_planes; ++k) P.lam_plane[(size_t)v * P.n_planes + k] = 0.f;
-        } else {
-            int g = s0 + (i - nvr);
-            float4 q = P.Q[g];
-            P.Qp[g] = q;
-            P.Q[g] = predict_quat(P, q, P.W[g]);
-            P.lamS[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-            P.lamS2[g] = make_float2(0.f, 0.f);
-        }
+        if (i < nvr)
+            predict_vertex_at(P, v0 + i, P.tau, contact_path != 0, true);
+        else
+            predict_segment_at(P, s0 + (i - nvr), true);
     }
 }
 
@@ -46,22 +32,10 @@ __global__ void finish_kernel(Params P, int v0, int v1, int s0, int s1, int appl
 {
     const int nvr = v1 - v0, total = nvr + (s1 - s0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        if (i < nvr) {
-            int v = v0 + i;
-            float4 x = P.X[v];
-            if (apply) x = apply_pending(P, v, x);
-            float4 xp = P.Xp[v];
-            float4 vel = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
-                                     (x.w - xp.w) * P.inv_h);
-            check_finite(P, x);
-            P.X[v] = x;
-            P.V[v] = vel;
-        } else {
-            int g = s0 + (i - nvr);
-            float4 q = P.Q[g];
-            check_finite(P, q);
-            P.W[g] = omega_of(P, q, P.Qp[g]);
-        }
+        if (i < nvr)
+            finish_vertex_at(P, v0 + i, apply != 0);
+        else
+            finish_segment_at(P, s0 + (i - nvr));
     }
 }
 
@@ -118,70 +92,7 @@ template <bool FULL>
 __global__ void __launch_bounds__(256) rod_kernel(Params P, int n_iter, int first, int apply)
 {
     extern __shared__ float4 smem[];
-    const int4 item = P.items[blockIdx.x];
-    float4 *sX = smem;
-    float4 *sQ = smem + item.y;
-    float4 *sXp = sQ + item.w;
-    float4 *sQp = sXp + item.y;
-
-    // ---- stage the item's state (coalesced float4 loads), predict if FULL
-    for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
-        const int v = item.x + i;
-        float4 x = P.X[v];
-        if (FULL) {
-            sXp[i] = x;
-            x = predict_vertex(P, x, P.V[v], P.RV1[v], P.tau);
-        } else if (apply) {
-            x = apply_pending(P, v, x);
-        }
-        sX[i] = x;
-    }
-    for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
-        const int g = item.z + j;
-        float4 q = P.Q[g];
-        if (FULL) {
-            sQp[j] = q;
-            q = predict_quat(P, q, P.W[g]);
-        }
-        sQ[j] = q;
-    }
-
-    // ---- this thread's constraints: segments 2p, 2p+1 and vertices 2p+1, 2p+2 of one rod
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    SlotRest R;
-    load_slot(P, item, P.slots[slot], R);
-    SlotLam L;
-    if (FULL || first)
-        zero_lam(L);
-    else
-        lam_load(P, slot, L);
-    __syncthreads();
-    const bool vol = P.volume != 0;
-#pragma unroll 1
-    for (int k = 0; k < n_iter; ++k) sweep(sX, sQ, R, L, P.inv_h2, vol);
-    if (!FULL && R.active) lam_store(P, slot, L);
-
-    // ---- write back (coalesced float4 stores); FULL also updates velocities
-    for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
-        const int v = item.x + i;
-        float4 x = sX[i];
-        if (FULL) {
-            float4 xp = sXp[i];
-            P.V[v] = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
-                                 (x.w - xp.w) * P.inv_h);
-            check_finite(P, x);
-        }
-        P.X[v] = x;
-    }
-    for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
-        const int g = item.z + j;
-        float4 q = sQ[j];
-        if (FULL) {
-            P.W[g] = omega_of(P, q, sQp[j]);
-            check_finite(P, q);
-        }
-        P.Q[g] = q;
-    }
+    rod_item<FULL>(P, blockIdx.x, n_iter, first != 0, apply != 0, P.tau, smem);
 }
 
 // ------------------------------------------------------------------ launchers

@@ -72,10 +72,15 @@ struct Params {
     float4 *spheres;
     unsigned int *bounds;
     int *cell_of, *cell_count, *cell_start, *cell_pills;
+    float4 *cell_sph;  // bounding spheres in cell order
+    int *cell_grp;     // collision groups in cell order
     int table;
     Grid *grid;
     int *err;
 };
+
+// Sections of the scene-free broadphase scratch (query.cu).
+constexpr int kBpSections = 11;
 
 struct Alloc {
     void *(*alloc)(size_t, void *) = nullptr;
@@ -135,8 +140,9 @@ struct viper_scene {
     std::vector<float2> u_RS1;
     std::vector<int> u_group;  // per caller rod
     std::vector<float4> u_origin;  // per caller rod: FP32 rest centroid
-    // pinned host mirror of the device error word (read without a stream sync)
+    // pinned, mapped host mirror of the device error word (read without a stream sync)
     int *h_err = nullptr;
+    int *d_herr = nullptr;  // its device address
     // scratch for host-pointer skinning
     float4 *skin_buf = nullptr;
     size_t skin_cap = 0;
@@ -182,6 +188,10 @@ void launch_state_out(viper_scene *s, int which, float4 *dst);
 void launch_state_in(viper_scene *s, int which, const float4 *src);
 void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);
 int configure_rod_kernels(int smem_bytes);
+// scene helpers shared with the multi-scene step (capi.cu)
+int scene_poll_latched(viper_scene *s);  // latched error of earlier frames as a VIPER_* code
+bool scene_contact_path(const viper_scene *s);
+int scene_decode_err(int e);
 int frame_configure(viper_scene *s);
 void launch_frame(viper_scene *s, int substeps, int iterations);
 

@@ -55,6 +55,13 @@ class ServerStats(C.Structure):
                 ("scenes", C.c_int), ("inflight", C.c_int), ("queued", C.c_int), ("used_bytes", C.c_size_t)]
 
 
+class BatchItem(C.Structure):
+    """Mirror of viper_batch_item."""
+    _fields_ = [("scene", C.c_void_p), ("bone_quat", C.c_void_p), ("bone_trans", C.c_void_p),
+                ("n_mesh", C.c_int), ("rest4", C.c_void_p), ("idx4", C.c_void_p), ("w4", C.c_void_p),
+                ("out4", C.c_void_p)]
+
+
 _lib = None
 _ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -109,6 +116,14 @@ def lib():
         L.viper_server_mesh_out.argtypes = [vp, C.c_int, vp]
         L.viper_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
         L.viper_server_reset_stats.argtypes = [vp]
+        L.viper_batch_create.argtypes = [vp, C.POINTER(vp)]
+        L.viper_batch_destroy.argtypes = [vp]
+        L.viper_batch_destroy.restype = None
+        L.viper_batch_step.argtypes = [vp, C.POINTER(BatchItem), C.c_int, C.c_float, C.c_int, C.c_int, _ip]
+        L.viper_batch_stream.argtypes = [vp]
+        L.viper_batch_stream.restype = vp
+        L.viper_batch_launch_count.argtypes = [vp]
+        L.viper_batch_launch_count.restype = C.c_longlong
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
         L.viper_error_string.argtypes = [C.c_int]
@@ -398,6 +413,78 @@ def broadphase(rod_offsets, group, x4, rbar, max_pairs, stream=None):
     got = pairs[: min(total, int(max_pairs))].cpu().numpy()
     order = np.lexsort((got[:, 1], got[:, 0])) if got.size else np.zeros(0, np.int64)
     return got[order], total
+
+
+class Batch:
+    """A multi-scene step context (viper_batch): one launch sequence per frame for many scenes."""
+
+    def __init__(self, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        _check(lib().viper_batch_create(C.c_void_p(self.stream.cuda_stream), C.byref(h)), "viper_batch_create")
+        self._h = h
+        _live.add(self)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().viper_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, scenes, poses=None, meshes=None, dt=1.0 / 60, substeps=10, iterations=4, check=True):
+        """One frame of every scene.  poses[i] = (quat [nb,4], trans [nb,3]) host arrays or None;
+        meshes[i] = Mesh or None.  Returns the per-scene latched status codes."""
+        n = len(scenes)
+        items = (BatchItem * max(n, 1))()
+        keep = []
+        for i, sc in enumerate(scenes):
+            it = items[i]
+            it.scene = sc.handle.value
+            pose = poses[i] if poses is not None else None
+            if pose is not None:
+                q = np.ascontiguousarray(pose[0], np.float32)
+                t = np.ascontiguousarray(pose[1], np.float32)
+                keep += [q, t]
+                it.bone_quat, it.bone_trans = q.ctypes.data, t.ctypes.data
+            m = meshes[i] if meshes is not None else None
+            if m is not None:
+                it.n_mesh = m.n
+                it.rest4, it.idx4 = m.rest.data_ptr(), m.idx.data_ptr()
+                it.w4, it.out4 = m.w.data_ptr(), m.out.data_ptr()
+        status = (C.c_int * max(n, 1))()
+        rc = lib().viper_batch_step(self._h, items, n, float(dt), int(substeps), int(iterations), status)
+        if check:
+            _check(rc, "viper_batch_step")
+        return [status[i] for i in range(n)]
+
+    def frame(self, scenes, meshes=None):
+        """One frame of each scene's own schedule (dt, substeps, iterations must agree), bones at the frame end."""
+        sc0 = scenes[0].scene
+        poses = []
+        for s in scenes:
+            sc = s.scene
+            if (sc.dt, sc.substeps, sc.iterations) != (sc0.dt, sc0.substeps, sc0.iterations):
+                raise ValueError("scenes of one batched frame share dt, substeps and iterations")
+            poses.append(sc.bone_pose(s.t + sc.dt) if sc.bones is not None else None)
+        st = self.step(scenes, poses, meshes, sc0.dt, sc0.substeps, sc0.iterations)
+        for s in scenes:
+            s.t += sc0.dt
+        return st
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def launch_count(self) -> int:
+        return int(lib().viper_batch_launch_count(self._h))
 
 
 def _ptr_f32(a):
