@@ -30,10 +30,6 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# Serving runs one stream per scene; give the driver more hardware work queues
-# than the default 8 so that frames of different scenes overlap (read once, at
-# context creation; a process setting, not a GPU setting).
-os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOAD_DESC = ("muscle_rig: 200 tapered rods of 8-64 vertices pinned to 20 animated bones, "
                  "pill-pill contacts, volume on, dt=1/60 s, 10 substeps x 4 iterations, "
@@ -265,6 +261,73 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
     return out
 
 
+def bench_multi_scene(V, torch, flush, dist, frames, n_scenes=64, rank=0):
+    """n serving-size muscle rigs advanced together by the multi-scene step, against
+    the same scenes stepped one after another (graph-replayed, per scene)."""
+    from paper_1906_05260_gb300 import serving as SV
+    temps = SV.scene_templates(seed=4 + rank)
+    objs = [V.Scene(temps[k % len(temps)]) for k in range(n_scenes)]
+    meshes = [V.Mesh(o.scene.mesh) for o in objs]
+    sc0 = objs[0].scene
+    nv = sum(o.nv for o in objs)
+    nm = sum(m.n for m in meshes)
+    units = reduce_sum(dist, nv * sc0.substeps)
+    Bt = V.Batch()
+    st = Bt.stream
+    poses = [[o.scene.bone_pose((f + 1) * sc0.dt) for o in objs] for f in range(frames + 3)]
+    for f in range(3):
+        Bt.step(objs, poses[f], meshes, sc0.dt, sc0.substeps, sc0.iterations)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    l0 = Bt.launch_count()
+    for i in range(frames):
+        with torch.cuda.stream(st):
+            flush.fill_(i & 0xFF)
+            e0.record(st)
+            Bt.step(objs, poses[3 + i], meshes, sc0.dt, sc0.substeps, sc0.iterations)
+            e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    launches = (Bt.launch_count() - l0) / frames
+    ms = reduce_max(dist, sum(ts) / len(ts))
+    out = {"workload": f"{n_scenes} muscle rigs of 50-500 rods (templates of the serving mix), "
+                       f"{nv} rod vertices and {nm} mesh vertices in all, 10 substeps x 4 iterations + LBS",
+           "batched": {"value": units / (ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": ms,
+                       "skinned_vertices_per_s": reduce_sum(dist, nm) / (ms * 1e-3),
+                       "launches_per_frame": launches,
+                       "solver": "multi-scene step: one launch sequence for all scenes"}}
+    # the same scenes, one graph-replayed frame each, serially on one stream
+    for o in objs:
+        o.close()
+    one = torch.cuda.Stream()
+    objs = [V.Scene(temps[k % len(temps)], stream=one) for k in range(n_scenes)]
+    for f in range(2):
+        for o, m in zip(objs, meshes):
+            o.frame()
+            o.skin(m)
+    torch.cuda.synchronize()
+    tp = []
+    for i in range(max(3, frames // 4)):
+        with torch.cuda.stream(one):
+            flush.fill_(i & 0xFF)
+            e0.record(one)
+            for o, m in zip(objs, meshes):
+                o.frame()
+                o.skin(m)
+            e1.record(one)
+        e1.synchronize()
+        tp.append(e0.elapsed_time(e1))
+    pm = reduce_max(dist, sum(tp) / len(tp))
+    out["per_scene_graphs"] = {"value": units / (pm * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": pm,
+                               "solver": "each scene's frame graph replayed in turn on one stream"}
+    out["batched_over_per_scene"] = out["batched"]["value"] / out["per_scene_graphs"]["value"]
+    for o in objs:
+        o.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +337,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--serving", type=float, default=10.0,
                     help="seconds of the real-time serving load (0 disables)")
     args = ap.parse_args()
@@ -490,6 +554,12 @@ def main():
     if not args.no_batching:
         batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
 
+    # ---- many scenes at once: the multi-scene step against per-scene graphs
+    multi = None
+    if not args.no_multi:
+        g.close()
+        multi = bench_multi_scene(V, torch, flush, dist, max(10, K // 2), rank=rank)
+
     # ---- serving: Poisson stream of muscle-rig scenes, 60 Hz frame requests each
     serving = None
     if args.serving > 0:
@@ -532,6 +602,7 @@ def main():
         "plain": plain,
         "graph_batched": graph,
         "batching": batching,
+        "multi_scene": multi,
         "serving": serving,
     }
     if rank == 0:

@@ -280,8 +280,9 @@ long long viper_launch_count(const viper_scene *scene);
  * contacts, Sec. 7.4 skinning -- to many scenes at once.)
  *
  * Every kernel of the frame covers all scenes of the call: its grid is the
- * concatenation of the scenes' grids, so a frame of S substeps and I
- * iterations costs S (7 + 2 I) + 2 launches however many scenes it carries.
+ * concatenation of the scenes' grids, so a frame of S substeps and I >= 1
+ * iterations costs S (2 I + 2) + 3 launches (contacts, skinning) however
+ * many scenes it carries.
  * Scenes with contacts or half-planes whose rods all fit the shared-memory
  * kernel (every scene whose rods are at most resident_max long) run the
  * contact-path sequence; such scenes without contacts run one launch per
@@ -340,12 +341,15 @@ long long viper_batch_launch_count(const viper_batch *batch);
  *
  * A server keeps every admitted scene resident on the device and admits new
  * scenes only while the sum of their footprints stays within budget_bytes.
- * A dispatcher thread keeps up to max_inflight frames on the GPU: whenever a
- * slot frees up it starts the oldest waiting request of every scene without a
- * frame in flight, each on the scene's own stream, so frames of different
- * scenes overlap on the device (continuous batching at frame granularity).
- * Frames of one scene run in submission order.  Per-scene results do not
- * depend on what else runs (no shared state; deterministic kernels).
+ * A dispatcher thread steps scenes with the multi-scene frame step: whenever
+ * fewer than two steps are in flight and requests wait, it takes the oldest
+ * waiting request of every scene without a frame in flight (those sharing
+ * the oldest request's dt, substeps and iterations; at most max_inflight
+ * frames in flight in all) and advances them all with one launch sequence on
+ * the server's stream, skinning included.  Requests that arrive meanwhile
+ * join the next step (continuous batching at frame granularity).  Frames of
+ * one scene run in submission order, and a scene's results do not depend on
+ * what else runs with it (no shared state; deterministic kernels).
  * ------------------------------------------------------------------------ */
 typedef struct viper_server viper_server;
 
@@ -356,17 +360,20 @@ typedef struct viper_server_stats {
     double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> completion latency    */
     int scenes, inflight, queued;
     size_t used_bytes;           /* admitted footprint                          */
+    long long steps;             /* multi-scene steps launched (frames / steps = mean batch) */
 } viper_server_stats;
 
 int viper_server_create(size_t budget_bytes, int max_inflight, viper_server **out);
 /* Drops queued requests, waits for frames in flight, releases every scene. */
 void viper_server_destroy(viper_server *server);
 /*
- * Admit a scene (desc as for viper_scene_create; desc->stream is ignored) with
- * an optional skinning mesh (host or device rest4/idx4/w4 [4 n_mesh], copied).
- * (dt, substeps, iterations) is the frame schedule the scene will be stepped
- * with: its graph is built here so that its first frame starts at once.
- * VIPER_EBUDGET if its footprint does not fit the remaining budget now.
+ * Admit a scene (desc as for viper_scene_create; desc->stream is ignored: the
+ * scene lives on the server's stream) with an optional skinning mesh (host or
+ * device rest4/idx4/w4 [4 n_mesh], copied).  solver_mode and (dt, substeps,
+ * iterations) apply to a scene the multi-scene kernels cannot take (rods
+ * longer than its shared-memory limit), which is stepped on its own with
+ * that solver (its graph built here for that schedule).  VIPER_EBUDGET if its
+ * footprint does not fit the remaining budget now.
  */
 int viper_server_admit(viper_server *server, const viper_scene_desc *desc, int n_mesh, const float *rest4,
                        const int *idx4, const float *w4, int solver_mode, float dt, int substeps,

@@ -8,11 +8,14 @@
 // per-element work is the one-scene kernels' device code (phases.cuh), so a
 // scene computes the same thing alone and in a batch.
 //
-// Per substep, contact path (pills and/or half-planes):
-//   predict | bounds | count | scan | scatter | emit | {rod sweep | contact} x I | finish
-// without contacts: one full shared-memory rod launch.  After the substeps
-// one launch builds the skinning frames, hands the bone pose on and mirrors
-// the error word to the host; one more skins every mesh.
+// Per substep, contact path (pills and/or half-planes), I >= 1 iterations:
+//   [velocity update of the previous substep + prediction + sweep 0] |
+//   grid (one CTA per scene: bounds, counts, scan, scatter) | pair search |
+//   contact | {sweep | contact} x (I - 1)
+// and one velocity update after the last substep: S (2 I + 2) + 1 launches.
+// Without contacts: one full shared-memory rod launch per substep.  After the
+// substeps one launch builds the skinning frames, hands the bone pose on and
+// mirrors the error word to the host; one more skins every mesh.
 //
 // The per-call table (scene parameters, block offsets, bone poses) is written
 // into pinned staging and uploaded with one copy; two staging buffers let the
@@ -183,7 +186,96 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
     for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
-        emit_cell(P, G, u, start);
+        emit_cell<4>(P, G, u, start);
+}
+
+// One scene's broadphase grid by one CTA: bounding spheres and their bounds,
+// the grid, cell counts (in shared memory when the grid spans at most
+// kGridSmemCells cells, else in cell_count), the exclusive cell scan into
+// cell_start, and the scatter into cell order with the sphere / group copies.
+constexpr int kGridThreads = 1024, kGridSmemCells = 12288, kGridMaxPills = 1 << 16;
+
+__global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    __shared__ unsigned int s_bounds[8];
+    __shared__ int ws[33];
+    extern __shared__ int s_cells[];
+    int local, nblk;
+    batch_enter(A, K_SCAN, sb, local, nblk);
+    const Params &P = sb.P;
+    const int t = threadIdx.x, bd = blockDim.x, ns = P.ns;
+    if (t < 8) s_bounds[t] = 0u;
+    __syncthreads();
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
+    for (int g = t; g < ns; g += bd) bound_pill(P, g, mn, mx, mr);
+    merge_bounds_to(s_bounds, mn, mx, mr);
+    __syncthreads();
+    bool ok;
+    const Grid G = make_grid_from(s_bounds, P.table, ok);
+    const int cells = (int)min((long long)G.dim[0] * G.dim[1] * G.dim[2], (long long)P.table);
+    const bool in_smem = cells <= kGridSmemCells;
+    int *cnt = in_smem ? s_cells : P.cell_count;  // cell_count is zero between substeps
+    if (in_smem)
+        for (int c = t; c < cells; c += bd) s_cells[c] = 0;
+    if (t == 0) {
+        *P.grid = G;
+        *P.npairs = 0;
+        if (!ok) atomicOr(P.err, ERR_NONFINITE);
+    }
+    __syncthreads();
+    for (int g = t; g < ns; g += bd) {
+        const int cell = bp_cell(G, P.spheres[g]);
+        P.cell_of[g] = cell;
+        atomicAdd(cnt + cell, 1);
+    }
+    __syncthreads();
+    // exclusive scan into cell_start, and into cnt as the running fill position of each cell
+    int carry = 0;
+    for (int base = 0; base < cells; base += bd * kScanPerB) {
+        const int b0 = base + t * kScanPerB;
+        int v[kScanPerB], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPerB; ++k) {
+            // counts in shared memory, or in global memory written by atomics (read from L2)
+            v[k] = (b0 + k < cells) ? (in_smem ? s_cells[b0 + k] : __ldcg(P.cell_count + b0 + k)) : 0;
+            sum += v[k];
+        }
+        int tot;
+        int off = block_excl_scan(sum, ws, &tot) + carry;
+#pragma unroll
+        for (int k = 0; k < kScanPerB; ++k) {
+            if (b0 + k < cells) {
+                P.cell_start[b0 + k] = off;
+                cnt[b0 + k] = off;
+            }
+            off += v[k];
+        }
+        carry += tot;
+    }
+    if (t == 0) P.cell_start[cells] = carry;
+    __syncthreads();
+    for (int g = t; g < ns; g += bd) {
+        const int pos = atomicAdd(cnt + P.cell_of[g], 1);
+        P.cell_pills[pos] = g;
+        P.cell_sph[pos] = P.spheres[g];
+        P.cell_grp[pos] = P.seg_group[g];
+    }
+    if (!in_smem) {  // return cell_count to zero for the next substep
+        __syncthreads();
+        for (int c = t; c < cells; c += bd) P.cell_count[c] = 0;
+    }
+}
+
+// First sweep of a substep with the previous substep's velocity update and
+// this substep's prediction folded in (see rod_item_first).
+__global__ void __launch_bounds__(256) batch_rod_first_kernel(BatchArgs A, int finish_prev, float tau)
+{
+    __shared__ BatchScene sb;
+    extern __shared__ float4 smem[];
+    int local, nblk;
+    batch_enter(A, K_ROD, sb, local, nblk);
+    rod_item_first(sb.P, local, finish_prev != 0, tau, sb.pills != 0, smem);
 }
 
 // One colour sweep of every work item (contact path): FULL = false, or the
@@ -275,7 +367,7 @@ __global__ void __launch_bounds__(kElemThreads) batch_skin_kernel(BatchArgs A)
 // ---------------------------------------------------------------- host side
 namespace {
 
-constexpr int kEmitPillsPerWarp = 8;
+constexpr int kEmitPillsPerWarp = 4;
 constexpr int kMeshPerThread = 4;
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -357,6 +449,7 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     const double h = (double)dt / substeps;
     size_t bcur = 0;
     int smem = 16, threads = 0;
+    bool fused_grid = true;  // every scene's broadphase fits one CTA
     for (int k = 0; k <= n; ++k)
         for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k] = 0;
     for (int k = 0; k < n; ++k) {
@@ -403,6 +496,7 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
         cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
         for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k + 1] = off[c * (n + 1) + k] + cnt[c];
         smem = std::max(smem, cp ? s->smem_iter : s->smem_full);
+        if (ns > kGridMaxPills) fused_grid = false;
         threads = s->block_threads;
     }
     int tot[K_KINDS];
@@ -414,8 +508,43 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     const void *rod_fn = cp ? reinterpret_cast<const void *>(batch_rod_kernel<false>)
                             : reinterpret_cast<const void *>(batch_rod_kernel<true>);
     if (raise_smem_limit(rod_fn, smem) != 0) return VIPER_EINVAL;
+    if (cp && raise_smem_limit(reinterpret_cast<const void *>(batch_rod_first_kernel), smem) != 0) return VIPER_EINVAL;
+    const int grid_smem = sizeof(int) * kGridSmemCells;
+    if (fused_grid && raise_smem_limit(reinterpret_cast<const void *>(batch_grid_kernel), grid_smem) != 0)
+        return VIPER_EINVAL;
     long long L = 0;
-    for (int k = 0; k < substeps; ++k) {
+    if (cp && iterations > 0) {
+        // per substep: [finish + predict + sweep 0] | grid | emit | contact | {sweep | contact} x (I - 1)
+        for (int k = 0; k < substeps; ++k) {
+            const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
+            batch_rod_first_kernel<<<tot[K_ROD], threads, smem, st>>>(A, k > 0 ? 1 : 0, tau);
+            ++L;
+            if (tot[K_PILL] > 0) {
+                if (fused_grid) {
+                    batch_grid_kernel<<<tot[K_SCAN], kGridThreads, grid_smem, st>>>(A);
+                    ++L;
+                } else {
+                    batch_bounds_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+                    batch_count_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+                    batch_scan_kernel<<<tot[K_SCAN], kScanThreadsB, 0, st>>>(A);
+                    batch_scatter_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
+                    L += 4;
+                }
+                batch_emit_kernel<<<tot[K_EMIT], 32 * kEmitWarpsB, 0, st>>>(A);
+                ++L;
+            }
+            batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
+            ++L;
+            for (int i = 1; i < iterations; ++i) {
+                batch_rod_kernel<false><<<tot[K_ROD], threads, smem, st>>>(A, 1, 0, 1, tau);
+                batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
+                L += 2;
+            }
+        }
+        batch_finish_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, 1);
+        ++L;
+    }
+    for (int k = 0; k < substeps && !(cp && iterations > 0); ++k) {
         const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
         if (!cp) {
             batch_rod_kernel<true><<<tot[K_ROD], threads, smem, st>>>(A, iterations, 1, 0, tau);

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) bp_emit_kernel(Params P)
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
     for (int u = blockIdx.x * kEmitWarps + wib; u < kEmitUnits * cells; u += nwarps)
-        emit_cell(P, G, u, start);
+        emit_cell<4>(P, G, u, start);
 }
 
 // ---------------------------------------------------------------- exclusive scan

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
                 const int cells = (int)min((long long)G.dim[0] * G.dim[1] * G.dim[2], (long long)P.table);
                 const FrameStart fs{cs, toff, table, T, ntiles};
                 for (int u = gwarp; u < kEmitUnits * cells; u += gwarps)
-                    emit_cell(P, G, u, fs);
+                    emit_cell<1>(P, G, u, fs);
             }
             if (!grid_barrier(P.bar, nb, P.err)) return;
         } else if (BARRIERS && iters > 0) {

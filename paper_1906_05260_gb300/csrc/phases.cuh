@@ -399,6 +399,63 @@ __device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, boo
     }
 }
 
+// First sweep of a substep on the contact path, for one work item: the
+// previous substep's velocity update (after its last contact pass) when
+// finish_prev, the prediction (Sec. 6) -- the start state kept in Xp / Qp,
+// the predicted world positions in Xpred when `world`, the half-plane
+// multipliers cleared -- then one colour sweep with fresh multipliers.
+// The same per-element arithmetic as finish_*_at, predict_*_at and rod_item.
+__device__ __forceinline__ void rod_item_first(const Params &P, int b, bool finish_prev, float tau, bool world,
+                                               float4 *smem)
+{
+    const int4 item = P.items[b];
+    float4 *sX = smem;
+    float4 *sQ = smem + item.y;
+    for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
+        const int v = item.x + i;
+        float4 x = P.X[v], vel;
+        if (finish_prev) {
+            x = apply_pending(P, v, x);
+            const float4 xp = P.Xp[v];
+            vel = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
+                              (x.w - xp.w) * P.inv_h);
+            check_finite(P, x);
+            P.V[v] = vel;
+        } else {
+            vel = P.V[v];
+        }
+        P.Xp[v] = x;
+        x = predict_vertex(P, x, vel, P.RV1[v], tau);
+        if (world) P.Xpred[v] = to_world(P, v, x);
+        for (int k = 0; k < P.n_planes; ++k) P.lam_plane[(size_t)v * P.n_planes + k] = 0.f;
+        sX[i] = x;
+    }
+    for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
+        const int g = item.z + j;
+        const float4 q = P.Q[g];
+        float4 w;
+        if (finish_prev) {
+            check_finite(P, q);
+            w = omega_of(P, q, P.Qp[g]);
+            P.W[g] = w;
+        } else {
+            w = P.W[g];
+        }
+        P.Qp[g] = q;
+        sQ[j] = predict_quat(P, q, w);
+    }
+    const int slot = b * blockDim.x + threadIdx.x;
+    SlotRest R;
+    load_slot(P, item, P.slots[slot], R);
+    SlotLam L;
+    zero_lam(L);
+    __syncthreads();
+    sweep(sX, sQ, R, L, P.inv_h2, P.volume != 0);
+    if (R.active) lam_store(P, slot, L);
+    for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
+    for (int j = threadIdx.x; j < item.w; j += blockDim.x) P.Q[item.z + j] = sQ[j];
+}
+
 // ================================================================ broadphase helpers
 // ---------------------------------------------------------------- ordered float encoding
 __device__ __forceinline__ unsigned int ord_enc(float f)
@@ -414,17 +471,17 @@ __device__ __forceinline__ float ord_dec(unsigned int u)
 // Grid from the bounds: cell = 2 R_max (1 + 2^-8); grown until the dense grid
 // fits the table and spans at most 4096 cells per axis.  Non-finite bounds
 // (a diverged state) give an empty grid and raise the non-finite flag.
-__device__ __forceinline__ Grid make_grid(const Params &P, bool &ok)
+__device__ __forceinline__ Grid make_grid_from(const unsigned int *bounds, int table, bool &ok)
 {
     Grid G;
     float lo[3], hi[3];
     ok = true;
     for (int c = 0; c < 3; ++c) {
-        lo[c] = -ord_dec(P.bounds[c]);
-        hi[c] = ord_dec(P.bounds[3 + c]);
+        lo[c] = -ord_dec(bounds[c]);
+        hi[c] = ord_dec(bounds[3 + c]);
         ok = ok && isfinite(lo[c]) && isfinite(hi[c]) && hi[c] >= lo[c];
     }
-    float cell = 2.f * ord_dec(P.bounds[6]) * 1.00390625f;
+    float cell = 2.f * ord_dec(bounds[6]) * 1.00390625f;
     ok = ok && isfinite(cell);
     if (!ok) {
         for (int c = 0; c < 3; ++c) {
@@ -448,7 +505,7 @@ __device__ __forceinline__ Grid make_grid(const Params &P, bool &ok)
             tot *= dim[c];
         }
         G.inv_cell = inv;
-        if (tot <= (long long)P.table) break;
+        if (tot <= (long long)table) break;
         cell *= 1.26f;
     }
     for (int c = 0; c < 3; ++c) {
@@ -458,6 +515,8 @@ __device__ __forceinline__ Grid make_grid(const Params &P, bool &ok)
     G.pad = 0;
     return G;
 }
+
+__device__ __forceinline__ Grid make_grid(const Params &P, bool &ok) { return make_grid_from(P.bounds, P.table, ok); }
 
 // Cells the grid spans (at most n, the table size); cells beyond stay empty.
 __device__ __forceinline__ int grid_cells(const Grid *g, int n)
@@ -530,10 +589,10 @@ __device__ __forceinline__ void bound_pill(const Params &P, int g, float mn[3], 
     mr = fmaxf(mr, sp.w);
 }
 
-// Warp-wide min/max of the running bounds, merged into P.bounds by lane 0:
+// Warp-wide min/max of the running bounds, merged into `bounds` by lane 0:
 // bounds[0..2] = enc(-min c), bounds[3..5] = enc(max c), bounds[6] = enc(max R),
 // all zero before the first merge.  Every lane of the warp must call it.
-__device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float mx[3], float mr)
+__device__ __forceinline__ void merge_bounds_to(unsigned int *bounds, float mn[3], float mx[3], float mr)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -545,11 +604,16 @@ __device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float
     }
     if ((threadIdx.x & 31) == 0 && mr > 0.f) {
         for (int c = 0; c < 3; ++c) {
-            atomicMax(P.bounds + c, ord_enc(-mn[c]));
-            atomicMax(P.bounds + 3 + c, ord_enc(mx[c]));
+            atomicMax(bounds + c, ord_enc(-mn[c]));
+            atomicMax(bounds + 3 + c, ord_enc(mx[c]));
         }
-        atomicMax(P.bounds + 6, ord_enc(mr));
+        atomicMax(bounds + 6, ord_enc(mr));
     }
+}
+
+__device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float mx[3], float mr)
+{
+    merge_bounds_to(P.bounds, mn, mx, mr);
 }
 
 __device__ __forceinline__ void count_pill(const Params &P, const Grid &G, int g)
@@ -585,7 +649,7 @@ __device__ __forceinline__ void scatter_pill(const Params &P, int g, int cell, i
 // order (start(c + 1) its end).
 constexpr int kEmitUnits = 14;
 
-template <class StartFn>
+template <int STEP, class StartFn>
 __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u, StartFn start)
 {
     const int lane = threadIdx.x & 31;
@@ -625,25 +689,34 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
                 cg = P.cell_grp[q];
             }
             const int m = min(32, d1 - cb);
-            for (int j = 0; j < m; ++j) {
-                float4 sj;
-                sj.x = __shfl_sync(full, cs.x, j);
-                sj.y = __shfl_sync(full, cs.y, j);
-                sj.z = __shfl_sync(full, cs.z, j);
-                sj.w = __shfl_sync(full, cs.w, j);
-                const int gj = __shfl_sync(full, cg, j);
-                const bool hit = own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
-                const unsigned hm = __ballot_sync(full, hit);
-                if (hm) {
-                    int out = 0;
-                    if (lane == 0) out = atomicAdd(P.npairs, __popc(hm));
-                    out = __shfl_sync(full, out, 0);
-                    if (hit) {
-                        const int idx = out + __popc(hm & ((1u << lane) - 1u));
-                        if (idx < P.max_pairs) {
-                            const int a = P.cell_pills[pa], b = P.cell_pills[cb + j];
-                            P.pairs[idx] = make_int2(min(a, b), max(a, b));
-                            if (P.lam_pair) P.lam_pair[idx] = 0.f;
+            // STEP candidates per step: their broadcasts and tests are independent
+            for (int j0 = 0; j0 < m; j0 += STEP) {
+                bool hit[STEP];
+#pragma unroll
+                for (int t = 0; t < STEP; ++t) {
+                    const int j = j0 + t;  // past m: no candidate (j & 31 is still a valid source lane)
+                    float4 sj;
+                    sj.x = __shfl_sync(full, cs.x, j & 31);
+                    sj.y = __shfl_sync(full, cs.y, j & 31);
+                    sj.z = __shfl_sync(full, cs.z, j & 31);
+                    sj.w = __shfl_sync(full, cs.w, j & 31);
+                    const int gj = __shfl_sync(full, cg, j & 31);
+                    hit[t] = j < m && own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
+                }
+#pragma unroll
+                for (int t = 0; t < STEP; ++t) {
+                    const unsigned hm = __ballot_sync(full, hit[t]);
+                    if (hm) {
+                        int out = 0;
+                        if (lane == 0) out = atomicAdd(P.npairs, __popc(hm));
+                        out = __shfl_sync(full, out, 0);
+                        if (hit[t]) {
+                            const int idx = out + __popc(hm & ((1u << lane) - 1u));
+                            if (idx < P.max_pairs) {
+                                const int a = P.cell_pills[pa], b = P.cell_pills[cb + j0 + t];
+                                P.pairs[idx] = make_int2(min(a, b), max(a, b));
+                                if (P.lam_pair) P.lam_pair[idx] = 0.f;
+                            }
                         }
                     }
                 }

@@ -2,13 +2,14 @@
 //
 // A server owns device-resident scenes admitted against a device-memory budget.
 // Clients submit frame-step requests (bone poses + dt/substeps/iterations)
-// for any scene at any time.  A dispatcher thread keeps up to max_inflight
-// frames on the GPU at once: whenever a slot frees up it starts the oldest
-// waiting request of every scene that has no frame in flight, each on its
-// scene's own stream, so frames of different scenes overlap on the device and
-// requests that arrive while others run join as soon as a slot is free
-// (continuous batching at frame granularity).  Completion is stamped by a host
-// callback enqueued behind the frame; latency is completion minus submission.
+// for any scene at any time.  A dispatcher thread runs the multi-scene frame
+// step (batch.cu): whenever fewer than two steps are in flight it takes the
+// oldest waiting request of every scene without a frame in flight (those
+// with the oldest request's schedule) and advances all of them with one
+// launch sequence on the server's stream; requests that arrive meanwhile
+// join the next step (continuous batching at frame granularity).  Completion
+// is stamped by a host callback enqueued behind the step; latency is
+// completion minus submission.
 //
 // Locking: server state is guarded by one mutex which is never held across a
 // CUDA call that can wait for the GPU (host callbacks take the same mutex).
@@ -48,7 +49,6 @@ struct Slot {
     bool releasing = false;
     float4 *mesh = nullptr;  // rest, idx (int4 bits), weights, out: 4 n float4
     int n_mesh = 0;
-    float *h_bq = nullptr, *h_bt = nullptr;  // pinned staging for bone poses
 };
 
 struct Done {
@@ -61,6 +61,9 @@ struct Done {
 struct viper_server {
     size_t budget = 0, used = 0;
     int max_inflight = 1, inflight = 0;
+    int steps_inflight = 0;
+    long long steps = 0;
+    viper_batch *batch = nullptr;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::unordered_map<int, Slot *> slots;
@@ -99,59 +102,79 @@ void complete(viper_server *S, Slot *sl, Req *r, int status)
     S->cv_work.notify_one();
 }
 
-struct CbCtx {
+// Frames advanced by one multi-scene step, completed by its host callback.
+struct StepCtx {
     viper_server *S;
-    Slot *sl;
-    Req *r;
-    int status;
+    std::vector<std::pair<Slot *, Req *>> frames;
+    std::vector<int> status;  // latched errors known when the step was queued
 };
 
-void CUDART_CB host_done(void *p)
+void CUDART_CB step_done(void *p)
 {
-    CbCtx *c = static_cast<CbCtx *>(p);
+    StepCtx *c = static_cast<StepCtx *>(p);
     {
         std::lock_guard<std::mutex> lk(c->S->mu);
-        complete(c->S, c->sl, c->r, c->status);
+        for (size_t i = 0; i < c->frames.size(); ++i) {
+            Slot *sl = c->frames[i].first;
+            int st = c->status[i];
+            // the step mirrored the scene's error word to the host
+            if (st == VIPER_OK) st = viper::scene_decode_err(*(volatile int *)sl->sc->h_err);
+            complete(c->S, sl, c->frames[i].second, st);
+        }
+        c->S->steps_inflight--;
     }
     delete c;
 }
 
-// Enqueue one frame of a scene (no lock held).
-void dispatch(viper_server *S, Slot *sl, Req *r)
+// Queue one multi-scene step (no lock held).
+void dispatch(viper_server *S, std::vector<std::pair<Slot *, Req *>> &todo)
 {
-    int rc = VIPER_OK;
-    if (sl->n_bones > 0) {
-        memcpy(sl->h_bq, r->bq.data(), sizeof(float) * 4 * sl->n_bones);
-        memcpy(sl->h_bt, r->bt.data(), sizeof(float) * 3 * sl->n_bones);
-        rc = viper_set_bones(sl->sc, sl->n_bones, sl->h_bq, sl->h_bt);
+    const int n = (int)todo.size();
+    std::vector<viper_batch_item> items(n);
+    for (int i = 0; i < n; ++i) {
+        Slot *sl = todo[i].first;
+        Req *r = todo[i].second;
+        viper_batch_item &it = items[i];
+        memset(&it, 0, sizeof(it));
+        it.scene = sl->sc;
+        if (sl->n_bones > 0) {
+            it.bone_quat = r->bq.data();
+            it.bone_trans = r->bt.data();
+        }
+        if (sl->n_mesh > 0) {
+            const int m = sl->n_mesh;
+            it.n_mesh = m;
+            it.rest4 = (const float *)sl->mesh;
+            it.idx4 = (const int *)(sl->mesh + m);
+            it.w4 = (const float *)(sl->mesh + 2 * m);
+            it.out4 = (float *)(sl->mesh + 3 * m);
+        }
     }
-    if (rc == VIPER_OK) rc = viper_step(sl->sc, r->dt, r->substeps, r->iterations);
-    if ((rc == VIPER_OK || rc == VIPER_EOVERFLOW) && sl->n_mesh > 0) {
-        const int n = sl->n_mesh;
-        int rs = viper_skin(sl->sc, n, (const float *)sl->mesh, (const int *)(sl->mesh + n),
-                            (const float *)(sl->mesh + 2 * n), (float *)(sl->mesh + 3 * n));
-        if (rs != VIPER_OK) rc = rs;
-    }
-    if (rc == VIPER_OK || rc == VIPER_EOVERFLOW) {
-        CbCtx *c = new CbCtx{S, sl, r, rc};
-        if (cudaLaunchHostFunc(sl->sc->stream, host_done, c) == cudaSuccess) return;
-        delete c;
-        rc = VIPER_ECUDA;
-    }
+    const Req *r0 = todo[0].second;
+    StepCtx *c = new StepCtx{S, todo, std::vector<int>(n, VIPER_OK)};
+    int rc = viper_batch_step(S->batch, items.data(), n, r0->dt, r0->substeps, r0->iterations, c->status.data());
+    if (rc == VIPER_OK && cudaLaunchHostFunc((cudaStream_t)viper_batch_stream(S->batch), step_done, c) == cudaSuccess)
+        return;
+    if (rc == VIPER_OK) rc = VIPER_ECUDA;
     std::lock_guard<std::mutex> lk(S->mu);
-    complete(S, sl, r, rc);
+    for (auto &t : todo) complete(S, t.first, t.second, rc);
+    S->steps_inflight--;
+    delete c;
 }
+
+constexpr int kMaxSteps = 2;  // multi-scene steps in flight
 
 void run(viper_server *S)
 {
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         std::vector<Slot *> ready;
-        for (auto &kv : S->slots) {
-            Slot *sl = kv.second;
-            if (!sl->inflight && !sl->queue.empty()) ready.push_back(sl);
-        }
-        // oldest waiting request first
+        if (S->steps_inflight < kMaxSteps)
+            for (auto &kv : S->slots) {
+                Slot *sl = kv.second;
+                if (!sl->inflight && !sl->queue.empty()) ready.push_back(sl);
+            }
+        // oldest waiting request first; one step takes the requests sharing its schedule
         std::sort(ready.begin(), ready.end(), [](Slot *a, Slot *b) {
             return a->queue.front()->t_submit < b->queue.front()->t_submit;
         });
@@ -159,18 +182,24 @@ void run(viper_server *S)
         for (Slot *sl : ready) {
             if (S->inflight >= S->max_inflight) break;
             Req *r = sl->queue.front();
+            if (!todo.empty()) {
+                const Req *r0 = todo[0].second;
+                if (r->dt != r0->dt || r->substeps != r0->substeps || r->iterations != r0->iterations) continue;
+            }
             sl->queue.pop_front();
             sl->inflight = r;
             S->inflight++;
             todo.emplace_back(sl, r);
         }
         if (todo.empty()) {
-            if (S->stop) return;
+            if (S->stop && S->steps_inflight == 0) return;
             S->cv_work.wait(lk);
             continue;
         }
+        S->steps_inflight++;
+        S->steps++;
         lk.unlock();
-        for (auto &t : todo) dispatch(S, t.first, t.second);
+        dispatch(S, todo);
         lk.lock();
     }
 }
@@ -179,8 +208,6 @@ void free_slot(Slot *sl)
 {
     if (sl->sc) viper_scene_destroy(sl->sc);
     if (sl->mesh) cudaFree(sl->mesh);
-    if (sl->h_bq) cudaFreeHost(sl->h_bq);
-    if (sl->h_bt) cudaFreeHost(sl->h_bt);
     delete sl;
 }
 
@@ -194,6 +221,11 @@ int viper_server_create(size_t budget_bytes, int max_inflight, viper_server **ou
     viper_server *S = new viper_server();
     S->budget = budget_bytes;
     S->max_inflight = max_inflight;
+    int rc = viper_batch_create(nullptr, &S->batch);
+    if (rc != VIPER_OK) {
+        delete S;
+        return rc;
+    }
     S->worker = std::thread(run, S);
     *out = S;
     return VIPER_OK;
@@ -210,10 +242,11 @@ void viper_server_destroy(viper_server *S)
         }
         S->stop = true;
         S->cv_work.notify_all();
-        S->cv_done.wait(lk, [&] { return S->inflight == 0; });
+        S->cv_done.wait(lk, [&] { return S->inflight == 0 && S->steps_inflight == 0; });
     }
     S->worker.join();
     for (auto &kv : S->slots) free_slot(kv.second);
+    viper_batch_destroy(S->batch);
     delete S;
 }
 
@@ -232,17 +265,15 @@ int viper_server_admit(viper_server *S, const viper_scene_desc *desc, int n_mesh
     }
     Slot *sl = new Slot();
     viper_scene_desc d = *desc;
-    d.stream = nullptr;  // every scene runs on its own stream
+    d.stream = viper_batch_stream(S->batch);  // scenes live on the server's stream
     int rc = viper_scene_create(&d, &sl->sc);
-    if (rc == VIPER_OK && solver_mode == VIPER_SOLVER_FRAME) {
-        // the frame kernel when the scene fits it, on as few CTAs as it has work
-        // items so that many scenes' frames share the GPU; else the graph path
-        sl->sc->frame_min_grid = 0;
-        if (viper_set_solver(sl->sc, VIPER_SOLVER_FRAME, 4, 512) != VIPER_OK) solver_mode = VIPER_SOLVER_BATCHED;
-    } else if (rc == VIPER_OK && solver_mode != VIPER_SOLVER_BATCHED) {
+    if (rc == VIPER_OK && (solver_mode == VIPER_SOLVER_PLAIN || solver_mode == VIPER_SOLVER_FRAME)) {
         rc = viper_set_solver(sl->sc, solver_mode, 4, 256);
+        if (rc != VIPER_OK && solver_mode == VIPER_SOLVER_FRAME) rc = VIPER_OK;  // not co-resident: batched
     }
-    if (rc == VIPER_OK && dt > 0 && substeps > 0 && iterations >= 0) rc = viper_prepare(sl->sc, dt, substeps, iterations);
+    // scenes the multi-scene kernels cannot take run on their own: build their graph now
+    if (rc == VIPER_OK && sl->sc->resident_nv != sl->sc->nv && dt > 0 && substeps > 0 && iterations >= 0)
+        rc = viper_prepare(sl->sc, dt, substeps, iterations);
     if (rc == VIPER_OK && n_mesh > 0) {
         const size_t nb = sizeof(float4) * (size_t)n_mesh;
         if (cudaMalloc((void **)&sl->mesh, 4 * nb) != cudaSuccess) {
@@ -256,11 +287,6 @@ int viper_server_admit(viper_server *S, const viper_scene_desc *desc, int n_mesh
         sl->n_mesh = n_mesh;
     }
     sl->n_bones = desc->n_bones;
-    if (rc == VIPER_OK && sl->n_bones > 0) {
-        if (cudaHostAlloc((void **)&sl->h_bq, sizeof(float) * 4 * sl->n_bones, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc((void **)&sl->h_bt, sizeof(float) * 3 * sl->n_bones, cudaHostAllocDefault) != cudaSuccess)
-            rc = VIPER_ENOMEM;
-    }
     if (rc != VIPER_OK) {
         free_slot(sl);
         std::lock_guard<std::mutex> lk(S->mu);
@@ -388,6 +414,7 @@ int viper_server_get_stats(viper_server *S, viper_server_stats *st)
     int q = 0;
     for (auto &kv : S->slots) q += (int)kv.second->queue.size();
     st->queued = q;
+    st->steps = S->steps;
     if (!S->lat.empty()) {
         std::vector<double> v = S->lat;
         std::sort(v.begin(), v.end());
@@ -413,6 +440,7 @@ int viper_server_reset_stats(viper_server *S)
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat.clear();
     S->frames = S->failed = 0;
+    S->steps = 0;
     S->units = 0;
     return VIPER_OK;
 }

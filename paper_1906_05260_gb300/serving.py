@@ -1,7 +1,8 @@
 """Serving driver: many independent scenes stepped as frame requests arrive.
 
 `Server` wraps the C ABI's viper_server_* calls (marshalling only; admission,
-queueing, dispatch and timing run in libviper.so's native dispatcher).
+queueing, dispatch through the multi-scene frame step and timing run in
+libviper.so's native dispatcher).
 `run_load` replays a seeded Poisson stream of muscle-rig scenes with
 exponential lifetimes, each issuing 60 Hz frame-step requests, in real time,
 and reports latency percentiles and aggregate throughput.
@@ -194,4 +195,5 @@ def run_load(duration: float = 60.0, rate: float = 6.4, mean_life: float = 10.0,
             "rod_vertex_substeps_per_s": st["rod_vertex_substeps"] / elapsed, "p50_ms": st["p50_ms"],
             "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"], "peak_live_scenes": peak_live,
             "arrivals": len(arrivals), "budget_refusals": refused, "max_inflight": max_inflight,
+            "steps": st["steps"], "mean_scenes_per_step": st["frames"] / max(st["steps"], 1),
             "admit_ms_p50": float(np.percentile(admit_ms, 50)) if admit_ms else None}

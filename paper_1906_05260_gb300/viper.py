@@ -52,7 +52,8 @@ class ServerStats(C.Structure):
     """Mirror of viper_server_stats."""
     _fields_ = [("frames", C.c_longlong), ("failed", C.c_longlong), ("rod_vertex_substeps", C.c_double),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
-                ("scenes", C.c_int), ("inflight", C.c_int), ("queued", C.c_int), ("used_bytes", C.c_size_t)]
+                ("scenes", C.c_int), ("inflight", C.c_int), ("queued", C.c_int), ("used_bytes", C.c_size_t),
+                ("steps", C.c_longlong)]
 
 
 class BatchItem(C.Structure):

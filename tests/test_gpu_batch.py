@@ -136,7 +136,7 @@ def test_batch_launch_count_independent_of_scene_count(V):
         B.step(objs, [o.scene.bone_pose(DT) for o in objs], meshes, DT, SUB, IT)
         counts.append(B.launch_count() - c0)
     B.synchronize()
-    assert counts[0] == counts[1] == SUB * (7 + 2 * IT) + 2, counts
+    assert counts[0] == counts[1] == SUB * (2 * IT + 2) + 3, counts
 
 
 def test_batch_quarantines_nonfinite_scene_only(V):
@@ -174,3 +174,30 @@ def test_batch_rejects_bad_arguments(V):
     items[0].n_mesh = 10  # mesh without pointers
     assert L.viper_batch_step(B._h, items, 1, DT, SUB, IT, None) == V.EINVAL
     assert L.viper_batch_step(B._h, items, 0, DT, SUB, IT, None) == 0  # empty call
+
+
+def test_batch_large_scene_and_zero_iterations(V):
+    """A scene too large for the one-CTA grid build (the multi-CTA broadphase
+    sequence), and frames without iterations (prediction, broadphase and
+    velocity update only), against viper_step."""
+    big = S.hair()  # 20,000 strands: 300,000 pills
+    small = S.muscle_rig(seed=3, n_rods=40, mesh_verts=0)
+    for iters, scenes in ((IT, [big, small]), (0, [small])):
+        a = [V.Scene(sc) for sc in scenes]
+        b = [V.Scene(sc) for sc in scenes]
+        B = V.Batch()
+        for f in range(2):
+            B.step(a, [_pose(sc, (f + 1) * DT) for sc in scenes], None, DT, SUB, iters)
+        B.synchronize()
+        for f in range(2):
+            for o, sc in zip(b, scenes):
+                p = _pose(sc, (f + 1) * DT)
+                if p is not None:
+                    o.set_bones(*p)
+                o.step(DT, SUB, iters)
+        for ga, gb in zip(a, b):
+            assert ga.sync() == 0 and gb.sync() == 0
+            sa, sb = ga.get_state(), gb.get_state()
+            scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
+            assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
+            assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4

@@ -53,6 +53,7 @@ def test_results_identical_alone_and_in_the_mix(SV):
         np.testing.assert_array_equal(alone[k], mix[k])
     np.testing.assert_array_equal(mesh_alone, mesh_mix)
     assert stats["frames"] == 48 and stats["failed"] == 0
+    assert stats["steps"] < stats["frames"]  # scenes were stepped together
 
 
 def test_admission_by_memory_budget(SV):
