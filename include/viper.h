@@ -253,8 +253,9 @@ size_t viper_scene_footprint(const viper_scene_desc *desc);
  * frame is captured into a graph; cached graphs are dropped).  cls:
  *   VIPER_PROF_NONE, VIPER_PROF_ROD (rod kernels: shared-memory and per-colour),
  *   VIPER_PROF_CONTACT (narrowphase + contact projection),
- *   VIPER_PROF_BROADPHASE (every broadphase kernel),
- *   VIPER_PROF_LBS (skinning gather), VIPER_PROF_ELEMENTWISE (predict, finish, apply).
+ *   VIPER_PROF_BROADPHASE (grid build: bounds, cell counts, scan, scatter),
+ *   VIPER_PROF_LBS (skinning gather), VIPER_PROF_ELEMENTWISE (predict, finish,
+ *   apply, end of frame), VIPER_PROF_PAIRS (candidate-pair search).
  * viper_profile_read synchronises and returns the summed device time (ms) and
  * number of bracketed launches of the last frame plus any skinning calls since.
  */
@@ -264,6 +265,7 @@ size_t viper_scene_footprint(const viper_scene_desc *desc);
 #define VIPER_PROF_BROADPHASE 3
 #define VIPER_PROF_LBS 4
 #define VIPER_PROF_ELEMENTWISE 5
+#define VIPER_PROF_PAIRS 6
 int viper_profile(viper_scene *scene, int kernel_class);
 int viper_profile_read(viper_scene *scene, double *ms, int *launches);
 

@@ -58,6 +58,8 @@ constexpr int kElemThreads = 256, kEmitWarpsB = 8, kScanThreadsB = 1024, kScanPe
 
 // Scene of this CTA for `kind` (the last scene whose first block is <= blockIdx.x),
 // staged in shared memory; local = block index within the scene, nblk = its block count.
+// Kernels are launched with programmatic dependent launch (see pdl_wait): this
+// prologue overlaps the predecessor kernel.
 __device__ __forceinline__ void batch_enter(const BatchArgs &A, int kind, BatchScene &sb, int &local, int &nblk)
 {
     __shared__ int s_lo, s_hi;
@@ -79,6 +81,11 @@ __device__ __forceinline__ void batch_enter(const BatchArgs &A, int kind, BatchS
     __syncthreads();
     local = b - s_lo;
     nblk = s_hi - s_lo;
+    // Everything above reads only the call's table, uploaded before the first
+    // kernel of the call; the scene state is read after the predecessor kernel
+    // has finished.  The successor is released once every CTA got here.
+    pdl_wait();
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- substep kernels
@@ -360,15 +367,35 @@ __global__ void __launch_bounds__(kElemThreads) batch_skin_kernel(BatchArgs A)
     __shared__ BatchScene sb;
     int local, nblk;
     batch_enter(A, K_MESH, sb, local, nblk);
-    for (int i = local * blockDim.x + threadIdx.x; i < sb.n_mesh; i += nblk * blockDim.x)
-        lbs_vertex_at(i, sb.P.ns, sb.rest, sb.idx, sb.w, sb.frames, sb.out, sb.P.err);
+    const int span = blockDim.x * kLbsBatch;
+    for (int base = local * span; base < sb.n_mesh; base += nblk * span)
+        lbs_vertices(base + threadIdx.x, blockDim.x, sb.n_mesh, sb.P.ns, sb.rest, sb.idx, sb.w, sb.frames, sb.out,
+                     sb.P.err);
 }
 
 // ---------------------------------------------------------------- host side
 namespace {
 
+// Launch with programmatic stream serialisation (the kernel's prologue may
+// overlap its predecessor; see batch_enter).
+template <typename... KArgs, typename... Args>
+void launch(void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int kEmitPillsPerWarp = 4;
-constexpr int kMeshPerThread = 4;
+constexpr int kMeshPerThread = 16;  // kLbsBatch vertices per round, 4 rounds
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -423,6 +450,124 @@ int stage_reserve(viper_batch::Stage &S, size_t bytes)
     return VIPER_OK;
 }
 
+// Launch shape of one sequence: blocks per kernel kind over all its scenes.
+struct Shape {
+    int tot[K_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int threads = 0, smem = 16;
+    bool cp = false, fused_grid = true;
+};
+
+// Device view of one scene for a frame of sub-step h (b.P.bq1 / bt1: the
+// scene's own target pose; the caller may point them elsewhere), and its
+// blocks per kernel kind.
+void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_batch_item &it, double h, bool cp)
+{
+    memset(&b, 0, sizeof(b));
+    b.P = s->P;
+    b.P.h = (float)h;
+    b.P.inv_h = (float)(1.0 / h);
+    b.P.inv_h2 = (float)(1.0 / (h * h));
+    b.LQ = s->LQ;
+    b.LC = s->LC;
+    b.sperm = s->d_sperm;
+    b.frames = s->frames;
+    b.rest = reinterpret_cast<const float4 *>(it.rest4);
+    b.idx = reinterpret_cast<const int4 *>(it.idx4);
+    b.w = reinterpret_cast<const float4 *>(it.w4);
+    b.out = reinterpret_cast<float4 *>(it.out4);
+    b.n_mesh = it.n_mesh;
+    b.bq0 = const_cast<float4 *>(s->P.bq0);
+    b.bq1_own = const_cast<float4 *>(s->P.bq1);
+    b.bt0 = const_cast<float *>(s->P.bt0);
+    b.bt1_own = const_cast<float *>(s->P.bt1);
+    b.herr = s->d_herr;
+    b.n_bones = s->n_bones;
+    b.pills = (s->flags & VIPER_FLAG_CONTACTS) ? 1 : 0;
+    const int nv = s->nv, ns = s->ns;
+    cnt[K_ELEM] = cdiv(nv + ns, kElemThreads);
+    cnt[K_PILL] = b.pills ? cdiv(ns, kElemThreads) : 0;
+    cnt[K_EMIT] = b.pills ? cdiv(ns, kEmitWarpsB * kEmitPillsPerWarp) : 0;  // a few work units per warp
+    cnt[K_SCAN] = b.pills ? 1 : 0;
+    cnt[K_ROD] = s->n_items;
+    cnt[K_CONTACT] = cp ? std::min(64, std::max(1, cdiv(ns + (s->n_planes > 0 ? nv : 0), kElemThreads))) : 0;
+    cnt[K_END] = it.n_mesh > 0 ? std::max(1, cdiv(ns, kElemThreads)) : 1;
+    cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
+}
+
+void shape_add(Shape &sh, const viper_scene *s, bool cp)
+{
+    sh.cp = cp;
+    sh.smem = std::max(sh.smem, cp ? s->smem_iter : s->smem_full);
+    if (s->ns > kGridMaxPills) sh.fused_grid = false;
+    sh.threads = s->block_threads;
+}
+
+// Enqueue the frame's launch sequence on st; returns the number of kernels or
+// -1.  With `prof`, each launch is bracketed by that scene's profiling events.
+long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, int iterations, cudaStream_t st,
+                           viper_scene *prof)
+{
+    const int *tot = sh.tot;
+    const int threads = sh.threads, smem = sh.smem;
+    const bool cp = sh.cp, fused_grid = sh.fused_grid;
+    const void *rod_fn = cp ? reinterpret_cast<const void *>(batch_rod_kernel<false>)
+                            : reinterpret_cast<const void *>(batch_rod_kernel<true>);
+    if (raise_smem_limit(rod_fn, smem) != 0) return -1;
+    if (cp && raise_smem_limit(reinterpret_cast<const void *>(batch_rod_first_kernel), smem) != 0) return -1;
+    const int grid_smem = sizeof(int) * kGridSmemCells;
+    if (fused_grid && raise_smem_limit(reinterpret_cast<const void *>(batch_grid_kernel), grid_smem) != 0) return -1;
+    long long L = 0;
+    auto go = [&](int cls, auto &&fn) {
+        ProfScope ps(prof, cls);
+        fn();
+        ++L;
+    };
+    auto broadphase = [&]() {
+        if (tot[K_PILL] <= 0) return;
+        if (fused_grid) {
+            go(PROF_BROADPHASE, [&] { launch(batch_grid_kernel, tot[K_SCAN], kGridThreads, grid_smem, st, A); });
+        } else {
+            go(PROF_BROADPHASE, [&] { launch(batch_bounds_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_count_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_scan_kernel, tot[K_SCAN], kScanThreadsB, 0, st, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_scatter_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
+        }
+        go(PROF_PAIRS, [&] { launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A); });
+    };
+    auto contact = [&]() {
+        go(PROF_CONTACT, [&] { launch(batch_contact_kernel, tot[K_CONTACT], kElemThreads, 0, st, A); });
+    };
+    if (cp && iterations > 0) {
+        // per substep: [finish + predict + sweep 0] | grid | emit | contact | {sweep | contact} x (I - 1)
+        for (int k = 0; k < substeps; ++k) {
+            const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
+            go(PROF_ROD, [&] { launch(batch_rod_first_kernel, tot[K_ROD], threads, smem, st, A, k > 0 ? 1 : 0, tau); });
+            broadphase();
+            contact();
+            for (int i = 1; i < iterations; ++i) {
+                go(PROF_ROD, [&] { launch(batch_rod_kernel<false>, tot[K_ROD], threads, smem, st, A, 1, 0, 1, tau); });
+                contact();
+            }
+        }
+        go(PROF_ELEM, [&] { launch(batch_finish_kernel, tot[K_ELEM], kElemThreads, 0, st, A, 1); });
+    } else {
+        for (int k = 0; k < substeps; ++k) {
+            const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
+            if (!cp) {
+                go(PROF_ROD, [&] { launch(batch_rod_kernel<true>, tot[K_ROD], threads, smem, st, A, iterations, 1, 0, tau); });
+                continue;
+            }
+            // contact path without iterations: prediction, broadphase, velocity update
+            go(PROF_ELEM, [&] { launch(batch_predict_kernel, tot[K_ELEM], kElemThreads, 0, st, A, tau); });
+            broadphase();
+            go(PROF_ELEM, [&] { launch(batch_finish_kernel, tot[K_ELEM], kElemThreads, 0, st, A, 0); });
+        }
+    }
+    go(PROF_ELEM, [&] { launch(batch_end_kernel, tot[K_END], kElemThreads, 0, st, A); });
+    if (tot[K_MESH] > 0) go(PROF_LBS, [&] { launch(batch_skin_kernel, tot[K_MESH], kElemThreads, 0, st, A); });
+    return cudaGetLastError() == cudaSuccess ? L : -1;
+}
+
 // One launch sequence for the scenes idx (same CTA size; contact path or not).
 int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<int> &idx, float dt, int substeps,
               int iterations, bool cp)
@@ -448,140 +593,89 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     const float *dbt = reinterpret_cast<const float *>(S.d + o_bt);
     const double h = (double)dt / substeps;
     size_t bcur = 0;
-    int smem = 16, threads = 0;
-    bool fused_grid = true;  // every scene's broadphase fits one CTA
-    for (int k = 0; k <= n; ++k)
-        for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k] = 0;
+    Shape sh;
+    for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1)] = 0;
     for (int k = 0; k < n; ++k) {
         const viper_batch_item &it = items[idx[k]];
         viper_scene *s = it.scene;
         BatchScene &b = hs[k];
-        memset(&b, 0, sizeof(b));
-        b.P = s->P;
-        b.P.h = (float)h;
-        b.P.inv_h = (float)(1.0 / h);
-        b.P.inv_h2 = (float)(1.0 / (h * h));
-        if (it.bone_quat && s->n_bones > 0) {
+        int cnt[K_KINDS];
+        fill_scene(b, cnt, s, it, h, cp);
+        if (it.bone_quat && s->n_bones > 0) {  // this frame's target pose, from the call's table
             memcpy(hbq + bcur, it.bone_quat, sizeof(float4) * s->n_bones);
             memcpy(hbt + 3 * bcur, it.bone_trans, sizeof(float) * 3 * s->n_bones);
             b.P.bq1 = dbq + bcur;
             b.P.bt1 = dbt + 3 * bcur;
             bcur += (size_t)s->n_bones;
         }
-        b.LQ = s->LQ;
-        b.LC = s->LC;
-        b.sperm = s->d_sperm;
-        b.frames = s->frames;
-        b.rest = reinterpret_cast<const float4 *>(it.rest4);
-        b.idx = reinterpret_cast<const int4 *>(it.idx4);
-        b.w = reinterpret_cast<const float4 *>(it.w4);
-        b.out = reinterpret_cast<float4 *>(it.out4);
-        b.n_mesh = it.n_mesh;
-        b.bq0 = const_cast<float4 *>(s->P.bq0);
-        b.bq1_own = const_cast<float4 *>(s->P.bq1);
-        b.bt0 = const_cast<float *>(s->P.bt0);
-        b.bt1_own = const_cast<float *>(s->P.bt1);
-        b.herr = s->d_herr;
-        b.n_bones = s->n_bones;
-        b.pills = (s->flags & VIPER_FLAG_CONTACTS) ? 1 : 0;
-        const int nv = s->nv, ns = s->ns;
-        int cnt[K_KINDS];
-        cnt[K_ELEM] = cdiv(nv + ns, kElemThreads);
-        cnt[K_PILL] = b.pills ? cdiv(ns, kElemThreads) : 0;
-        cnt[K_EMIT] = b.pills ? cdiv(ns, kEmitWarpsB * kEmitPillsPerWarp) : 0;  // a few work units per warp
-        cnt[K_SCAN] = b.pills ? 1 : 0;
-        cnt[K_ROD] = s->n_items;
-        cnt[K_CONTACT] = cp ? std::min(64, std::max(1, cdiv(ns + (s->n_planes > 0 ? nv : 0), kElemThreads))) : 0;
-        cnt[K_END] = it.n_mesh > 0 ? std::max(1, cdiv(ns, kElemThreads)) : 1;
-        cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
         for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1) + k + 1] = off[c * (n + 1) + k] + cnt[c];
-        smem = std::max(smem, cp ? s->smem_iter : s->smem_full);
-        if (ns > kGridMaxPills) fused_grid = false;
-        threads = s->block_threads;
+        shape_add(sh, s, cp);
     }
-    int tot[K_KINDS];
-    for (int c = 0; c < K_KINDS; ++c) tot[c] = off[c * (n + 1) + n];
+    for (int c = 0; c < K_KINDS; ++c) sh.tot[c] = off[c * (n + 1) + n];
 
     cudaStream_t st = B->stream;
     if (cudaMemcpyAsync(S.d, S.h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return VIPER_ECUDA;
     BatchArgs A{reinterpret_cast<const BatchScene *>(S.d), reinterpret_cast<const int *>(S.d + o_off), n};
-    const void *rod_fn = cp ? reinterpret_cast<const void *>(batch_rod_kernel<false>)
-                            : reinterpret_cast<const void *>(batch_rod_kernel<true>);
-    if (raise_smem_limit(rod_fn, smem) != 0) return VIPER_EINVAL;
-    if (cp && raise_smem_limit(reinterpret_cast<const void *>(batch_rod_first_kernel), smem) != 0) return VIPER_EINVAL;
-    const int grid_smem = sizeof(int) * kGridSmemCells;
-    if (fused_grid && raise_smem_limit(reinterpret_cast<const void *>(batch_grid_kernel), grid_smem) != 0)
-        return VIPER_EINVAL;
-    long long L = 0;
-    if (cp && iterations > 0) {
-        // per substep: [finish + predict + sweep 0] | grid | emit | contact | {sweep | contact} x (I - 1)
-        for (int k = 0; k < substeps; ++k) {
-            const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
-            batch_rod_first_kernel<<<tot[K_ROD], threads, smem, st>>>(A, k > 0 ? 1 : 0, tau);
-            ++L;
-            if (tot[K_PILL] > 0) {
-                if (fused_grid) {
-                    batch_grid_kernel<<<tot[K_SCAN], kGridThreads, grid_smem, st>>>(A);
-                    ++L;
-                } else {
-                    batch_bounds_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-                    batch_count_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-                    batch_scan_kernel<<<tot[K_SCAN], kScanThreadsB, 0, st>>>(A);
-                    batch_scatter_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-                    L += 4;
-                }
-                batch_emit_kernel<<<tot[K_EMIT], 32 * kEmitWarpsB, 0, st>>>(A);
-                ++L;
-            }
-            batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
-            ++L;
-            for (int i = 1; i < iterations; ++i) {
-                batch_rod_kernel<false><<<tot[K_ROD], threads, smem, st>>>(A, 1, 0, 1, tau);
-                batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
-                L += 2;
-            }
-        }
-        batch_finish_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, 1);
-        ++L;
-    }
-    for (int k = 0; k < substeps && !(cp && iterations > 0); ++k) {
-        const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
-        if (!cp) {
-            batch_rod_kernel<true><<<tot[K_ROD], threads, smem, st>>>(A, iterations, 1, 0, tau);
-            ++L;
-            continue;
-        }
-        batch_predict_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, tau);
-        ++L;
-        if (tot[K_PILL] > 0) {
-            batch_bounds_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-            batch_count_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-            batch_scan_kernel<<<tot[K_SCAN], kScanThreadsB, 0, st>>>(A);
-            batch_scatter_kernel<<<tot[K_PILL], kElemThreads, 0, st>>>(A);
-            batch_emit_kernel<<<tot[K_EMIT], 32 * kEmitWarpsB, 0, st>>>(A);
-            L += 5;
-        }
-        for (int i = 0; i < iterations; ++i) {
-            batch_rod_kernel<false><<<tot[K_ROD], threads, smem, st>>>(A, 1, i == 0 ? 1 : 0, i > 0 ? 1 : 0, tau);
-            batch_contact_kernel<<<tot[K_CONTACT], kElemThreads, 0, st>>>(A);
-            L += 2;
-        }
-        batch_finish_kernel<<<tot[K_ELEM], kElemThreads, 0, st>>>(A, iterations > 0 ? 1 : 0);
-        ++L;
-    }
-    batch_end_kernel<<<tot[K_END], kElemThreads, 0, st>>>(A);
-    ++L;
-    if (tot[K_MESH] > 0) {
-        batch_skin_kernel<<<tot[K_MESH], kElemThreads, 0, st>>>(A);
-        ++L;
-    }
+    const long long L = enqueue_sequence(A, sh, substeps, iterations, st, nullptr);
+    if (L < 0) return VIPER_ECUDA;
     B->launches += L;
     if (cudaEventRecord(S.done, st) != cudaSuccess) return VIPER_ECUDA;
     S.used = true;
-    return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;
+    return VIPER_OK;
 }
 
 }  // namespace
+
+bool self_batch_ok(const viper_scene *s)
+{
+    return s->resident_nv == s->nv && s->n_items > 0 &&
+           (!(s->flags & VIPER_FLAG_CONTACTS) || s->ns <= kGridMaxPills);
+}
+
+int self_batch_capture(viper_scene *s, float dt, int substeps, int iterations, cudaGraph_t *graph,
+                       long long *launches)
+{
+    const size_t o_off = align16(sizeof(BatchScene));
+    const size_t bytes = o_off + sizeof(int) * K_KINDS * 2;
+    if (!s->self_table) {
+        int rc = scene_alloc(s, bytes, &s->self_table);
+        if (rc) return rc;
+    }
+    std::vector<char> h(bytes, 0);
+    BatchScene *b = reinterpret_cast<BatchScene *>(h.data());
+    int *off = reinterpret_cast<int *>(h.data() + o_off);
+    viper_batch_item it;
+    memset(&it, 0, sizeof(it));
+    it.scene = s;
+    const bool cp = scene_contact_path(s);
+    int cnt[K_KINDS];
+    fill_scene(*b, cnt, s, it, (double)dt / substeps, cp);  // bones: the scene's own target pose
+    Shape sh;
+    shape_add(sh, s, cp);
+    for (int c = 0; c < K_KINDS; ++c) {
+        off[2 * c] = 0;
+        off[2 * c + 1] = cnt[c];
+        sh.tot[c] = cnt[c];
+    }
+    // stream-ordered after any replay of an earlier graph that reads the table
+    if (cudaMemcpyAsync(s->self_table, h.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return VIPER_ECUDA;
+    const char *t = static_cast<const char *>(s->self_table);
+    BatchArgs A{reinterpret_cast<const BatchScene *>(t), reinterpret_cast<const int *>(t + o_off), 1};
+    s->prof_used = 0;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VIPER_ECUDA;
+    const long long L = enqueue_sequence(A, sh, substeps, iterations, s->stream, s);
+    cudaError_t ce = cudaStreamEndCapture(s->stream, graph);
+    if (L < 0 || ce != cudaSuccess) {
+        if (ce == cudaSuccess && *graph) cudaGraphDestroy(*graph);
+        *graph = nullptr;
+        return VIPER_ECUDA;
+    }
+    *launches = L;
+    return VIPER_OK;
+}
+
 }  // namespace viper
 
 using namespace viper;

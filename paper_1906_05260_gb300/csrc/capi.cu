@@ -409,6 +409,13 @@ namespace viper {
 int scene_poll_latched(viper_scene *s) { return poll_latched(s); }
 bool scene_contact_path(const viper_scene *s) { return contact_path(s); }
 int scene_decode_err(int e) { return decode_err(e); }
+int scene_alloc(viper_scene *s, size_t bytes, void **out)
+{
+    char *p = nullptr;
+    int rc = dalloc(s, &p, bytes);
+    if (rc == VIPER_OK) *out = p;
+    return rc;
+}
 
 static void prof_record(viper_scene *s, cudaEvent_t ev)
 {
@@ -838,15 +845,26 @@ static int ensure_graph(viper_scene *s, float dt, int substeps, int iterations)
         s->gexec = nullptr;
     }
     cudaGraph_t graph = nullptr;
-    long long before = s->launches;
-    VCHECK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_frame(s, dt, substeps, iterations);
-    cudaError_t ce = cudaStreamEndCapture(s->stream, &graph);
-    if (ce != cudaSuccess) return VIPER_ECUDA;
-    ce = cudaGraphInstantiate(&s->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    s->g_launches = s->launches - before;  // kernels per replay (counted while capturing)
-    s->launches = before;
+    cudaError_t ce;
+    if (self_batch_ok(s)) {
+        // the multi-scene kernels for this scene alone (fused phases, programmatic launches)
+        long long L = 0;
+        int rc = self_batch_capture(s, dt, substeps, iterations, &graph, &L);
+        if (rc) return rc;
+        ce = cudaGraphInstantiate(&s->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        s->g_launches = L;
+    } else {
+        long long before = s->launches;
+        VCHECK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_frame(s, dt, substeps, iterations);
+        ce = cudaStreamEndCapture(s->stream, &graph);
+        if (ce != cudaSuccess) return VIPER_ECUDA;
+        ce = cudaGraphInstantiate(&s->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        s->g_launches = s->launches - before;  // kernels per replay (counted while capturing)
+        s->launches = before;
+    }
     if (ce != cudaSuccess) {
         s->gexec = nullptr;
         return VIPER_ECUDA;
@@ -1062,7 +1080,7 @@ int viper_get_predicted(viper_scene *s, float *x4, float *rbar)
 
 int viper_profile(viper_scene *s, int cls)
 {
-    if (!s || cls < PROF_NONE || cls > PROF_ELEM) return VIPER_EINVAL;
+    if (!s || cls < PROF_NONE || cls > PROF_PAIRS) return VIPER_EINVAL;
     s->prof_class = cls;
     s->prof_used = s->prof_used_skin = 0;
     if (s->gexec) {

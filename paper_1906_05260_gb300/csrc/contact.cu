@@ -213,7 +213,7 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
         int eg = (P.ns + 8 * kEmitWarps - 1) / (8 * kEmitWarps);  // a warp per 8 pills: a few units each
         if (eg > 8 * sm_count()) eg = 8 * sm_count();
         if (eg < 1) eg = 1;
-        ProfScope ps(s, PROF_BROADPHASE);
+        ProfScope ps(s, PROF_PAIRS);
         bp_emit_kernel<<<eg, 32 * kEmitWarps, 0, st>>>(P);
     }
     if (s) s->launches += 4;

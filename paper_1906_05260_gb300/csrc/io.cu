@@ -17,12 +17,14 @@ __global__ void lbs_frames_kernel(Params P, const float4 *__restrict__ LQ, const
     if (g < P.ns) lbs_frame_at(P, LQ, LC, sperm, frames, g);
 }
 
+// Each thread skins kLbsBatch vertices per round, one CTA-stride apart (coalesced).
 __global__ void lbs_gather_kernel(int n, int ns, const float4 *__restrict__ rest, const int4 *__restrict__ idx,
                                   const float4 *__restrict__ w, const float4 *__restrict__ frames,
                                   float4 *__restrict__ out, int *err)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        lbs_vertex_at(i, ns, rest, idx, w, frames, out, err);
+    const int span = blockDim.x * kLbsBatch;
+    for (int base = blockIdx.x * span; base < n; base += gridDim.x * span)
+        lbs_vertices(base + threadIdx.x, blockDim.x, n, ns, rest, idx, w, frames, out, err);
 }
 
 static int sms()
@@ -40,7 +42,7 @@ static int sms()
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out)
 {
     lbs_frames_kernel<<<(s->ns + 255) / 256, 256, 0, s->ls>>>(s->P, s->LQ, s->LC, s->d_sperm, s->frames);
-    int grid = (n + 255) / 256;
+    int grid = (n + 256 * kLbsBatch - 1) / (256 * kLbsBatch);
     if (grid > 8 * sms()) grid = 8 * sms();
     if (grid < 1) grid = 1;
     ProfScope ps(s, PROF_LBS);

@@ -44,6 +44,15 @@ inline int raise_smem_limit(const void *fn, int bytes)
     return 0;
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic stream serialisation attribute may be scheduled while its
+// predecessor in the stream still runs.  pdl_wait blocks until the
+// predecessor grid has completed and its memory is visible (a no-op for a
+// normal launch); pdl_trigger lets the successor be scheduled once every CTA
+// of this grid has issued it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ================================================================ rods
 // Pin target in the rod's local frame.  Bone pose at substep fraction tau:
 // normalised lerp of the (sign-aligned) rotations and lerp of the origins
@@ -823,15 +832,11 @@ __device__ __forceinline__ void lbs_frame_at(const Params &P, const float4 *__re
 }
 
 // Skinned position of mesh vertex i: sum_k w_k T_k Tbar_k^-1 rest_i over its
-// four frames.  Frame ids outside [0, ns) contribute nothing and raise the
-// error word.  Streaming loads / stores: the mesh is touched once per frame.
-__device__ __forceinline__ void lbs_vertex_at(int i, int ns, const float4 *__restrict__ rest,
-                                              const int4 *__restrict__ idx, const float4 *__restrict__ w,
-                                              const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
+// four frames, from the vertex's rest position, frame ids and weights.
+// Frame ids outside [0, ns) contribute nothing and raise the error word.
+__device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns, const float4 *__restrict__ frames,
+                                           int *err)
 {
-    const float4 p = __ldcs(rest + i);
-    const int4 id = __ldcs(idx + i);
-    const float4 ww = __ldcs(w + i);
     const int ids[4] = {id.x, id.y, id.z, id.w};
     const float wv[4] = {ww.x, ww.y, ww.z, ww.w};
     float ox = 0.f, oy = 0.f, oz = 0.f;
@@ -847,7 +852,34 @@ __device__ __forceinline__ void lbs_vertex_at(int i, int ns, const float4 *__res
         oy += wv[k] * (r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w);
         oz += wv[k] * (r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
     }
-    __stcs(out + i, make_float4(ox, oy, oz, 0.f));
+    return make_float4(ox, oy, oz, 0.f);
+}
+
+// Skinning of the mesh vertices i0 + k stride (k < kLbsBatch, those below n):
+// the streaming 128-bit loads of all of them are issued first (the mesh is
+// read once per frame and bypasses L1), then each blends its frames (L2
+// resident) and is written with a streaming 128-bit store.
+constexpr int kLbsBatch = 4;
+__device__ __forceinline__ void lbs_vertices(int i0, int stride, int n, int ns, const float4 *__restrict__ rest,
+                                             const int4 *__restrict__ idx, const float4 *__restrict__ w,
+                                             const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
+{
+    float4 p[kLbsBatch], ww[kLbsBatch];
+    int4 id[kLbsBatch];
+#pragma unroll
+    for (int k = 0; k < kLbsBatch; ++k) {
+        const int i = i0 + k * stride;
+        if (i < n) {
+            p[k] = __ldcs(rest + i);
+            id[k] = __ldcs(idx + i);
+            ww[k] = __ldcs(w + i);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kLbsBatch; ++k) {
+        const int i = i0 + k * stride;
+        if (i < n) __stcs(out + i, lbs_blend(p[k], id[k], ww[k], ns, frames, err));
+    }
 }
 
 }  // namespace viper

@@ -143,6 +143,7 @@ struct viper_scene {
     // pinned, mapped host mirror of the device error word (read without a stream sync)
     int *h_err = nullptr;
     int *d_herr = nullptr;  // its device address
+    void *self_table = nullptr;  // one-scene table of the multi-scene kernels (graph path)
     // scratch for host-pointer skinning
     float4 *skin_buf = nullptr;
     size_t skin_cap = 0;
@@ -160,7 +161,9 @@ struct viper_scene {
 
 namespace viper {
 
-enum : int { PROF_NONE = 0, PROF_ROD = 1, PROF_CONTACT = 2, PROF_BROADPHASE = 3, PROF_LBS = 4, PROF_ELEM = 5 };
+enum : int {
+    PROF_NONE = 0, PROF_ROD = 1, PROF_CONTACT = 2, PROF_BROADPHASE = 3, PROF_LBS = 4, PROF_ELEM = 5, PROF_PAIRS = 6
+};
 
 // Brackets the launches issued during its lifetime with events when the scene
 // profiles kernel class `cls`.
@@ -192,6 +195,13 @@ int configure_rod_kernels(int smem_bytes);
 int scene_poll_latched(viper_scene *s);  // latched error of earlier frames as a VIPER_* code
 bool scene_contact_path(const viper_scene *s);
 int scene_decode_err(int e);
+int scene_alloc(viper_scene *s, size_t bytes, void **out);  // device memory owned by the scene
+// The graph path of a scene whose rods all fit the shared-memory kernels (and,
+// with pills, whose grid fits one CTA): one frame of the multi-scene kernels
+// for this scene alone, captured on its stream (batch.cu).
+bool self_batch_ok(const viper_scene *s);
+int self_batch_capture(viper_scene *s, float dt, int substeps, int iterations, cudaGraph_t *graph,
+                       long long *launches);
 int frame_configure(viper_scene *s);
 void launch_frame(viper_scene *s, int substeps, int iterations);
 

@@ -22,7 +22,7 @@ EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4
 FLAG_CONTACTS, FLAG_VOLUME = 1, 2
 SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
 SOLVER_AUTO = -1
-PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE = 0, 1, 2, 3, 4, 5
+PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE, PROF_PAIRS = 0, 1, 2, 3, 4, 5, 6
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
