@@ -462,7 +462,7 @@ def main():
 
     # ---- per-kernel-class device time (events around each launch inside the graph)
     classes = {"rod": V.PROF_ROD, "contact": V.PROF_CONTACT, "broadphase": V.PROF_BROADPHASE,
-               "lbs_gather": V.PROF_LBS, "elementwise": V.PROF_ELEMENTWISE}
+               "pairs": V.PROF_PAIRS, "lbs_gather": V.PROF_LBS, "elementwise": V.PROF_ELEMENTWISE}
     per_class = {}
     prof_frames = min(K, 20)
     for name, cls in classes.items():

@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(kElemThreads) batch_scatter_kernel(BatchArgs A
     }
 }
 
-// Candidate pairs, one warp per work unit of a grid cell (see emit_cell).
-__global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs A)
+// Candidate pairs, one warp per work unit: a 32-pill chunk against one
+// neighbour list when the grid came from batch_grid_kernel (see emit_chunk),
+// else a cell against one neighbour cell (see emit_cell).
+__global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs A, int chunked)
 {
     __shared__ BatchScene sb;
     int local, nblk;
@@ -192,8 +194,13 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     const int cells = grid_cells(P.grid, P.table);
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
-    for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
-        emit_cell<4>(P, G, u, start);
+    if (chunked) {
+        const int n = kEmitUnits * *P.n_chunks;
+        for (int u = local * kEmitWarpsB + wib; u < n; u += nblk * kEmitWarpsB) emit_chunk<4>(P, G, u, start);
+    } else {
+        for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
+            emit_cell<4>(P, G, u, start);
+    }
 }
 
 // One scene's broadphase grid by one CTA: bounding spheres and their bounds,
@@ -237,30 +244,41 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         atomicAdd(cnt + cell, 1);
     }
     __syncthreads();
-    // exclusive scan into cell_start, and into cnt as the running fill position of each cell
-    int carry = 0;
+    // exclusive scans of the counts (into cell_start, and into cnt as the running
+    // fill position of each cell) and of the 32-pill chunks per cell (into the
+    // pair search's work list chunk_of)
+    int carry = 0, ccarry = 0;
     for (int base = 0; base < cells; base += bd * kScanPerB) {
         const int b0 = base + t * kScanPerB;
-        int v[kScanPerB], sum = 0;
+        int v[kScanPerB], sum = 0, csum = 0;
 #pragma unroll
         for (int k = 0; k < kScanPerB; ++k) {
             // counts in shared memory, or in global memory written by atomics (read from L2)
             v[k] = (b0 + k < cells) ? (in_smem ? s_cells[b0 + k] : __ldcg(P.cell_count + b0 + k)) : 0;
             sum += v[k];
+            csum += (v[k] + 31) >> 5;
         }
-        int tot;
+        int tot, ctot;
         int off = block_excl_scan(sum, ws, &tot) + carry;
+        int coff = block_excl_scan(csum, ws, &ctot) + ccarry;
 #pragma unroll
         for (int k = 0; k < kScanPerB; ++k) {
             if (b0 + k < cells) {
                 P.cell_start[b0 + k] = off;
                 cnt[b0 + k] = off;
+                const int nch = (v[k] + 31) >> 5;
+                for (int h = 0; h < nch; ++h) P.chunk_of[coff + h] = make_int2(b0 + k, h);
+                coff += nch;
             }
             off += v[k];
         }
         carry += tot;
+        ccarry += ctot;
     }
-    if (t == 0) P.cell_start[cells] = carry;
+    if (t == 0) {
+        P.cell_start[cells] = carry;
+        *P.n_chunks = ccarry;
+    }
     __syncthreads();
     for (int g = t; g < ns; g += bd) {
         const int pos = atomicAdd(cnt + P.cell_of[g], 1);
@@ -532,7 +550,9 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
             go(PROF_BROADPHASE, [&] { launch(batch_scan_kernel, tot[K_SCAN], kScanThreadsB, 0, st, A); });
             go(PROF_BROADPHASE, [&] { launch(batch_scatter_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
         }
-        go(PROF_PAIRS, [&] { launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A); });
+        go(PROF_PAIRS, [&] {
+            launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A, fused_grid ? 1 : 0);
+        });
     };
     auto contact = [&]() {
         go(PROF_CONTACT, [&] { launch(batch_contact_kernel, tot[K_CONTACT], kElemThreads, 0, st, A); });

@@ -711,6 +711,8 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(P.spheres, pills ? ns : 1); A(P.bounds, 8); A(P.grid, 1);
     A(P.cell_of, pills ? ns : 1); A(P.cell_pills, pills ? ns : 1);
     A(P.cell_sph, pills ? ns : 1); A(P.cell_grp, pills ? ns : 1);
+    // at most one chunk per occupied cell plus one per 32 pills
+    A(P.chunk_of, pills ? ns + ns / 32 + 1 : 1); A(P.n_chunks, 1);
     A(P.cell_count, P.table); A(P.cell_start, P.table + 1);
     A(s->d_scan_tmp, 4096);
     A(P.bar, 4); A(P.tile_sums, 1024);

@@ -734,6 +734,92 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
     }
 }
 
+// Candidate pairs of one chunk of up to 32 pills of a cell (chunk_of[q] =
+// (cell, chunk)) with one neighbour list, by one warp: work unit u = 14 q + k
+// pairs the chunk with the cell's forward neighbour k < 13, or with the rest of
+// its own cell from the chunk on (k = 13).  Every pair of pills of neighbouring
+// cells is visited once (as in emit_cell), and no unit is larger than one
+// chunk against one neighbour cell, so the units are balanced across warps.
+// The chunk's pills sit one per lane; the neighbour's are loaded 32 at a time
+// and broadcast, STEP candidates per step.
+template <int STEP, class StartFn>
+__device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u, StartFn start)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int k = u % kEmitUnits;
+    const int2 ch = P.chunk_of[u / kEmitUnits];
+    const int c = ch.x;
+    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
+    const int o1 = min(o0 + 32, cend);
+    int d0, d1;
+    if (k == 13) {  // the own cell from this chunk on: pairs with pb > pa
+        d0 = o0;
+        d1 = cend;
+    } else {
+        int dx, dy, dz;
+        if (k < 9) {
+            dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
+        } else if (k < 12) {
+            dx = k - 10; dy = 1; dz = 0;
+        } else {
+            dx = 1; dy = 0; dz = 0;
+        }
+        const int ix = c % G.dim[0], iy = (c / G.dim[0]) % G.dim[1], iz = c / (G.dim[0] * G.dim[1]);
+        const int x = ix + dx, y = iy + dy, z = iz + dz;
+        if (x < 0 || x >= G.dim[0] || y < 0 || y >= G.dim[1] || z >= G.dim[2]) return;
+        const int d = x + G.dim[0] * (y + G.dim[1] * z);
+        d0 = start(d);
+        d1 = start(d + 1);
+    }
+    if (d0 >= d1) return;  // uniform over the warp
+    const int pa = o0 + lane;
+    const bool own = pa < o1;
+    const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ga = own ? P.cell_grp[pa] : 0;
+    for (int cb = d0; cb < d1; cb += 32) {
+        const int q = cb + lane;
+        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cg = 0;
+        if (q < d1) {
+            cs = P.cell_sph[q];
+            cg = P.cell_grp[q];
+        }
+        const int m = min(32, d1 - cb);
+        for (int j0 = 0; j0 < m; j0 += STEP) {
+            bool hit[STEP];
+#pragma unroll
+            for (int t = 0; t < STEP; ++t) {
+                const int j = j0 + t;  // past m: no candidate (j & 31 is still a valid source lane)
+                float4 sj;
+                sj.x = __shfl_sync(full, cs.x, j & 31);
+                sj.y = __shfl_sync(full, cs.y, j & 31);
+                sj.z = __shfl_sync(full, cs.z, j & 31);
+                sj.w = __shfl_sync(full, cs.w, j & 31);
+                const int gj = __shfl_sync(full, cg, j & 31);
+                hit[t] = j < m && own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
+            }
+#pragma unroll
+            for (int t = 0; t < STEP; ++t) {
+                const unsigned hm = __ballot_sync(full, hit[t]);
+                if (hm) {
+                    int out = 0;
+                    if (lane == 0) out = atomicAdd(P.npairs, __popc(hm));
+                    out = __shfl_sync(full, out, 0);
+                    if (hit[t]) {
+                        const int idx = out + __popc(hm & ((1u << lane) - 1u));
+                        if (idx < P.max_pairs) {
+                            const int a = P.cell_pills[pa], b = P.cell_pills[cb + j0 + t];
+                            P.pairs[idx] = make_int2(min(a, b), max(a, b));
+                            if (P.lam_pair) P.lam_pair[idx] = 0.f;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ================================================================ contacts
 __device__ __forceinline__ void acc_add(const Params &P, int v, V3 d, float ds)
 {
