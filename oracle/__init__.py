@@ -35,6 +35,7 @@ class _Desc(C.Structure):
         ("pin_vertex", _ip), ("pin_bone", _ip), ("pin_offset", _dp), ("n_bones", C.c_int),
         ("bone_quat", _dp), ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("contacts", C.c_int), ("volume", C.c_int),
+        ("surface_bending", C.c_int),
     ]
 
 
@@ -80,6 +81,10 @@ def lib():
         L.vo_rest.argtypes = [C.c_void_p, _dp, _dp]
         L.vo_colouring.argtypes = [C.c_void_p, _ip, _ip]
         L.vo_constraint_rms.argtypes = [C.c_void_p, _dp]
+        L.vo_laplacian_constraint.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                              _dp, _dp]
+        L.vo_laplacian_compliance.restype = C.c_double
+        L.vo_laplacian_compliance.argtypes = [C.c_void_p, C.c_int]
         _lib = L
     return _lib
 
@@ -142,6 +147,7 @@ class OracleScene:
         desc.contact_compliance = float(scene.contact_compliance)
         desc.contacts = int(bool(scene.contacts))
         desc.volume = int(bool(scene.volume))
+        desc.surface_bending = int(bool(getattr(scene, "surface_bending", False)))
         h = L.vo_create(C.byref(desc))
         if not h:
             raise ValueError("vo_create rejected the scene")
@@ -240,10 +246,22 @@ class OracleScene:
         lib().vo_colouring(self._h, sc.ctypes.data_as(_ip), vc.ctypes.data_as(_ip))
         return sc, vc
 
+    def laplacian_compliance(self, i):
+        return float(lib().vo_laplacian_compliance(self._h, int(i)))
+
     def constraint_rms(self):
         out = np.zeros(6)
         lib().vo_constraint_rms(self._h, _d(out)[1])
         return dict(zip(["S", "V", "X", "G", "B", "Vb"], out))
+
+
+def laplacian_constraint(s_prev, s, s_next, la, lb):
+    """Surface-bending constraint value and its three scale Jacobian entries."""
+    c = np.zeros(1)
+    j = np.zeros(3)
+    lib().vo_laplacian_constraint(float(s_prev), float(s), float(s_next), float(la), float(lb), _d(c)[1],
+                                  _d(j)[1])
+    return float(c[0]), j
 
 
 def broadphase_f32(rod_offsets, group, x4, rbar, brute=False):

@@ -53,6 +53,8 @@ struct vo_scene {
     double *xp, *sp, *qp;
     double *lam_seg;   /* 6 per segment: S(3), V, X, G */
     double *lam_vtx;   /* 5 per vertex: B(3), Vb(2)    */
+    double *lam_lap;   /* 1 per vertex: surface bending */
+    int surface;
     double *lam_pair, *lam_plane;
     int *pairs;
     int npairs, cap_pairs;
@@ -474,6 +476,57 @@ static void project_vertex(vo_scene *S, int i, int kind, double h)
 }
 
 /*
+ * Surface bending (Sec. 5, E_bending): the second-order variation of the
+ * scale, C = lap(s) - lap(s_bar) at an interior vertex, with s_bar = 1 so that
+ * lap(s_bar) = 0.  The discrete Laplacian of Sec. 7.5 is a difference of the
+ * two adjacent first differences; reading: it is divided once more by the
+ * vertex length lv = (l_a + l_b)/2, which makes it the second derivative
+ * (exact for quadratic profiles):
+ *   lap(s) = ((s_next - s)/l_b - (s - s_prev)/l_a) / lv.
+ */
+int vo_laplacian_constraint(double s_prev, double s, double s_next, double la, double lb, double *C,
+                            double *J)
+{
+    double lv = 0.5 * (la + lb);
+    *C = ((s_next - s) / lb - (s - s_prev) / la) / lv;
+    J[0] = 1.0 / (la * lv);
+    J[1] = -(1.0 / la + 1.0 / lb) / lv;
+    J[2] = 1.0 / (lb * lv);
+    return 1;
+}
+
+/* Stiffness: the energy density 1/4 pi r^4 (k_x + k_y) of Sec. 5 with
+ * k_x = k_y = k_b (the bend family), times the element length lv. */
+double vo_laplacian_compliance(const vo_scene *S, int i)
+{
+    if (i < 0 || i >= S->nv) return 0.0;
+    int r = S->rod_of_v[i];
+    if (i == S->off[r] || i == S->off[r + 1] - 1) return 0.0;
+    int gb = i - r, ga = gb - 1;
+    double lv = 0.5 * (S->lbar[ga] + S->lbar[gb]);
+    double rb = S->rbar[i];
+    double K = 0.25 * VO_PI * rb * rb * rb * rb * (2.0 / S->cb[r]) * lv;
+    return 1.0 / K;
+}
+
+static void project_laplacian(vo_scene *S, int i, double h)
+{
+    int r = S->rod_of_v[i];
+    int gb = i - r, ga = gb - 1;
+    double C, J[3];
+    vo_laplacian_constraint(S->s[i - 1], S->s[i], S->s[i + 1], S->lbar[ga], S->lbar[gb], &C, J);
+    double alpha = vo_laplacian_compliance(S, i);
+    blk_t b[3];
+    for (int k = 0; k < 3; ++k) {
+        b[k].type = BLK_SCALE;
+        b[k].idx = i - 1 + k;
+        b[k].J[0] = J[k];
+    }
+    xpbd_solve(S, 1, &C, b, 3, &alpha, S->lam_lap + i, h);
+    apply_blocks(S, b, 3);
+}
+
+/*
  * Constraint projection, Gauss-Seidel over four colours (Sec. 6 allows block
  * Jacobi or Gauss-Seidel; reading: even/odd colouring along each rod):
  *   colour 0: segments with even local index   -> S, V, X, G in this order
@@ -494,12 +547,17 @@ static void colour_sweep(vo_scene *S, int colour, double h)
                 project_segment(S, g, 2, h);
                 project_segment(S, g, 3, h);
             }
-        } else {
+        } else if (colour < 4) {
             int start = (colour == 2) ? 2 : 1;
             for (int i = start; i < n - 1; i += 2) {
                 project_vertex(S, v0 + i, 0, h);
                 if (S->volume) project_vertex(S, v0 + i, 1, h);
             }
+        } else {
+            /* surface bending couples three consecutive scales: interior
+             * vertices i with i mod 3 == colour - 4 touch disjoint scales */
+            for (int i = 1; i < n - 1; ++i)
+                if (i % 3 == colour - 4) project_laplacian(S, v0 + i, h);
         }
     }
 }
@@ -958,6 +1016,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->ccomp = d->contact_compliance;
     S->contacts = d->contacts;
     S->volume = d->volume;
+    S->surface = d->surface_bending;
 
     /* state starts at rest (Sec. 4: the rest pose is the initial pose) */
     S->x = xcalloc(3 * (size_t)nv, sizeof(double));
@@ -974,6 +1033,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->qp = xcalloc(4 * (size_t)ns, sizeof(double));
     S->lam_seg = xcalloc(6 * (size_t)ns, sizeof(double));
     S->lam_vtx = xcalloc(5 * (size_t)nv, sizeof(double));
+    S->lam_lap = xcalloc((size_t)nv, sizeof(double));
     S->lam_plane = xcalloc((size_t)nv * (size_t)(S->np ? S->np : 1), sizeof(double));
     S->acc = xcalloc(4 * (size_t)nv, sizeof(double));
     S->cnt = xcalloc((size_t)nv, sizeof(int));
@@ -987,7 +1047,7 @@ void vo_destroy(vo_scene *S)
                     S->obar, S->minv, S->sinv, S->mseg, S->rm, S->cs, S->cb, S->cv, S->group,
                     S->pin_of_v, S->pin_bone, S->pin_off, S->bq0, S->bt0, S->bq1, S->bt1, S->bq,
                     S->bt, S->planes, S->x, S->s, S->v, S->sd, S->q, S->w, S->xp, S->sp, S->qp,
-                    S->lam_seg, S->lam_vtx, S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
+                    S->lam_seg, S->lam_vtx, S->lam_lap, S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(S);
 }
@@ -1100,6 +1160,7 @@ int vo_step(vo_scene *S, double dt, int substeps, int iterations)
         /* multipliers start at zero each substep (App. C: lambda^0 = 0) */
         memset(S->lam_seg, 0, sizeof(double) * 6 * (size_t)S->ns);
         memset(S->lam_vtx, 0, sizeof(double) * 5 * (size_t)S->nv);
+        memset(S->lam_lap, 0, sizeof(double) * (size_t)S->nv);
         memset(S->lam_plane, 0, sizeof(double) * (size_t)S->nv * (size_t)(S->np ? S->np : 1));
         /* collision detection on the predicted state (Sec. 7) */
         S->npairs = 0;
@@ -1109,6 +1170,8 @@ int vo_step(vo_scene *S, double dt, int substeps, int iterations)
         }
         for (int it = 0; it < iterations; ++it) {
             for (int c = 0; c < 4; ++c) colour_sweep(S, c, h);
+            if (S->surface)
+                for (int c = 4; c < 7; ++c) colour_sweep(S, c, h);
             if ((S->contacts && S->npairs > 0) || S->np > 0) contact_pass(S, h);
         }
         /* velocity update: reading (not written out in the paper): the

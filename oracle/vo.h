@@ -45,6 +45,7 @@ typedef struct vo_desc {
     double contact_compliance;
     int contacts;                /* pill-pill contacts on/off                     */
     int volume;                  /* volume constraints on/off                     */
+    int surface_bending;         /* scale-Laplacian constraints on/off            */
 } vo_desc;
 
 vo_scene *vo_create(const vo_desc *d);
@@ -73,6 +74,13 @@ int vo_last_pairs(const vo_scene *s, int *pairs, int cap);
  * Returns the pair count (pairs filled up to cap), sorted lexicographically. */
 int vo_broadphase_f32(int n_rods, const int *rod_offsets, const int *group,
                       const float *x4, const float *rbar, int brute, int *pairs, int cap);
+/* Surface-bending constraint at an interior vertex from its scale and its
+ * neighbours' (s_prev, s, s_next) and the adjacent rest lengths: the value C
+ * and the three scale Jacobian entries J[3] (s_prev, s, s_next). */
+int vo_laplacian_constraint(double s_prev, double s, double s_next, double la, double lb, double *C,
+                            double *J);
+/* Compliance of the surface-bending constraint at vertex i (0 at rod ends). */
+double vo_laplacian_compliance(const vo_scene *s, int i);
 /* Barycentric coordinate of the closest sphere of a tapered capsule (App. D). */
 double vo_pill_project(const double *c1, double r1, const double *c2, double r2,
                        const double *x);

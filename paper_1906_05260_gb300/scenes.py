@@ -101,6 +101,7 @@ class Scene:
     init_pos: Optional[np.ndarray] = None
     init_quat: Optional[np.ndarray] = None
     mesh: Optional[Mesh] = None
+    surface_bending: bool = False     # scale-Laplacian constraints (Sec. 5, E_bending)
 
     @property
     def n_rods(self) -> int:

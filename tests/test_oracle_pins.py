@@ -650,3 +650,84 @@ def test_colouring_separates_shared_dofs():
         # adjacent interior vertices share a segment rotation -> different colours
         assert (inner[1:] != inner[:-1]).all()
         assert set(np.unique(inner)).issubset({2, 3})
+
+
+# --------------------------------------------------------------------------
+# Surface bending (Sec. 5, E_bending; discrete Laplacian of Sec. 7.5)
+# --------------------------------------------------------------------------
+
+def test_surface_bending_laplacian_is_exact_for_quadratic_profiles():
+    """The discrete scale Laplacian at a vertex with unequal neighbouring
+    segments equals the second derivative of any quadratic profile."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        la, lb = rng.uniform(0.002, 0.05, 2)
+        a, b, c = rng.normal(size=3)
+        prof = lambda z: a + b * z + c * z * z
+        C, _ = oracle.laplacian_constraint(prof(-la), prof(0.0), prof(lb), la, lb)
+        np.testing.assert_allclose(C, 2 * c, rtol=1e-8, atol=1e-8)
+        # a linear profile has no curvature
+        C0, _ = oracle.laplacian_constraint(a - b * la, a, a + b * lb, la, lb)
+        assert abs(C0) < 1e-9 * (1 + abs(b) / min(la, lb))
+
+
+def test_surface_bending_jacobian_matches_finite_differences():
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        la, lb = rng.uniform(0.005, 0.03, 2)
+        s = rng.uniform(0.7, 1.3, 3)
+        _, J = oracle.laplacian_constraint(*s, la, lb)
+        eps = 1e-6
+        for k in range(3):
+            sp, sm = s.copy(), s.copy()
+            sp[k] += eps
+            sm[k] -= eps
+            fd = (oracle.laplacian_constraint(*sp, la, lb)[0] - oracle.laplacian_constraint(*sm, la, lb)[0]) / (2 * eps)
+            np.testing.assert_allclose(J[k], fd, rtol=1e-6)
+
+
+def test_surface_bending_compliance_equals_integrated_energy_coefficient():
+    """K per unit length equals the disc integral of the bending-approximation
+    integrand ||R^T lap(phi) - Rbar^T lap(phibar)||_Kb^2 of Sec. 5 for a unit
+    scale Laplacian: (k_x x^2 + k_y y^2) over the disc, k_x = k_y = 1/c_b."""
+    r, l, cb = 0.03, 0.01, 2e-6
+    sc = dataclasses.replace(_one_rod_scene(r=r, lbar=l, cb=cb), surface_bending=True)
+    o = oracle.OracleScene(sc)
+    X, Y, W = _disc_quadrature(r)
+    kb = 1 / cb
+    K_L = (kb * (X ** 2 + Y ** 2) * W).sum()
+    np.testing.assert_allclose(1 / (o.laplacian_compliance(1) * l), K_L, rtol=1e-10)
+    assert o.laplacian_compliance(0) == 0.0 and o.laplacian_compliance(sc.nv - 1) == 0.0
+
+
+def _scale_bump_rod(surface):
+    # soft first-order scale terms (X, G use the stretch compliance), stiff bending
+    sc = _one_rod_scene(n=12, r=0.02, lbar=0.01, cs=1e-2, cb=1e-9, cv=1e-2)
+    sc = dataclasses.replace(sc, surface_bending=surface, substeps=4, iterations=8, volume=False)
+    o = oracle.OracleScene(sc)
+    s = np.ones(sc.nv)
+    s[6] = 1.3  # a sharp bump in the middle of a straight rod
+    o.set_state(s=s)
+    return sc, o
+
+
+def _laplacian_residual(s, lb):
+    out = []
+    for i in range(1, len(s) - 1):
+        out.append(oracle.laplacian_constraint(s[i - 1], s[i], s[i + 1], lb[i - 1], lb[i])[0])
+    return np.sqrt(np.mean(np.square(out)))
+
+
+def test_surface_bending_smooths_a_scale_bump():
+    """With the constraint on, the scale profile's Laplacian falls faster than
+    with the first-order terms (cross-section, scale gradient) alone; it acts on
+    scales only, so positions and frames of the straight rod stay put."""
+    res = {}
+    for surface in (False, True):
+        sc, o = _scale_bump_rod(surface)
+        o.step(sc.dt, sc.substeps, sc.iterations)
+        st = o.get_state()
+        lb, _ = o.rest()
+        res[surface] = _laplacian_residual(st["s"], lb)
+        np.testing.assert_allclose(st["x"], sc.rest_pos, atol=1e-9)
+    assert res[True] < 0.5 * res[False], res
