@@ -52,6 +52,7 @@ extern "C" {
 
 #define VIPER_FLAG_CONTACTS 1 /* pill-pill contacts (Sec. 7.1, 7.2)                */
 #define VIPER_FLAG_VOLUME 2   /* volume constraints (Sec. 5 "Volume potential")    */
+#define VIPER_FLAG_SURFACE_BENDING 4 /* scale-Laplacian constraints (Sec. 5 E_bending) */
 
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
 #define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,

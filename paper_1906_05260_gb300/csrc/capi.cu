@@ -163,15 +163,20 @@ Schedule build_schedule(const std::vector<int> &rod_n, int block_warps, int resi
 }
 
 // Build the colour lists (internal ids) for the internal rods [r0, r1).
-void colour_lists(const std::vector<int> &int_off, int r0, int r1, std::vector<int> lists[4])
+// Colour lists of the plain path: segments (0, 1: even / odd local index),
+// interior vertices (2, 3: even / odd), surface bending (4 + i mod 3).
+void colour_lists(const std::vector<int> &int_off, int r0, int r1, std::vector<int> lists[7])
 {
-    for (int c = 0; c < 4; ++c) lists[c].clear();
+    for (int c = 0; c < 7; ++c) lists[c].clear();
     for (int r = r0; r < r1; ++r) {
         int v0 = int_off[r], n = int_off[r + 1] - v0, s0 = v0 - r;
         for (int j = 0; j < n - 1; ++j) lists[j & 1].push_back(s0 + j);
         for (int i = 1; i < n - 1; ++i) lists[(i % 2 == 0) ? 2 : 3].push_back(v0 + i);
+        for (int i = 1; i < n - 1; ++i) lists[4 + i % 3].push_back(v0 + i);
     }
 }
+
+int n_colours(const viper_scene *s) { return s->P.surface ? 7 : 4; }
 
 // (Re)build the internal layout and upload every internal-order table.  The
 // state is carried across in caller order through the staging buffer.
@@ -225,7 +230,7 @@ int rebuild(viper_scene *s, bool keep_state)
     if (configure_rod_kernels(s->smem_full) != 0) return VIPER_EINVAL;
 
     // internal-order tables
-    std::vector<float4> RV0(nv), RV1(nv), RS0(ns), LQ(ns), LC(ns);
+    std::vector<float4> RV0(nv), RV1(nv), RV2(nv), RS0(ns), LQ(ns), LC(ns);
     std::vector<float2> RS1(ns);
     std::vector<int> seg_v0(ns), vtx_seg(nv), seg_group(ns), rod_of_v(nv);
     std::vector<float4> rod_origin(nr);
@@ -238,6 +243,7 @@ int rebuild(viper_scene *s, bool keep_state)
             rod_of_v[vi] = k;
             RV0[vi] = s->u_RV0[s->h_vperm[vi]];
             RV1[vi] = s->u_RV1[s->h_vperm[vi]];
+            RV2[vi] = s->u_RV2[s->h_vperm[vi]];
             vtx_seg[vi] = vi - k;
         }
         for (int j = 0; j < n - 1; ++j) {
@@ -255,6 +261,7 @@ int rebuild(viper_scene *s, bool keep_state)
     if ((rc = upload(s, const_cast<float4 *>(P.RV0), RV0))) return rc;
     P.bp_rbar = reinterpret_cast<const float *>(P.RV0) + 3;  // RV0[v].w = rest radius
     if ((rc = upload(s, const_cast<float4 *>(P.RV1), RV1))) return rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.RV2), RV2))) return rc;
     if ((rc = upload(s, const_cast<float4 *>(P.RS0), RS0))) return rc;
     if ((rc = upload(s, const_cast<float2 *>(P.RS1), RS1))) return rc;
     if ((rc = upload(s, s->LQ, LQ))) return rc;
@@ -274,19 +281,19 @@ int rebuild(viper_scene *s, bool keep_state)
     if (nslots > (size_t)P.slot_stride || !P.items) {
         if ((rc = dalloc(s, const_cast<int4 **>(&P.items), std::max<size_t>(S.items.size(), 1) + nv))) return rc;
         if ((rc = dalloc(s, const_cast<int2 **>(&P.slots), std::max<size_t>(nslots, 1) + 2 * (size_t)nv))) return rc;
-        if ((rc = dalloc(s, &P.slot_lam, 22 * (std::max<size_t>(nslots, 1) + 2 * (size_t)nv)))) return rc;
+        if ((rc = dalloc(s, &P.slot_lam, kSlotLam * (std::max<size_t>(nslots, 1) + 2 * (size_t)nv)))) return rc;
         P.slot_stride = (int)(std::max<size_t>(nslots, 1) + 2 * (size_t)nv);
     }
     if ((rc = upload(s, const_cast<int4 *>(P.items), S.items))) return rc;
     if ((rc = upload(s, const_cast<int2 *>(P.slots), S.slots))) return rc;
 
     // colour lists: all rods on the plain path, streamed rods on the batched path
-    std::vector<int> lists[4];
+    std::vector<int> lists[7];
     if (s->mode == VIPER_SOLVER_PLAIN)
         colour_lists(s->h_int_off, 0, nr, lists);
     else
         colour_lists(s->h_int_off, S.n_resident_rods, nr, lists);
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 7; ++c) {
         s->col_n[c] = (int)lists[c].size();
         if ((rc = upload(s, s->col_list[c], lists[c]))) return rc;
     }
@@ -333,7 +340,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
             launch_predict(s, 0, nv, 0, ns, cp);
             if (pills) launch_broadphase(s);
             for (int it = 0; it < iterations; ++it) {
-                for (int c = 0; c < 4; ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
+                for (int c = 0; c < n_colours(s); ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
                 if (cp) {
                     launch_contacts(s);
                     launch_apply(s, 0, nv);
@@ -345,7 +352,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
             if (s->resident_nv < nv) {
                 launch_predict(s, s->resident_nv, nv, s->resident_ns, ns, false);
                 for (int it = 0; it < iterations; ++it)
-                    for (int c = 0; c < 4; ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
+                    for (int c = 0; c < n_colours(s); ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
                 launch_finish(s, s->resident_nv, nv, s->resident_ns, ns, false);
             }
         } else {
@@ -369,7 +376,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
                 if (it == 0 && forked) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
                 if (s->resident_nv < nv) {
                     if (it > 0) launch_apply(s, s->resident_nv, nv);
-                    for (int c = 0; c < 4; ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
+                    for (int c = 0; c < n_colours(s); ++c) launch_colour(s, c, s->col_list[c], s->col_n[c]);
                 }
                 launch_contacts(s);
             }
@@ -618,6 +625,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     }
     s->u_RV0.assign(nv, make_float4(0, 0, 0, 0));
     s->u_RV1.assign(nv, make_float4(0, 0, 0, 0));
+    s->u_RV2.assign(nv, make_float4(0, 0, 0, 0));
     s->u_RS0.resize(ns);
     s->u_RS1.resize(ns);
     s->u_LQ.resize(ns);
@@ -663,6 +671,10 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
                 double r4l = kPi * rb * rb * rb * rb * lv;
                 aB = cb / r4l;          // compliance (4, 4, 2) * aB: H = pi r^4 k_b diag(1/4, 1/4, 1/2)
                 aVb = cv / (0.25 * r4l);
+                // surface bending: K = 1/4 pi r^4 (k_x + k_y) lv with k_x = k_y = 1/c_b (Sec. 5 E_bending);
+                // Laplacian ((s_next - s)/l_b - (s - s_prev)/l_a)/lv
+                s->u_RV2[v] = make_float4((float)(1.0 / (lbar[ga] * lv)), (float)(1.0 / (lbar[gb] * lv)),
+                                          (float)(2.0 * cb / r4l), 0.f);
             }
             float wx = pin_of_v[v] >= 0 ? -(float)(pin_of_v[v] + 1) : (float)(1.0 / mass[v]);
             s->u_RV0[v] = make_float4((float)ob[0], (float)ob[1], (float)ob[2], (float)d->radius[v]);
@@ -680,6 +692,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.gy = (float)d->gravity[1];
     P.gz = (float)d->gravity[2];
     P.volume = (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
+    P.surface = (d->flags & VIPER_FLAG_SURFACE_BENDING) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
     P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0;
@@ -690,14 +703,15 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     if ((rc = dalloc(s, const_cast<type **>(&(ptr)), (size_t)(n)))) return fail(rc)
     A(P.X, nv); A(P.V, nv); A(P.Xp, nv); A(P.Xpred, nv);
     A(P.Q, ns); A(P.W, ns); A(P.Qp, ns);
-    AC(P.RV0, float4, nv); AC(P.RV1, float4, nv); AC(P.RS0, float4, ns); AC(P.RS1, float2, ns);
+    AC(P.RV0, float4, nv); AC(P.RV1, float4, nv); AC(P.RV2, float4, nv);
+    AC(P.RS0, float4, ns); AC(P.RS1, float2, ns);
     AC(P.seg_v0, int, ns); AC(P.vtx_seg, int, nv); AC(P.seg_group, int, ns);
     AC(P.rod_of_v, int, nv); AC(P.rod_origin, float4, nr);
     A(s->LQ, ns); A(s->LC, ns); A(s->frames, 3 * (size_t)ns);
     A(s->d_vperm, nv); A(s->d_sperm, ns); A(s->d_sinv, ns);
-    A(P.lamS, ns); A(P.lamS2, ns); A(P.lamB, nv); A(P.lamB2, nv);
+    A(P.lamS, ns); A(P.lamS2, ns); A(P.lamB, nv); A(P.lamB2, nv); A(P.lamL, nv);
     A(s->stage4, std::max(nv, ns)); A(s->stage1, nv);
-    for (int c = 0; c < 4; ++c) A(s->col_list[c], std::max(nv, ns));
+    for (int c = 0; c < 7; ++c) A(s->col_list[c], std::max(nv, ns));
     A(P.err, 1);
     AC(P.pins, float4, 2 * std::max(d->n_pins, 1));
     AC(P.bq0, float4, std::max(d->n_bones, 1)); AC(P.bq1, float4, std::max(d->n_bones, 1));

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
         }
         if (iters > 0 && owner) {
             __syncthreads();
-            sweep(sX, sQ, R, L, P.inv_h2, vol);
+            sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
             if (BARRIERS)
                 for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
         }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
             if (it + 1 < iters) {
                 if (owner) {
                     __syncthreads();
-                    sweep(sX, sQ, R, L, P.inv_h2, vol);
+                    sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
                     if (BARRIERS)
                         for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
                 }

@@ -148,6 +148,7 @@ __device__ __forceinline__ void predict_vertex_at(const Params &P, int v, float 
     if (plain_lam) {
         P.lamB[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         P.lamB2[v] = 0.f;
+        P.lamL[v] = 0.f;
     }
     for (int k = 0; k < P.n_planes; ++k) P.lam_plane[(size_t)v * P.n_planes + k] = 0.f;
 }
@@ -183,20 +184,21 @@ __device__ __forceinline__ void finish_segment_at(const Params &P, int g)
     P.W[g] = omega_of(P, q, P.Qp[g]);
 }
 
-// Multipliers of one slot kept across launches (contact path): 22 floats.
+// Multipliers of one slot kept across launches (contact path): 24 floats.
 struct SlotLam {
     float4 s0, s1, b1, b2;
     float2 x0, x1;
     float v1, v2;
+    float l1, l2;  // surface bending at vertices 2p+1, 2p+2
 };
 
 __device__ __forceinline__ void lam_load(const Params &P, int slot, SlotLam &L)
 {
     const float *b = P.slot_lam + slot;
     const int st = P.slot_stride;
-    float t[22];
+    float t[kSlotLam];
 #pragma unroll
-    for (int k = 0; k < 22; ++k) t[k] = b[k * st];
+    for (int k = 0; k < kSlotLam; ++k) t[k] = b[k * st];
     L.s0 = make_float4(t[0], t[1], t[2], t[3]);
     L.s1 = make_float4(t[4], t[5], t[6], t[7]);
     L.b1 = make_float4(t[8], t[9], t[10], t[11]);
@@ -205,16 +207,19 @@ __device__ __forceinline__ void lam_load(const Params &P, int slot, SlotLam &L)
     L.x1 = make_float2(t[18], t[19]);
     L.v1 = t[20];
     L.v2 = t[21];
+    L.l1 = t[22];
+    L.l2 = t[23];
 }
 
 __device__ __forceinline__ void lam_store(const Params &P, int slot, const SlotLam &L)
 {
     float *b = P.slot_lam + slot;
     const int st = P.slot_stride;
-    const float t[22] = {L.s0.x, L.s0.y, L.s0.z, L.s0.w, L.s1.x, L.s1.y, L.s1.z, L.s1.w, L.b1.x, L.b1.y, L.b1.z,
-                         L.b1.w, L.b2.x, L.b2.y, L.b2.z, L.b2.w, L.x0.x, L.x0.y, L.x1.x, L.x1.y, L.v1, L.v2};
+    const float t[kSlotLam] = {L.s0.x, L.s0.y, L.s0.z, L.s0.w, L.s1.x, L.s1.y, L.s1.z, L.s1.w,
+                               L.b1.x, L.b1.y, L.b1.z, L.b1.w, L.b2.x, L.b2.y, L.b2.z, L.b2.w,
+                               L.x0.x, L.x0.y, L.x1.x, L.x1.y, L.v1, L.v2, L.l1, L.l2};
 #pragma unroll
-    for (int k = 0; k < 22; ++k) b[k * st] = t[k];
+    for (int k = 0; k < kSlotLam; ++k) b[k * st] = t[k];
 }
 
 
@@ -224,9 +229,11 @@ __device__ __forceinline__ void lam_store(const Params &P, int slot, const SlotL
 struct SlotRest {
     bool active, has0, has1, hasv2;
     int lv, ls;  // local first vertex / segment of the slot inside the item
+    int gv;      // global index of vertex 2p
+    int p2;      // 2p: rod-local index of vertex 2p
     float4 rs00, rs01, rv01, rv02;
     float2 rs10, rs11;
-    float w0, w1, w2, ws0, ws1, ws2, aB1, aV1, aB2, aV2, l2, im2;
+    float w0, w1, w2, ws0, ws1, ws2, ws3, aB1, aV1, aB2, aV2, l2, im2;
 };
 
 __device__ __forceinline__ void load_slot(const Params &P, int4 item, int2 sd, SlotRest &R)
@@ -237,6 +244,8 @@ __device__ __forceinline__ void load_slot(const Params &P, int4 item, int2 sd, S
     R.lv = vb + 2 * p;
     R.ls = sb + 2 * p;
     const int gv = item.x + R.lv, gs = item.z + R.ls;
+    R.gv = gv;
+    R.p2 = 2 * p;
     R.has0 = R.active;
     R.has1 = R.active && (2 * p + 1 <= N - 2);   // segment 2p+1 and vertex 2p+1
     R.hasv2 = R.active && (2 * p + 2 <= N - 2);  // vertex 2p+2
@@ -246,7 +255,7 @@ __device__ __forceinline__ void load_slot(const Params &P, int4 item, int2 sd, S
     R.rv02 = R.rv01;
     R.rs10 = make_float2(0.f, 0.f);
     R.rs11 = R.rs10;
-    R.w0 = R.w1 = R.w2 = R.ws0 = R.ws1 = R.ws2 = 0.f;
+    R.w0 = R.w1 = R.w2 = R.ws0 = R.ws1 = R.ws2 = R.ws3 = 0.f;
     R.aB1 = R.aV1 = R.aB2 = R.aV2 = 0.f;
     R.l2 = 1.f;
     R.im2 = 0.f;
@@ -276,6 +285,7 @@ __device__ __forceinline__ void load_slot(const Params &P, int4 item, int2 sd, S
         R.l2 = r.x;
         R.im2 = r.y;
         R.rv02 = P.RV0[gv + 2];
+        if (P.surface) R.ws3 = P.RV1[gv + 3].y;
     }
 }
 
@@ -284,12 +294,15 @@ __device__ __forceinline__ void zero_lam(SlotLam &L)
     L.s0 = L.s1 = L.b1 = L.b2 = make_float4(0.f, 0.f, 0.f, 0.f);
     L.x0 = L.x1 = make_float2(0.f, 0.f);
     L.v1 = L.v2 = 0.f;
+    L.l1 = L.l2 = 0.f;
 }
 
-// One sweep of the four colours over the item staged in shared memory.  Every
-// thread of the CTA must call it (it synchronises the CTA between colours).
+// One sweep of the four colours over the item staged in shared memory, then,
+// with surface bending (RV2 non-null), three colours of interior vertices
+// i mod 3 (each couples scales i-1, i, i+1).  Every thread of the CTA must call
+// it (it synchronises the CTA between colours).
 __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L, float inv_h2,
-                                      bool vol)
+                                      bool vol, const float4 *__restrict__ RV2 = nullptr)
 {
     const int lv = R.lv, ls = R.ls;
     // colour 0: even segments
@@ -332,6 +345,25 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
         reinterpret_cast<float *>(sX + lv + 1)[3] = s;
     }
     __syncthreads();
+    if (RV2) {
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            if (R.has1 && (R.p2 + 1) % 3 == c) {  // vertex 2p+1: scales 2p, 2p+1, 2p+2
+                float sp = sX[lv].w, s = sX[lv + 1].w, sn = sX[lv + 2].w;
+                project_laplacian(sp, s, sn, R.ws0, R.ws1, R.ws2, __ldg(RV2 + R.gv + 1), L.l1, inv_h2);
+                reinterpret_cast<float *>(sX + lv)[3] = sp;
+                reinterpret_cast<float *>(sX + lv + 1)[3] = s;
+                reinterpret_cast<float *>(sX + lv + 2)[3] = sn;
+            } else if (R.hasv2 && (R.p2 + 2) % 3 == c) {  // vertex 2p+2: scales 2p+1, 2p+2, 2p+3
+                float sp = sX[lv + 1].w, s = sX[lv + 2].w, sn = sX[lv + 3].w;
+                project_laplacian(sp, s, sn, R.ws1, R.ws2, R.ws3, __ldg(RV2 + R.gv + 2), L.l2, inv_h2);
+                reinterpret_cast<float *>(sX + lv + 1)[3] = sp;
+                reinterpret_cast<float *>(sX + lv + 2)[3] = s;
+                reinterpret_cast<float *>(sX + lv + 3)[3] = sn;
+            }
+            __syncthreads();
+        }
+    }
 }
 
 // One work item of the shared-memory rod solve: a CTA stages the item's float4
@@ -383,7 +415,7 @@ __device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, boo
     __syncthreads();
     const bool vol = P.volume != 0;
 #pragma unroll 1
-    for (int k = 0; k < n_iter; ++k) sweep(sX, sQ, R, L, P.inv_h2, vol);
+    for (int k = 0; k < n_iter; ++k) sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
     if (!FULL && R.active) lam_store(P, slot, L);
 
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
@@ -459,7 +491,7 @@ __device__ __forceinline__ void rod_item_first(const Params &P, int b, bool fini
     SlotLam L;
     zero_lam(L);
     __syncthreads();
-    sweep(sX, sQ, R, L, P.inv_h2, P.volume != 0);
+    sweep(sX, sQ, R, L, P.inv_h2, P.volume != 0, P.surface ? P.RV2 : nullptr);
     if (R.active) lam_store(P, slot, L);
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
     for (int j = threadIdx.x; j < item.w; j += blockDim.x) P.Q[item.z + j] = sQ[j];

@@ -87,6 +87,22 @@ __global__ void vtx_colour_kernel(Params P, const int *__restrict__ list, int n)
     P.lamB2[v] = lv;
 }
 
+// Surface bending at the interior vertices of one colour (i mod 3), plain path.
+__global__ void lap_colour_kernel(Params P, const int *__restrict__ list, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int v = list[i];
+    float *sp = reinterpret_cast<float *>(P.X + v - 1) + 3;
+    float *s = reinterpret_cast<float *>(P.X + v) + 3;
+    float *sn = reinterpret_cast<float *>(P.X + v + 1) + 3;
+    float a = *sp, b = *s, c = *sn;
+    project_laplacian(a, b, c, P.RV1[v - 1].y, P.RV1[v].y, P.RV1[v + 1].y, P.RV2[v], P.lamL[v], P.inv_h2);
+    *sp = a;
+    *s = b;
+    *sn = c;
+}
+
 // ------------------------------------------------------------------ shared-memory rods
 template <bool FULL>
 __global__ void __launch_bounds__(256) rod_kernel(Params P, int n_iter, int first, int apply)
@@ -134,8 +150,10 @@ void launch_colour(viper_scene *s, int colour, const int *list, int n)
     ProfScope ps(s, PROF_ROD);
     if (colour < 2)
         seg_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
-    else
+    else if (colour < 4)
         vtx_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
+    else
+        lap_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
     s->launches++;
 }
 

@@ -290,6 +290,25 @@ __device__ __forceinline__ void project_vertex(float4 &qa, float4 &qb, float &s,
     }
 }
 
+// ---------------------------------------------------------------- surface bending
+// Interior vertex with scales (sp, s, sn) of vertices i-1, i, i+1 and inverse
+// scale weights (wp, w, wn); rv2 = (jp, jn, alpha_L) with jp = 1/(l_a lv),
+// jn = 1/(l_b lv), lv = (l_a + l_b)/2 (Sec. 5 E_bending, Laplacian of Sec. 7.5
+// read as the second derivative, s_bar = 1):
+//  L  C = jn (sn - s) - jp (s - sp),  J = (jp, -(jp + jn), jn)
+__device__ __forceinline__ void project_laplacian(float &sp, float &s, float &sn, float wp, float w, float wn,
+                                                  float4 rv2, float &lam, float inv_h2)
+{
+    const float jp = rv2.x, jn = rv2.y, jc = -(jp + jn);
+    const float C = jn * (sn - s) - jp * (s - sp);
+    const float at = rv2.z * inv_h2;
+    const float dl = (-C - at * lam) / (wp * jp * jp + w * jc * jc + wn * jn * jn + at);
+    lam += dl;
+    sp += wp * jp * dl;
+    s += w * jc * dl;
+    sn += wn * jn * dl;
+}
+
 // ---------------------------------------------------------------- pills
 // Closed-form closest sphere of a tapered capsule (App. D): t = (a - h tan th)/l
 // clamped, sin th = (r1 - r2)/l; one end sphere containing the other -> the

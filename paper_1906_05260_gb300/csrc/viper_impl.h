@@ -36,6 +36,9 @@ struct Params {
     float4 *X, *V, *Q, *W, *Xp, *Qp, *Xpred;
     // rest
     const float4 *RV0, *RV1, *RS0;
+    // surface bending per vertex: (1/(l_a lv), 1/(l_b lv), compliance, 0), zero at rod ends
+    const float4 *RV2;
+    int surface;
     const float2 *RS1;
     const int *seg_v0, *vtx_seg, *seg_group;
     // Vertex positions are stored relative to a per-rod FP32 origin (the rod's
@@ -49,6 +52,7 @@ struct Params {
     float4 *lamS, *lamB;
     float2 *lamS2;
     float *lamB2;
+    float *lamL;  // surface bending
     // shared-memory path
     const int4 *items;
     const int2 *slots;
@@ -80,6 +84,9 @@ struct Params {
     Grid *grid;
     int *err;
 };
+
+// Multipliers carried per rod-kernel slot between launches (SlotLam).
+constexpr int kSlotLam = 24;
 
 // Sections of the scene-free broadphase scratch (query.cu).
 constexpr int kBpSections = 11;
@@ -114,8 +121,9 @@ struct viper_scene {
     float4 *frames = nullptr;             // LBS frames, 3 float4 per caller segment
     float4 *stage4 = nullptr;             // staging for get/set state (max(nv, ns) float4)
     float *stage1 = nullptr;
-    int *col_list[4] = {nullptr, nullptr, nullptr, nullptr};
-    int col_n[4] = {0, 0, 0, 0};
+    // plain path: segments (colours 0, 1), interior vertices (2, 3), surface bending (4, 5, 6)
+    int *col_list[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int col_n[7] = {0, 0, 0, 0, 0, 0, 0};
     int *d_scan_tmp = nullptr;
     int scan_tmp_n = 0;
     // batched schedule
@@ -138,7 +146,7 @@ struct viper_scene {
     int last_cuda = 0;  // cudaError_t of the last failed CUDA call (viper_cuda_error)
     int latched = 0;
     // rest tables in caller order (FP64 precompute rounded to FP32), kept to rebuild the schedule
-    std::vector<float4> u_RV0, u_RV1, u_RS0, u_LQ, u_LC;
+    std::vector<float4> u_RV0, u_RV1, u_RV2, u_RS0, u_LQ, u_LC;
     std::vector<float2> u_RS1;
     std::vector<int> u_group;  // per caller rod
     std::vector<float4> u_origin;  // per caller rod: FP32 rest centroid

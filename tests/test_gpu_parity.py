@@ -287,3 +287,49 @@ def test_frame_kernel_equals_graph_path(V, name):
     scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
     assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
     assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4
+
+
+# --------------------------------------------------------------------------
+# surface bending (scale Laplacian, three extra vertex colours)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
+def test_surface_bending_plain_small(V, solver):
+    sc = dataclasses.replace(S.plain_small(), surface_bending=True)
+    g, o = _pair(V, sc, solver)
+    g.frame(); o.frame()
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="surface bending, 1 frame")
+    for _ in range(19):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e20 = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_100, rad_tol=1e-4, ang_tol=1e-3,
+                        what="surface bending, 20 frames")
+    print("surface bending plain_small errors vs FP64, 1 / 20 frames:", e, e20)
+
+
+@pytest.mark.parametrize("solver", [1, 2], ids=["batched", "frame"])
+def test_surface_bending_with_contacts(V, solver):
+    sc = dataclasses.replace(S.muscle_rig(n_rods=60, mesh_verts=0), surface_bending=True)
+    g, o = _pair(V, sc, solver)
+    for _ in range(2):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="surface bending, muscle rig")
+    print("surface bending muscle_rig 2 frames errors vs FP64:", e)
+
+
+def test_surface_bending_scale_bump_matches_oracle(V):
+    """A sharp scale bump on a free straight rod: the scale profile the GPU
+    relaxes to matches the oracle's (radii are what the constraint moves)."""
+    sc = dataclasses.replace(S.plain_small(), surface_bending=True, gravity=np.zeros(3))
+    g, o = _pair(V, sc, 1)
+    st = g.get_state()
+    x4 = st["x4"].copy()
+    x4[5::32, 3] *= 1.3
+    g.set_state(x4=x4)
+    o.set_state(s=x4[:, 3].astype(np.float64) / sc.radius)
+    for _ in range(3):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, rad_tol=1e-5, what="scale bump")
+    print("surface bending scale bump errors vs FP64:", e)
