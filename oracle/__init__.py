@@ -35,7 +35,7 @@ class _Desc(C.Structure):
         ("pin_vertex", _ip), ("pin_bone", _ip), ("pin_offset", _dp), ("n_bones", C.c_int),
         ("bone_quat", _dp), ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("contacts", C.c_int), ("volume", C.c_int),
-        ("surface_bending", C.c_int),
+        ("surface_bending", C.c_int), ("jacobi", C.c_int),
     ]
 
 
@@ -148,6 +148,7 @@ class OracleScene:
         desc.contacts = int(bool(scene.contacts))
         desc.volume = int(bool(scene.volume))
         desc.surface_bending = int(bool(getattr(scene, "surface_bending", False)))
+        desc.jacobi = int(bool(getattr(scene, "jacobi", False)))
         h = L.vo_create(C.byref(desc))
         if not h:
             raise ValueError("vo_create rejected the scene")

@@ -54,7 +54,10 @@ struct vo_scene {
     double *lam_seg;   /* 6 per segment: S(3), V, X, G */
     double *lam_vtx;   /* 5 per vertex: B(3), Vb(2)    */
     double *lam_lap;   /* 1 per vertex: surface bending */
-    int surface;
+    int surface, jacobi;
+    /* Jacobi pass: summed corrections and the number of constraints acting */
+    double *jdx, *jds, *jdth;
+    int *jcx, *jcs, *jcq;
     double *lam_pair, *lam_plane;
     int *pairs;
     int npairs, cap_pairs;
@@ -426,6 +429,31 @@ static void xpbd_solve(const vo_scene *S, int k, const double *C, blk_t *b, int 
     }
 }
 
+/*
+ * Jacobi with averaging (Sec. 7: "constraints are computed in parallel, and
+ * the resulting positional displacements are averaged out by a reduction"):
+ * instead of being applied, a constraint's corrections are summed per degree
+ * of freedom, each acting block adding one to that degree of freedom's count.
+ * acts[i] says whether block i acts (reading: a block acts when its Jacobian
+ * is structurally non-zero for the constraint kind).
+ */
+static void accumulate_blocks(vo_scene *S, const blk_t *b, int nb, const int *acts)
+{
+    for (int i = 0; i < nb; ++i) {
+        if (!acts[i]) continue;
+        if (b[i].type == BLK_POS) {
+            for (int c = 0; c < 3; ++c) S->jdx[3 * b[i].idx + c] += b[i].delta[c];
+            S->jcx[b[i].idx] += 1;
+        } else if (b[i].type == BLK_SCALE) {
+            S->jds[b[i].idx] += b[i].delta[0];
+            S->jcs[b[i].idx] += 1;
+        } else {
+            for (int c = 0; c < 3; ++c) S->jdth[3 * b[i].idx + c] += b[i].delta[c];
+            S->jcq[b[i].idx] += 1;
+        }
+    }
+}
+
 static void apply_blocks(vo_scene *S, blk_t *b, int nb)
 {
     for (int i = 0; i < nb; ++i) {
@@ -454,7 +482,13 @@ static void project_segment(vo_scene *S, int g, int kind, double h)
     b[4].type = BLK_ROT;   b[4].idx = g;     memcpy(b[4].J, Jth, sizeof(double) * 3 * k);
     static const int lam_off[4] = {0, 3, 4, 5};
     xpbd_solve(S, k, C, b, 5, alpha, S->lam_seg + 6 * g + lam_off[kind], h);
-    apply_blocks(S, b, 5);
+    if (S->jacobi) {
+        /* blocks acting per kind: positions, scales, frame */
+        static const int acts[4][5] = {{1, 1, 0, 0, 1}, {1, 1, 1, 1, 1}, {0, 0, 1, 1, 0}, {0, 0, 1, 1, 0}};
+        accumulate_blocks(S, b, 5, acts[kind]);
+    } else {
+        apply_blocks(S, b, 5);
+    }
 }
 
 static void project_vertex(vo_scene *S, int i, int kind, double h)
@@ -472,7 +506,12 @@ static void project_vertex(vo_scene *S, int i, int kind, double h)
     b[1].type = BLK_ROT;   b[1].idx = gb; memcpy(b[1].J, Jthb, sizeof(double) * 3 * k);
     b[2].type = BLK_SCALE; b[2].idx = i;  memcpy(b[2].J, Js, sizeof(double) * k);
     xpbd_solve(S, k, C, b, 3, alpha, S->lam_vtx + 5 * i + (kind == 0 ? 0 : 3), h);
-    apply_blocks(S, b, 3);
+    if (S->jacobi) {
+        static const int acts[3] = {1, 1, 1};
+        accumulate_blocks(S, b, 3, acts);
+    } else {
+        apply_blocks(S, b, 3);
+    }
 }
 
 /*
@@ -523,7 +562,51 @@ static void project_laplacian(vo_scene *S, int i, double h)
         b[k].J[0] = J[k];
     }
     xpbd_solve(S, 1, &C, b, 3, &alpha, S->lam_lap + i, h);
-    apply_blocks(S, b, 3);
+    if (S->jacobi) {
+        static const int acts[3] = {1, 1, 1};
+        accumulate_blocks(S, b, 3, acts);
+    } else {
+        apply_blocks(S, b, 3);
+    }
+}
+
+/*
+ * One Jacobi iteration over the rod constraints: every constraint (S, V, X,
+ * G per segment, B, Vb per interior vertex, and L with surface bending) is
+ * evaluated on the state at the start of the iteration, then each degree of
+ * freedom moves by the mean of the corrections of the constraints acting on
+ * it; frames turn by the mean increment.
+ */
+static void jacobi_pass(vo_scene *S, double h)
+{
+    memset(S->jdx, 0, sizeof(double) * 3 * (size_t)S->nv);
+    memset(S->jds, 0, sizeof(double) * (size_t)S->nv);
+    memset(S->jdth, 0, sizeof(double) * 3 * (size_t)S->ns);
+    memset(S->jcx, 0, sizeof(int) * (size_t)S->nv);
+    memset(S->jcs, 0, sizeof(int) * (size_t)S->nv);
+    memset(S->jcq, 0, sizeof(int) * (size_t)S->ns);
+    for (int g = 0; g < S->ns; ++g) {
+        project_segment(S, g, 0, h);
+        if (S->volume) project_segment(S, g, 1, h);
+        project_segment(S, g, 2, h);
+        project_segment(S, g, 3, h);
+    }
+    for (int r = 0; r < S->n_rods; ++r)
+        for (int i = S->off[r] + 1; i < S->off[r + 1] - 1; ++i) {
+            project_vertex(S, i, 0, h);
+            if (S->volume) project_vertex(S, i, 1, h);
+            if (S->surface) project_laplacian(S, i, h);
+        }
+    for (int i = 0; i < S->nv; ++i) {
+        if (S->jcx[i])
+            for (int c = 0; c < 3; ++c) S->x[3 * i + c] += S->jdx[3 * i + c] / S->jcx[i];
+        if (S->jcs[i]) S->s[i] += S->jds[i] / S->jcs[i];
+    }
+    for (int g = 0; g < S->ns; ++g)
+        if (S->jcq[g]) {
+            double d[3] = {S->jdth[3 * g] / S->jcq[g], S->jdth[3 * g + 1] / S->jcq[g], S->jdth[3 * g + 2] / S->jcq[g]};
+            apply_dtheta(S->q + 4 * g, d);
+        }
 }
 
 /*
@@ -1017,6 +1100,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->contacts = d->contacts;
     S->volume = d->volume;
     S->surface = d->surface_bending;
+    S->jacobi = d->jacobi;
 
     /* state starts at rest (Sec. 4: the rest pose is the initial pose) */
     S->x = xcalloc(3 * (size_t)nv, sizeof(double));
@@ -1034,6 +1118,12 @@ vo_scene *vo_create(const vo_desc *d)
     S->lam_seg = xcalloc(6 * (size_t)ns, sizeof(double));
     S->lam_vtx = xcalloc(5 * (size_t)nv, sizeof(double));
     S->lam_lap = xcalloc((size_t)nv, sizeof(double));
+    S->jdx = xcalloc(3 * (size_t)nv, sizeof(double));
+    S->jds = xcalloc((size_t)nv, sizeof(double));
+    S->jdth = xcalloc(3 * (size_t)ns, sizeof(double));
+    S->jcx = xcalloc((size_t)nv, sizeof(int));
+    S->jcs = xcalloc((size_t)nv, sizeof(int));
+    S->jcq = xcalloc((size_t)ns, sizeof(int));
     S->lam_plane = xcalloc((size_t)nv * (size_t)(S->np ? S->np : 1), sizeof(double));
     S->acc = xcalloc(4 * (size_t)nv, sizeof(double));
     S->cnt = xcalloc((size_t)nv, sizeof(int));
@@ -1047,7 +1137,8 @@ void vo_destroy(vo_scene *S)
                     S->obar, S->minv, S->sinv, S->mseg, S->rm, S->cs, S->cb, S->cv, S->group,
                     S->pin_of_v, S->pin_bone, S->pin_off, S->bq0, S->bt0, S->bq1, S->bt1, S->bq,
                     S->bt, S->planes, S->x, S->s, S->v, S->sd, S->q, S->w, S->xp, S->sp, S->qp,
-                    S->lam_seg, S->lam_vtx, S->lam_lap, S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
+                    S->lam_seg, S->lam_vtx, S->lam_lap, S->jdx, S->jds, S->jdth, S->jcx, S->jcs, S->jcq,
+                    S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(S);
 }
@@ -1169,9 +1260,13 @@ int vo_step(vo_scene *S, double dt, int substeps, int iterations)
             memset(S->lam_pair, 0, sizeof(double) * (size_t)(S->npairs ? S->npairs : 1));
         }
         for (int it = 0; it < iterations; ++it) {
-            for (int c = 0; c < 4; ++c) colour_sweep(S, c, h);
-            if (S->surface)
-                for (int c = 4; c < 7; ++c) colour_sweep(S, c, h);
+            if (S->jacobi) {
+                jacobi_pass(S, h);
+            } else {
+                for (int c = 0; c < 4; ++c) colour_sweep(S, c, h);
+                if (S->surface)
+                    for (int c = 4; c < 7; ++c) colour_sweep(S, c, h);
+            }
             if ((S->contacts && S->npairs > 0) || S->np > 0) contact_pass(S, h);
         }
         /* velocity update: reading (not written out in the paper): the

@@ -46,6 +46,8 @@ typedef struct vo_desc {
     int contacts;                /* pill-pill contacts on/off                     */
     int volume;                  /* volume constraints on/off                     */
     int surface_bending;         /* scale-Laplacian constraints on/off            */
+    int jacobi;                  /* rod constraints: 0 four-colour Gauss-Seidel,  */
+                                 /* 1 Jacobi with averaging (Sec. 7 engine)       */
 } vo_desc;
 
 vo_scene *vo_create(const vo_desc *d);

@@ -102,6 +102,7 @@ class Scene:
     init_quat: Optional[np.ndarray] = None
     mesh: Optional[Mesh] = None
     surface_bending: bool = False     # scale-Laplacian constraints (Sec. 5, E_bending)
+    jacobi: bool = False              # rod constraints by Jacobi with averaging (Sec. 7 engine)
 
     @property
     def n_rods(self) -> int:

@@ -275,8 +275,9 @@ def _helix_scene(n_rods=4, n=12, lbar=0.01, seed=5):
         dt=1 / 60, substeps=10, iterations=4, frames=1)
 
 
-def test_rest_state_is_stationary_without_gravity():
-    sc = _helix_scene()
+@pytest.mark.parametrize("jacobi", [False, True], ids=["colours", "jacobi"])
+def test_rest_state_is_stationary_without_gravity(jacobi):
+    sc = dataclasses.replace(_helix_scene(), jacobi=jacobi)
     o = oracle.OracleScene(sc)
     _, ob = o.rest()
     assert np.abs(ob).max() > 1.0  # curved and twisted: Omega_bar is not zero
@@ -340,11 +341,12 @@ def _rigid(R, t, x):
     return x @ R.T + t
 
 
-def test_rigid_motion_invariance():
+@pytest.mark.parametrize("jacobi", [False, True], ids=["colours", "jacobi"])
+def test_rigid_motion_invariance(jacobi):
     """Rotating and translating the whole scene (rest pose, initial state,
     pins and gravity) rotates and translates the result."""
     rng = np.random.default_rng(7)
-    base = S.plain_small(n_rods=4, n_verts=12)
+    base = dataclasses.replace(S.plain_small(n_rods=4, n_verts=12), jacobi=jacobi)
     # start from a perturbed state so that every constraint family is active
     init_q = S.quat_mul(S.axis_angle_quat(rng.normal(size=(base.ns, 3)) * 0.2), base.rest_quat)
     init_x = base.rest_pos + rng.normal(size=base.rest_pos.shape) * 1e-3
@@ -731,3 +733,55 @@ def test_surface_bending_smooths_a_scale_bump():
         res[surface] = _laplacian_residual(st["s"], lb)
         np.testing.assert_allclose(st["x"], sc.rest_pos, atol=1e-9)
     assert res[True] < 0.5 * res[False], res
+
+
+# --------------------------------------------------------------------------
+# Jacobi with averaging (Sec. 7 engine) as an alternative ordering
+# --------------------------------------------------------------------------
+
+def test_jacobi_first_vertex_equals_gauss_seidel_after_one_iteration():
+    """With volume and surface bending off, a free rod's first vertex is moved
+    only by the stretch/shear constraint of segment 0.  Gauss-Seidel projects
+    that constraint first, on the predicted state, and nothing after it in the
+    sweep touches the vertex; Jacobi projects it on the same state and divides
+    by a count of one: after one iteration the vertex agrees exactly."""
+    rng = np.random.default_rng(21)
+    base = dataclasses.replace(_helix_scene(n_rods=3), volume=False)
+    init_x = base.rest_pos + rng.normal(size=base.rest_pos.shape) * 2e-3
+    init_q = S.quat_mul(S.axis_angle_quat(rng.normal(size=(base.ns, 3)) * 0.2), base.rest_quat)
+    out = []
+    for jacobi in (False, True):
+        o = oracle.OracleScene(dataclasses.replace(base, jacobi=jacobi))
+        o.set_state(x=init_x, q=init_q)
+        assert o.step(dt=1 / 60, substeps=1, iterations=1) == 0
+        out.append(o.get_state()["x"])
+    first = base.rod_offsets[:-1]
+    np.testing.assert_allclose(out[1][first], out[0][first], rtol=0, atol=1e-14)
+    # elsewhere the two orderings differ
+    assert np.abs(out[1] - out[0]).max() > 1e-6
+
+
+def test_jacobi_converges_more_slowly_than_colouring():
+    """E9-style: bars pulled to 2x instantly.  Each ordering approaches its own
+    limit (Jacobi with averaging and full multiplier updates does not share
+    Gauss-Seidel's fixed point), the distance falling with the iteration count;
+    Gauss-Seidel, which carries a correction along the chain within one sweep,
+    is closer to its limit at every count (the paper reports linear
+    convergence for its Jacobi engine)."""
+    n = 12
+    sc = _one_rod_scene(n=n, r=0.01, lbar=0.01, cs=1e-9, cb=1e-7, cv=1e-9)
+    sc = dataclasses.replace(sc, pin_vertex=np.array([0, n - 1], np.int32), pin_bone=np.array([-1, -1], np.int32),
+                             pin_offset=np.array([[0, 0, 0], [2.0 * 0.01 * (n - 1), 0, 0]]))
+
+    def run(jacobi, iters):
+        o = oracle.OracleScene(dataclasses.replace(sc, jacobi=jacobi))
+        assert o.step(dt=1 / 60, substeps=1, iterations=iters) == 0
+        return o.get_state()["x"]
+
+    dist = {}
+    for jacobi, limit_iters in ((False, 4096), (True, 16384)):
+        limit = run(jacobi, limit_iters)
+        dist[jacobi] = [np.abs(run(jacobi, it) - limit).max() for it in (1, 4, 16, 64, 256)]
+        d = dist[jacobi]
+        assert all(a > b for a, b in zip(d, d[1:])), (jacobi, d)
+    assert all(g < j for g, j in zip(dist[False][1:], dist[True][1:])), dist
