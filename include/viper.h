@@ -53,6 +53,10 @@ extern "C" {
 #define VIPER_FLAG_CONTACTS 1 /* pill-pill contacts (Sec. 7.1, 7.2)                */
 #define VIPER_FLAG_VOLUME 2   /* volume constraints (Sec. 5 "Volume potential")    */
 #define VIPER_FLAG_SURFACE_BENDING 4 /* scale-Laplacian constraints (Sec. 5 E_bending) */
+/* Rod constraints by Jacobi with averaging (Sec. 7 engine) instead of the
+ * four-colour Gauss-Seidel sweep.  Needs every rod in shared memory (at most
+ * resident_max vertices) and a non-plain solver: VIPER_EINVAL otherwise. */
+#define VIPER_FLAG_JACOBI 8
 
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
 #define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,

@@ -225,6 +225,15 @@ int rebuild(viper_scene *s, bool keep_state)
     s->smem_iter = std::max(S.smem_iter, 16);
     s->resident_nv = s->h_int_off[S.n_resident_rods];
     s->resident_ns = s->resident_nv - S.n_resident_rods;
+    if (s->P.jacobi) {
+        // Jacobi runs only in the shared-memory sweep, with 3 float4 of records per
+        // vertex and per segment behind the 2 (y + w) float4 of state
+        if (s->mode == VIPER_SOLVER_PLAIN || s->resident_nv < nv) return VIPER_EINVAL;
+        for (const int4 &it : S.items) {
+            s->smem_full = std::max(s->smem_full, 16 * 5 * (it.y + it.w));
+            s->smem_iter = std::max(s->smem_iter, 16 * 5 * (it.y + it.w));
+        }
+    }
     s->h_items = S.items;
     s->h_slots = S.slots;
     if (configure_rod_kernels(s->smem_full) != 0) return VIPER_EINVAL;
@@ -693,6 +702,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.gz = (float)d->gravity[2];
     P.volume = (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
     P.surface = (d->flags & VIPER_FLAG_SURFACE_BENDING) ? 1 : 0;
+    P.jacobi = (d->flags & VIPER_FLAG_JACOBI) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
     P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0;

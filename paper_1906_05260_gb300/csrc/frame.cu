@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
     const int wib = threadIdx.x >> 5, gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
     const int gwarps = gridDim.x * (blockDim.x >> 5);
     const bool planes = P.n_planes > 0;
-    const bool vol = P.volume != 0;
     const float at = P.contact_alpha * P.inv_h2;
 
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
@@ -197,7 +196,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
         }
         if (iters > 0 && owner) {
             __syncthreads();
-            sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
+            sweep_any(P, sX, sQ, R, L, sQp + item.w, item);
             if (BARRIERS)
                 for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
         }
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
             if (it + 1 < iters) {
                 if (owner) {
                     __syncthreads();
-                    sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
+                    sweep_any(P, sX, sQ, R, L, sQp + item.w, item);
                     if (BARRIERS)
                         for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
                 }
@@ -296,7 +295,7 @@ int frame_configure(viper_scene *s)
     const bool barriers = pills || s->n_planes > 0;
     int maxyw = 0;
     for (const int4 &it : s->h_items) maxyw = std::max(maxyw, it.y + it.w);
-    const int smem = 48 * maxyw;
+    const int smem = (s->P.jacobi ? 96 : 48) * maxyw;  // state, and the Jacobi records behind it
     void *fn = pick(barriers, pills);
     if (raise_smem_limit(fn, smem) != 0) return VIPER_EINVAL;
     int grid = s->n_items;

@@ -231,6 +231,7 @@ struct SlotRest {
     int lv, ls;  // local first vertex / segment of the slot inside the item
     int gv;      // global index of vertex 2p
     int p2;      // 2p: rod-local index of vertex 2p
+    int n;       // vertices of the slot's rod
     float4 rs00, rs01, rv01, rv02;
     float2 rs10, rs11;
     float w0, w1, w2, ws0, ws1, ws2, ws3, aB1, aV1, aB2, aV2, l2, im2;
@@ -246,6 +247,7 @@ __device__ __forceinline__ void load_slot(const Params &P, int4 item, int2 sd, S
     const int gv = item.x + R.lv, gs = item.z + R.ls;
     R.gv = gv;
     R.p2 = 2 * p;
+    R.n = N;
     R.has0 = R.active;
     R.has1 = R.active && (2 * p + 1 <= N - 2);   // segment 2p+1 and vertex 2p+1
     R.hasv2 = R.active && (2 * p + 2 <= N - 2);  // vertex 2p+2
@@ -366,6 +368,138 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
     }
 }
 
+// One Jacobi-with-averaging iteration over the item staged in shared memory
+// (Sec. 7 engine): every constraint is evaluated on the iteration's starting
+// state with its own multiplier; the increments go to per-constraint records
+// in shared memory (jS: 3 float4 per segment, jV: 2 per vertex, jL: 1 per
+// vertex with surface bending); then each thread moves the degrees of freedom
+// it owns (vertices 2p, 2p+1 and the rod's last one, segments 2p, 2p+1) by the
+// sum of the records acting on them divided by their number.  Every thread
+// of the CTA must call it.
+__device__ __forceinline__ void sweep_jacobi(float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L, float inv_h2,
+                                             bool vol, const float4 *__restrict__ RV2, float4 *jS, float4 *jV,
+                                             float4 *jL)
+{
+    const int lv = R.lv, ls = R.ls;
+    // ---- every constraint on the starting state
+    if (R.has0) {
+        SegDelta d;
+        jacobi_segment(sX[lv], sX[lv + 1], sQ[ls], R.w0, R.w1, R.ws0, R.ws1, R.rs00, R.rs10, L.s0, L.x0, inv_h2, vol,
+                       d);
+        jS[3 * ls] = make_float4(d.dxa.x, d.dxa.y, d.dxa.z, d.dsa);
+        jS[3 * ls + 1] = make_float4(d.dxb.x, d.dxb.y, d.dxb.z, d.dsb);
+        jS[3 * ls + 2] = make_float4(d.dth.x, d.dth.y, d.dth.z, 0.f);
+    }
+    if (R.has1) {
+        SegDelta d;
+        jacobi_segment(sX[lv + 1], sX[lv + 2], sQ[ls + 1], R.w1, R.w2, R.ws1, R.ws2, R.rs01, R.rs11, L.s1, L.x1,
+                       inv_h2, vol, d);
+        jS[3 * (ls + 1)] = make_float4(d.dxa.x, d.dxa.y, d.dxa.z, d.dsa);
+        jS[3 * (ls + 1) + 1] = make_float4(d.dxb.x, d.dxb.y, d.dxb.z, d.dsb);
+        jS[3 * (ls + 1) + 2] = make_float4(d.dth.x, d.dth.y, d.dth.z, 0.f);
+        // vertex 2p+1 between segments 2p and 2p+1
+        VtxDelta e;
+        jacobi_vertex(sQ[ls], sQ[ls + 1], sX[lv + 1].w, sX[lv].w, sX[lv + 2].w, R.rs00.x, R.rs01.x, R.rs00.y,
+                      R.rs01.y, R.ws1, R.rv01, R.aB1, R.aV1, L.b1, L.v1, inv_h2, vol, e);
+        jV[2 * (lv + 1)] = make_float4(e.dtha.x, e.dtha.y, e.dtha.z, e.ds);
+        jV[2 * (lv + 1) + 1] = make_float4(e.dthb.x, e.dthb.y, e.dthb.z, 0.f);
+        if (RV2) {
+            float dsp, ds, dsn;
+            laplacian_increments(sX[lv].w, sX[lv + 1].w, sX[lv + 2].w, R.ws0, R.ws1, R.ws2, __ldg(RV2 + R.gv + 1),
+                                 L.l1, inv_h2, dsp, ds, dsn);
+            jL[lv + 1] = make_float4(dsp, ds, dsn, 0.f);
+        }
+    }
+    if (R.hasv2) {  // vertex 2p+2 between segments 2p+1 and 2p+2
+        VtxDelta e;
+        jacobi_vertex(sQ[ls + 1], sQ[ls + 2], sX[lv + 2].w, sX[lv + 1].w, sX[lv + 3].w, R.rs01.x, R.l2, R.rs01.y,
+                      R.im2, R.ws2, R.rv02, R.aB2, R.aV2, L.b2, L.v2, inv_h2, vol, e);
+        jV[2 * (lv + 2)] = make_float4(e.dtha.x, e.dtha.y, e.dtha.z, e.ds);
+        jV[2 * (lv + 2) + 1] = make_float4(e.dthb.x, e.dthb.y, e.dthb.z, 0.f);
+        if (RV2) {
+            float dsp, ds, dsn;
+            laplacian_increments(sX[lv + 1].w, sX[lv + 2].w, sX[lv + 3].w, R.ws1, R.ws2, R.ws3,
+                                 __ldg(RV2 + R.gv + 2), L.l2, inv_h2, dsp, ds, dsn);
+            jL[lv + 2] = make_float4(dsp, ds, dsn, 0.f);
+        }
+    }
+    __syncthreads();
+    // ---- each owner averages the records acting on its degrees of freedom
+    if (R.active) {
+        const int N = R.n, vb = lv - R.p2, sb = ls - R.p2;  // the rod's first vertex / segment in the item
+        const float nS = vol ? 2.f : 1.f;   // S, V on positions and on the frame
+        const float nSs = vol ? 3.f : 2.f;  // V, X, G on scales
+        const float nB = vol ? 2.f : 1.f;   // B, Vb on the vertex scale and both frames
+        const int last = (R.p2 + 2 == N - 1) ? 3 : 2;
+        for (int k = 0; k < last; ++k) {
+            const int i = R.p2 + k;  // rod-local vertex
+            V3 dx = v3(0.f, 0.f, 0.f);
+            float ds = 0.f, cx = 0.f, cs = 0.f;
+            if (i >= 1) {
+                const float4 b = jS[3 * (sb + i - 1) + 1];
+                dx = dx + xyz(b);
+                ds += b.w;
+                cx += nS;
+                cs += nSs;
+            }
+            if (i <= N - 2) {
+                const float4 a = jS[3 * (sb + i)];
+                dx = dx + xyz(a);
+                ds += a.w;
+                cx += nS;
+                cs += nSs;
+            }
+            if (i >= 1 && i <= N - 2) {
+                ds += jV[2 * (vb + i)].w;
+                cs += nB;
+            }
+            if (RV2) {
+                if (i - 1 >= 1) { ds += jL[vb + i - 1].z; cs += 1.f; }
+                if (i >= 1 && i <= N - 2) { ds += jL[vb + i].y; cs += 1.f; }
+                if (i + 1 <= N - 2) { ds += jL[vb + i + 1].x; cs += 1.f; }
+            }
+            float4 x = sX[vb + i];
+            add_to(x, (1.f / cx) * dx);
+            x.w += ds / cs;
+            sX[vb + i] = x;
+        }
+        for (int k = 0; k < 2; ++k) {
+            const int j = R.p2 + k;  // rod-local segment
+            if (j > N - 2) break;
+            const float4 t = jS[3 * (sb + j) + 2];
+            V3 dth = xyz(t);
+            float cq = nS;
+            if (j >= 1) {
+                dth = dth + xyz(jV[2 * (vb + j) + 1]);
+                cq += nB;
+            }
+            if (j + 1 <= N - 2) {
+                dth = dth + xyz(jV[2 * (vb + j + 1)]);
+                cq += nB;
+            }
+            float4 q = sQ[sb + j];
+            rotate_by(q, (1.f / cq) * dth);
+            sQ[sb + j] = q;
+        }
+    }
+    __syncthreads();
+}
+
+// The iteration of either ordering.  rec: the shared-memory records of
+// sweep_jacobi (3 float4 per segment, 3 per vertex), unused by the colours.
+__device__ __forceinline__ void sweep_any(const Params &P, float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L,
+                                          float4 *rec, int4 item)
+{
+    const bool vol = P.volume != 0;
+    const float4 *RV2 = P.surface ? P.RV2 : nullptr;
+    if (P.jacobi) {
+        float4 *jS = rec, *jV = rec + 3 * item.w, *jL = jV + 2 * item.y;
+        sweep_jacobi(sX, sQ, R, L, P.inv_h2, vol, RV2, jS, jV, jL);
+    } else {
+        sweep(sX, sQ, R, L, P.inv_h2, vol, RV2);
+    }
+}
+
 // One work item of the shared-memory rod solve: a CTA stages the item's float4
 // state in shared memory with coalesced loads (FULL: predicting it first; else
 // adding the pending contact corrections when `apply`), runs n_iter colour
@@ -413,9 +547,9 @@ __device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, boo
     else
         lam_load(P, slot, L);
     __syncthreads();
-    const bool vol = P.volume != 0;
+    float4 *rec = smem + 2 * (item.y + item.w);  // Jacobi records behind the state
 #pragma unroll 1
-    for (int k = 0; k < n_iter; ++k) sweep(sX, sQ, R, L, P.inv_h2, vol, P.surface ? P.RV2 : nullptr);
+    for (int k = 0; k < n_iter; ++k) sweep_any(P, sX, sQ, R, L, rec, item);
     if (!FULL && R.active) lam_store(P, slot, L);
 
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
@@ -491,7 +625,7 @@ __device__ __forceinline__ void rod_item_first(const Params &P, int b, bool fini
     SlotLam L;
     zero_lam(L);
     __syncthreads();
-    sweep(sX, sQ, R, L, P.inv_h2, P.volume != 0, P.surface ? P.RV2 : nullptr);
+    sweep_any(P, sX, sQ, R, L, smem + 2 * (item.y + item.w), item);
     if (R.active) lam_store(P, slot, L);
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
     for (int j = threadIdx.x; j < item.w; j += blockDim.x) P.Q[item.z + j] = sQ[j];

@@ -80,8 +80,9 @@ __device__ __forceinline__ float inv_mass(float4 rv1) { return fmaxf(rv1.x, 0.f)
 
 // ---------------------------------------------------------------- segment constraints
 // Segment j between vertices a, b, frame q; per-constraint multipliers in lam
-// (S.xyz, V) and lam2 (X, G).  Order S, V, X, G, each evaluated at the state the
-// previous one left (Gauss-Seidel inside the element).
+// (S.xyz, V) and lam2 (X, G).  project_segment: order S, V, X, G, each evaluated
+// at the state the previous one left (Gauss-Seidel inside the element);
+// jacobi_segment: all four evaluated on the same state, increments summed.
 //
 //  S  C = (xb - xa)/l - d3                (Eq. stretch_z, isotropic vector form)
 //     J_xa = -I/l, J_xb = I/l, J_theta = [d3]x; with the rotational inverse
@@ -91,69 +92,137 @@ __device__ __forceinline__ float inv_mass(float4 rv1) { return fmaxf(rv1.x, 0.f)
 //  V  C = s_m^2 d3.(xb - xa)/l - 1        (determinant of grad p, App. A)
 //  X  C = s_m - 1                         (Eq. stretch_xy)
 //  G  C = (sb - sa)/l                     (Eq. surface_stretch)
+
+// Increments of one segment constraint: positions and scales of both ends and
+// the frame's world rotation increment (applied as rotate_by).
+struct SegDelta {
+    V3 dxa, dxb, dth;
+    float dsa, dsb;
+};
+
+// S on (xa, xb, q): multiplier update and increments.
+__device__ __forceinline__ void seg_stretch(const float4 &xa, const float4 &xb, const float4 &q, float wa, float wb,
+                                            float4 rs0, float inv_l, float4 &lam, float inv_h2, SegDelta &d)
+{
+    V3 d3 = qd3(q);
+    V3 C = (xyz(xb) - xyz(xa)) * inv_l - d3;
+    float sm = 0.5f * (xa.w + xb.w);
+    float a = 4.f * rs0.y / (sm * sm);
+    float wp = (wa + wb) * inv_l * inv_l;
+    float at = rs0.z * inv_h2;
+    V3 lm = {lam.x, lam.y, lam.z};
+    V3 rhs = -C - at * lm;
+    float dn = dot(rhs, d3);
+    V3 dl = (rhs - dn * d3) * (1.f / (wp + a + at)) + d3 * (dn / (wp + at));
+    lam.x += dl.x;
+    lam.y += dl.y;
+    lam.z += dl.z;
+    d.dxa = (-wa * inv_l) * dl;
+    d.dxb = (wb * inv_l) * dl;
+    d.dth = a * cross(dl, d3);
+    d.dsa = d.dsb = 0.f;
+}
+
+// V on (xa, xb, q).
+__device__ __forceinline__ void seg_volume(const float4 &xa, const float4 &xb, const float4 &q, float wa, float wb,
+                                           float wsa, float wsb, float4 rs0, float inv_l, float4 &lam, float inv_h2,
+                                           SegDelta &d)
+{
+    V3 d3 = qd3(q);
+    V3 dx = xyz(xb) - xyz(xa);
+    float sm = 0.5f * (xa.w + xb.w);
+    float e = dot(d3, dx);
+    float C = sm * sm * e * inv_l - 1.f;
+    float jx = sm * sm * inv_l;  // J_xb = jx d3, J_xa = -jx d3
+    float js = sm * e * inv_l;   // J_sa = J_sb
+    V3 jt = (sm * sm * inv_l) * cross(d3, dx);  // J_theta (orthogonal to d3)
+    float a = 4.f * rs0.y / (sm * sm);
+    float at = rs0.w * inv_h2;
+    float den = (wa + wb) * jx * jx + (wsa + wsb) * js * js + a * dot(jt, jt) + at;
+    float dl = (-C - at * lam.w) / den;
+    lam.w += dl;
+    d.dxa = (-wa * jx * dl) * d3;
+    d.dxb = (wb * jx * dl) * d3;
+    d.dsa = wsa * js * dl;
+    d.dsb = wsb * js * dl;
+    d.dth = (a * dl) * jt;
+}
+
+// X on the end scales (sa, sb).
+__device__ __forceinline__ void seg_xsection(float sa, float sb, float wsa, float wsb, float2 rs1, float2 &lam2,
+                                             float inv_h2, float &dsa, float &dsb)
+{
+    float C = 0.5f * (sa + sb) - 1.f;
+    float at = rs1.x * inv_h2;
+    float dl = (-C - at * lam2.x) / (0.25f * (wsa + wsb) + at);
+    lam2.x += dl;
+    dsa = 0.5f * wsa * dl;
+    dsb = 0.5f * wsb * dl;
+}
+
+// G on the end scales (sa, sb).
+__device__ __forceinline__ void seg_gradient(float sa, float sb, float wsa, float wsb, float2 rs1, float inv_l,
+                                             float2 &lam2, float inv_h2, float &dsa, float &dsb)
+{
+    float C = (sb - sa) * inv_l;
+    float at = rs1.y * inv_h2;
+    float dl = (-C - at * lam2.y) / ((wsa + wsb) * inv_l * inv_l + at);
+    lam2.y += dl;
+    dsa = -wsa * inv_l * dl;
+    dsb = wsb * inv_l * dl;
+}
+
+// Gauss-Seidel: S, V, X, G, each evaluated at the state the previous one left.
 __device__ __forceinline__ void project_segment(float4 &xa, float4 &xb, float4 &q, float wa, float wb,
                                                 float wsa, float wsb, float4 rs0, float2 rs1,
                                                 float4 &lam, float2 &lam2, float inv_h2, bool volume)
 {
     const float inv_l = 1.f / rs0.x;
-    // ---- S: stretch / shear
-    {
-        V3 d3 = qd3(q);
-        V3 C = (xyz(xb) - xyz(xa)) * inv_l - d3;
-        float sm = 0.5f * (xa.w + xb.w);
-        float a = 4.f * rs0.y / (sm * sm);
-        float wp = (wa + wb) * inv_l * inv_l;
-        float at = rs0.z * inv_h2;
-        V3 lm = {lam.x, lam.y, lam.z};
-        V3 rhs = -C - at * lm;
-        float dn = dot(rhs, d3);
-        V3 dl = (rhs - dn * d3) * (1.f / (wp + a + at)) + d3 * (dn / (wp + at));
-        lam.x += dl.x;
-        lam.y += dl.y;
-        lam.z += dl.z;
-        add_to(xa, (-wa * inv_l) * dl);
-        add_to(xb, (wb * inv_l) * dl);
-        rotate_by(q, a * cross(dl, d3));
-    }
-    // ---- V: volume (determinant form)
+    SegDelta d;
+    seg_stretch(xa, xb, q, wa, wb, rs0, inv_l, lam, inv_h2, d);
+    add_to(xa, d.dxa);
+    add_to(xb, d.dxb);
+    rotate_by(q, d.dth);
     if (volume) {
-        V3 d3 = qd3(q);
-        V3 dx = xyz(xb) - xyz(xa);
-        float sm = 0.5f * (xa.w + xb.w);
-        float e = dot(d3, dx);
-        float C = sm * sm * e * inv_l - 1.f;
-        float jx = sm * sm * inv_l;  // J_xb = jx d3, J_xa = -jx d3
-        float js = sm * e * inv_l;   // J_sa = J_sb
-        V3 jt = (sm * sm * inv_l) * cross(d3, dx);  // J_theta (orthogonal to d3)
-        float a = 4.f * rs0.y / (sm * sm);
-        float at = rs0.w * inv_h2;
-        float den = (wa + wb) * jx * jx + (wsa + wsb) * js * js + a * dot(jt, jt) + at;
-        float dl = (-C - at * lam.w) / den;
-        lam.w += dl;
-        add_to(xa, (-wa * jx * dl) * d3);
-        add_to(xb, (wb * jx * dl) * d3);
-        xa.w += wsa * js * dl;
-        xb.w += wsb * js * dl;
-        rotate_by(q, (a * dl) * jt);
+        seg_volume(xa, xb, q, wa, wb, wsa, wsb, rs0, inv_l, lam, inv_h2, d);
+        add_to(xa, d.dxa);
+        add_to(xb, d.dxb);
+        xa.w += d.dsa;
+        xb.w += d.dsb;
+        rotate_by(q, d.dth);
     }
-    // ---- X: cross-section scale
-    {
-        float C = 0.5f * (xa.w + xb.w) - 1.f;
-        float at = rs1.x * inv_h2;
-        float dl = (-C - at * lam2.x) / (0.25f * (wsa + wsb) + at);
-        lam2.x += dl;
-        xa.w += 0.5f * wsa * dl;
-        xb.w += 0.5f * wsb * dl;
+    float dsa, dsb;
+    seg_xsection(xa.w, xb.w, wsa, wsb, rs1, lam2, inv_h2, dsa, dsb);
+    xa.w += dsa;
+    xb.w += dsb;
+    seg_gradient(xa.w, xb.w, wsa, wsb, rs1, inv_l, lam2, inv_h2, dsa, dsb);
+    xa.w += dsa;
+    xb.w += dsb;
+}
+
+// Jacobi: S, V, X, G all evaluated on (xa, xb, q); their increments summed.
+__device__ __forceinline__ void jacobi_segment(const float4 &xa, const float4 &xb, const float4 &q, float wa,
+                                               float wb, float wsa, float wsb, float4 rs0, float2 rs1, float4 &lam,
+                                               float2 &lam2, float inv_h2, bool volume, SegDelta &sum)
+{
+    const float inv_l = 1.f / rs0.x;
+    seg_stretch(xa, xb, q, wa, wb, rs0, inv_l, lam, inv_h2, sum);
+    if (volume) {
+        SegDelta d;
+        seg_volume(xa, xb, q, wa, wb, wsa, wsb, rs0, inv_l, lam, inv_h2, d);
+        sum.dxa = sum.dxa + d.dxa;
+        sum.dxb = sum.dxb + d.dxb;
+        sum.dth = sum.dth + d.dth;
+        sum.dsa += d.dsa;
+        sum.dsb += d.dsb;
     }
-    // ---- G: scale gradient
-    {
-        float C = (xb.w - xa.w) * inv_l;
-        float at = rs1.y * inv_h2;
-        float dl = (-C - at * lam2.y) / ((wsa + wsb) * inv_l * inv_l + at);
-        lam2.y += dl;
-        xa.w -= wsa * inv_l * dl;
-        xb.w += wsb * inv_l * dl;
-    }
+    float dsa, dsb;
+    seg_xsection(xa.w, xb.w, wsa, wsb, rs1, lam2, inv_h2, dsa, dsb);
+    sum.dsa += dsa;
+    sum.dsb += dsb;
+    seg_gradient(xa.w, xb.w, wsa, wsb, rs1, inv_l, lam2, inv_h2, dsa, dsb);
+    sum.dsa += dsa;
+    sum.dsb += dsb;
 }
 
 // ---------------------------------------------------------------- vertex constraints
@@ -198,8 +267,8 @@ __device__ __forceinline__ void rel_frame(RelFrame &f, float4 qa, float4 qb, flo
     f.N[5] = -c0 * pv.y * pv.z + c1 * m1.y * m1.z + c2 * m2.y * m2.z;
 }
 
-// Apply dtheta_a = -c R_a D_a M^T dl, dtheta_b = c R_a R(p) D_b R(p)^T M^T dl.
-__device__ __forceinline__ void apply_rel(const RelFrame &f, float4 &qa, float4 &qb, V3 dl, float c)
+// dtheta_a = -c R_a D_a M^T dl, dtheta_b = c R_a R(p) D_b R(p)^T M^T dl.
+__device__ __forceinline__ void rel_increments(const RelFrame &f, float4 qa, V3 dl, float c, V3 &dtha, V3 &dthb)
 {
     V3 pv = {f.p.x, f.p.y, f.p.z};
     V3 u = f.p.w * dl + cross(pv, dl);  // M^T dl
@@ -207,8 +276,16 @@ __device__ __forceinline__ void apply_rel(const RelFrame &f, float4 &qa, float4 
     V3 vb = f.db * u + (-0.5f * f.db * dot(u, f.e)) * f.e;
     V3 ta = qrot(qa, va);
     V3 tb = qrot(qa, vb);
-    rotate_by(qa, (-c) * ta);
-    rotate_by(qb, c * tb);
+    dtha = (-c) * ta;
+    dthb = c * tb;
+}
+
+__device__ __forceinline__ void apply_rel(const RelFrame &f, float4 &qa, float4 &qb, V3 dl, float c)
+{
+    V3 dtha, dthb;
+    rel_increments(f, qa, dl, c, dtha, dthb);
+    rotate_by(qa, dtha);
+    rotate_by(qb, dthb);
 }
 
 // Solve the symmetric 3x3 system [a0 a3 a4; a3 a1 a5; a4 a5 a2] x = b by
@@ -237,56 +314,93 @@ __device__ __forceinline__ V3 solve_sym3(const float *A_, V3 b)
 // Interior vertex i with neighbours' scales s_prev, s_next; segments a = i-1
 // and b = i.  rv0 = (Omega_bar, rbar); aB = alpha_B base (the compliance is
 // aB * (4, 4, 2)); aVb = volume-bending compliance; lam = (B.xyz, Vb.u),
-// lam_v = Vb.v.  Order B, Vb.
+// lam_v = Vb.v.  project_vertex: order B, Vb (Gauss-Seidel); jacobi_vertex:
+// both on the same state, increments summed.
 //  B   C = s Omega - Omega_bar            (Eq. bending_twist, s_bar = 1)
 //  Vb  C = s^3 Omega_uv - Omega_bar_uv    (Eq. vol, u and v rows)
+struct VtxDelta {
+    V3 dtha, dthb;
+    float ds;
+};
+
+__device__ __forceinline__ void vtx_bend(const float4 &qa, const float4 &qb, float s, float s_prev, float s_next,
+                                         float kappa, float imr2a, float imr2b, float ws, float4 rv0, float aB,
+                                         float4 &lam, float inv_h2, VtxDelta &d)
+{
+    RelFrame f;
+    rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
+    V3 C = s * f.om - v3(rv0.x, rv0.y, rv0.z);
+    float k = s * s * f.h2 * f.h2;
+    float atu = 4.f * aB * inv_h2, atw = 2.f * aB * inv_h2;
+    float A[6] = {k * f.N[0] + ws * f.om.x * f.om.x + atu, k * f.N[1] + ws * f.om.y * f.om.y + atu,
+                  k * f.N[2] + ws * f.om.z * f.om.z + atw, k * f.N[3] + ws * f.om.x * f.om.y,
+                  k * f.N[4] + ws * f.om.x * f.om.z,       k * f.N[5] + ws * f.om.y * f.om.z};
+    V3 rhs = {-C.x - atu * lam.x, -C.y - atu * lam.y, -C.z - atw * lam.z};
+    V3 dl = solve_sym3(A, rhs);
+    lam.x += dl.x;
+    lam.y += dl.y;
+    lam.z += dl.z;
+    d.ds = ws * dot(f.om, dl);
+    rel_increments(f, qa, dl, s * f.h2, d.dtha, d.dthb);
+}
+
+__device__ __forceinline__ void vtx_volbend(const float4 &qa, const float4 &qb, float s, float s_prev, float s_next,
+                                            float kappa, float imr2a, float imr2b, float ws, float4 rv0, float aVb,
+                                            float4 &lam, float &lam_v, float inv_h2, VtxDelta &d)
+{
+    RelFrame f;
+    rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
+    float s2 = s * s, s3 = s2 * s;
+    float cu = s3 * f.om.x - rv0.x, cv = s3 * f.om.y - rv0.y;
+    float k = s3 * s3 * f.h2 * f.h2;
+    float js_u = 3.f * s2 * f.om.x, js_v = 3.f * s2 * f.om.y;
+    float at = aVb * inv_h2;
+    float a00 = k * f.N[0] + ws * js_u * js_u + at;
+    float a11 = k * f.N[1] + ws * js_v * js_v + at;
+    float a01 = k * f.N[3] + ws * js_u * js_v;
+    float r0 = -cu - at * lam.w, r1 = -cv - at * lam_v;
+    const float sc = 1.f / fmaxf(fmaxf(fabsf(a00), fabsf(a11)), 1e-30f);  // keep the determinant in range
+    a00 *= sc; a11 *= sc; a01 *= sc; r0 *= sc; r1 *= sc;
+    float id = 1.f / (a00 * a11 - a01 * a01);
+    float d0 = (a11 * r0 - a01 * r1) * id, d1 = (a00 * r1 - a01 * r0) * id;
+    lam.w += d0;
+    lam_v += d1;
+    d.ds = ws * (js_u * d0 + js_v * d1);
+    rel_increments(f, qa, v3(d0, d1, 0.f), s3 * f.h2, d.dtha, d.dthb);
+}
+
 __device__ __forceinline__ void project_vertex(float4 &qa, float4 &qb, float &s, float s_prev, float s_next,
                                                float la, float lb, float imr2a, float imr2b, float ws,
                                                float4 rv0, float aB, float aVb, float4 &lam, float &lam_v,
                                                float inv_h2, bool volume)
 {
     const float kappa = 4.f / (la + lb);
-    // ---- B: bend / twist
-    {
-        RelFrame f;
-        rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
-        V3 C = s * f.om - v3(rv0.x, rv0.y, rv0.z);
-        float k = s * s * f.h2 * f.h2;
-        float atu = 4.f * aB * inv_h2, atw = 2.f * aB * inv_h2;
-        float A[6] = {k * f.N[0] + ws * f.om.x * f.om.x + atu, k * f.N[1] + ws * f.om.y * f.om.y + atu,
-                      k * f.N[2] + ws * f.om.z * f.om.z + atw, k * f.N[3] + ws * f.om.x * f.om.y,
-                      k * f.N[4] + ws * f.om.x * f.om.z,       k * f.N[5] + ws * f.om.y * f.om.z};
-        V3 rhs = {-C.x - atu * lam.x, -C.y - atu * lam.y, -C.z - atw * lam.z};
-        V3 dl = solve_sym3(A, rhs);
-        lam.x += dl.x;
-        lam.y += dl.y;
-        lam.z += dl.z;
-        float ds = ws * dot(f.om, dl);
-        apply_rel(f, qa, qb, dl, s * f.h2);
-        s += ds;
-    }
-    // ---- Vb: volume bending
+    VtxDelta d;
+    vtx_bend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aB, lam, inv_h2, d);
+    rotate_by(qa, d.dtha);
+    rotate_by(qb, d.dthb);
+    s += d.ds;
     if (volume) {
-        RelFrame f;
-        rel_frame(f, qa, qb, 0.5f * (s_prev + s), 0.5f * (s + s_next), kappa, imr2a, imr2b);
-        float s2 = s * s, s3 = s2 * s;
-        float cu = s3 * f.om.x - rv0.x, cv = s3 * f.om.y - rv0.y;
-        float k = s3 * s3 * f.h2 * f.h2;
-        float js_u = 3.f * s2 * f.om.x, js_v = 3.f * s2 * f.om.y;
-        float at = aVb * inv_h2;
-        float a00 = k * f.N[0] + ws * js_u * js_u + at;
-        float a11 = k * f.N[1] + ws * js_v * js_v + at;
-        float a01 = k * f.N[3] + ws * js_u * js_v;
-        float r0 = -cu - at * lam.w, r1 = -cv - at * lam_v;
-        const float sc = 1.f / fmaxf(fmaxf(fabsf(a00), fabsf(a11)), 1e-30f);  // keep the determinant in range
-        a00 *= sc; a11 *= sc; a01 *= sc; r0 *= sc; r1 *= sc;
-        float id = 1.f / (a00 * a11 - a01 * a01);
-        float d0 = (a11 * r0 - a01 * r1) * id, d1 = (a00 * r1 - a01 * r0) * id;
-        lam.w += d0;
-        lam_v += d1;
-        float ds = ws * (js_u * d0 + js_v * d1);
-        apply_rel(f, qa, qb, v3(d0, d1, 0.f), s3 * f.h2);
-        s += ds;
+        vtx_volbend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aVb, lam, lam_v, inv_h2, d);
+        rotate_by(qa, d.dtha);
+        rotate_by(qb, d.dthb);
+        s += d.ds;
+    }
+}
+
+__device__ __forceinline__ void jacobi_vertex(const float4 &qa, const float4 &qb, float s, float s_prev, float s_next,
+                                              float la, float lb, float imr2a, float imr2b, float ws, float4 rv0,
+                                              float aB, float aVb, float4 &lam, float &lam_v, float inv_h2,
+                                              bool volume, VtxDelta &sum)
+{
+    const float kappa = 4.f / (la + lb);
+    vtx_bend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aB, lam, inv_h2, sum);
+    if (volume) {
+        VtxDelta d;
+        vtx_volbend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aVb, lam, lam_v, inv_h2, d);
+        sum.dtha = sum.dtha + d.dtha;
+        sum.dthb = sum.dthb + d.dthb;
+        sum.ds += d.ds;
     }
 }
 
@@ -296,17 +410,28 @@ __device__ __forceinline__ void project_vertex(float4 &qa, float4 &qb, float &s,
 // jn = 1/(l_b lv), lv = (l_a + l_b)/2 (Sec. 5 E_bending, Laplacian of Sec. 7.5
 // read as the second derivative, s_bar = 1):
 //  L  C = jn (sn - s) - jp (s - sp),  J = (jp, -(jp + jn), jn)
-__device__ __forceinline__ void project_laplacian(float &sp, float &s, float &sn, float wp, float w, float wn,
-                                                  float4 rv2, float &lam, float inv_h2)
+__device__ __forceinline__ void laplacian_increments(float sp, float s, float sn, float wp, float w, float wn,
+                                                     float4 rv2, float &lam, float inv_h2, float &dsp, float &ds,
+                                                     float &dsn)
 {
     const float jp = rv2.x, jn = rv2.y, jc = -(jp + jn);
     const float C = jn * (sn - s) - jp * (s - sp);
     const float at = rv2.z * inv_h2;
     const float dl = (-C - at * lam) / (wp * jp * jp + w * jc * jc + wn * jn * jn + at);
     lam += dl;
-    sp += wp * jp * dl;
-    s += w * jc * dl;
-    sn += wn * jn * dl;
+    dsp = wp * jp * dl;
+    ds = w * jc * dl;
+    dsn = wn * jn * dl;
+}
+
+__device__ __forceinline__ void project_laplacian(float &sp, float &s, float &sn, float wp, float w, float wn,
+                                                  float4 rv2, float &lam, float inv_h2)
+{
+    float dsp, ds, dsn;
+    laplacian_increments(sp, s, sn, wp, w, wn, rv2, lam, inv_h2, dsp, ds, dsn);
+    sp += dsp;
+    s += ds;
+    sn += dsn;
 }
 
 // ---------------------------------------------------------------- pills

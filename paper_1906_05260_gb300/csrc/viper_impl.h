@@ -39,6 +39,7 @@ struct Params {
     // surface bending per vertex: (1/(l_a lv), 1/(l_b lv), compliance, 0), zero at rod ends
     const float4 *RV2;
     int surface;
+    int jacobi;  // rod constraints by Jacobi with averaging instead of four-colour Gauss-Seidel
     const float2 *RS1;
     const int *seg_v0, *vtx_seg, *seg_group;
     // Vertex positions are stored relative to a per-rod FP32 origin (the rod's

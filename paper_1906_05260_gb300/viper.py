@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libviper.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
-FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING = 1, 2, 4
+FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI = 1, 2, 4, 8
 SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
 SOLVER_AUTO = -1
 PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE, PROF_PAIRS = 0, 1, 2, 3, 4, 5, 6
@@ -222,7 +222,8 @@ def make_desc(scene, stream_handle=None, max_pairs=0):
     desc.planes = d(scene.planes if n_planes else np.zeros(4))
     desc.contact_compliance = float(scene.contact_compliance)
     desc.flags = ((FLAG_CONTACTS if scene.contacts else 0) | (FLAG_VOLUME if scene.volume else 0)
-                  | (FLAG_SURFACE_BENDING if getattr(scene, "surface_bending", False) else 0))
+                  | (FLAG_SURFACE_BENDING if getattr(scene, "surface_bending", False) else 0)
+                  | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0))
     desc.max_pairs = int(max_pairs)
     desc.stream = stream_handle
     return desc, keep

@@ -333,3 +333,59 @@ def test_surface_bending_scale_bump_matches_oracle(V):
     assert g.sync() == 0
     e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, rad_tol=1e-5, what="scale bump")
     print("surface bending scale bump errors vs FP64:", e)
+
+
+# --------------------------------------------------------------------------
+# Jacobi with averaging (Sec. 7 engine) instead of the four colours
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver", [1, 2], ids=["batched", "frame"])
+def test_jacobi_plain_small(V, solver):
+    sc = dataclasses.replace(S.plain_small(), jacobi=True)
+    g, o = _pair(V, sc, solver)
+    g.frame(); o.frame()
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="jacobi, 1 frame")
+    for _ in range(19):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e20 = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_100, rad_tol=1e-4, ang_tol=1e-3,
+                        what="jacobi, 20 frames")
+    print("jacobi plain_small errors vs FP64, 1 / 20 frames:", e, e20)
+
+
+@pytest.mark.parametrize("solver", [1, 2], ids=["batched", "frame"])
+def test_jacobi_muscle_rig_with_surface_bending(V, solver):
+    sc = dataclasses.replace(S.muscle_rig(n_rods=60, mesh_verts=0), jacobi=True, surface_bending=True)
+    g, o = _pair(V, sc, solver)
+    for _ in range(2):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="jacobi + surface bending, muscle rig")
+    print("jacobi + surface bending muscle_rig 2 frames errors vs FP64:", e)
+
+
+def test_jacobi_batching_sampled_rods(V):
+    """Ragged rods of 4..256 vertices, 20 x 8: a sample of rods against the oracle."""
+    sc = dataclasses.replace(S.batching(n_rods=512), jacobi=True)
+    g = V.Scene(sc, resident_max=256)
+    g.frame()
+    assert g.sync() == 0
+    rods = np.arange(0, sc.n_rods, 37)
+    sub = sc.subset(rods)
+    o = oracle.OracleScene(sub)
+    o.frame()
+    st = g.get_state()
+    off = sc.rod_offsets
+    vsel = np.concatenate([np.arange(off[r], off[r + 1]) for r in rods])
+    ssel = np.concatenate([np.arange(off[r] - r, off[r + 1] - r - 1) for r in rods])
+    gs = {"x4": st["x4"][vsel], "q4": st["q4"][ssel]}
+    e = assert_parity(sub, gs, o.get_state(), POS_TOL_1, what="jacobi batching sample")
+    print("jacobi batching sample errors vs FP64:", e)
+
+
+def test_jacobi_needs_the_shared_memory_solvers(V):
+    sc = dataclasses.replace(S.plain_small(), jacobi=True)
+    g = V.Scene(sc)
+    assert V.lib().viper_set_solver(g.handle, V.SOLVER_PLAIN, 4, 256) == V.EINVAL
+    g.frame()  # the scene keeps its previous solver
+    assert g.sync() == 0
