@@ -258,6 +258,64 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
         g.close()
     out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
     out["frame_over_plain"] = out["frame"]["value"] / out["plain"]["value"]
+    # the same workload with the paper's Jacobi ordering, and with surface bending
+    import dataclasses
+    for key, variant in (("jacobi", dict(jacobi=True)), ("surface_bending", dict(surface_bending=True))):
+        g = V.Scene(dataclasses.replace(sc, **variant), resident_max=256)
+        st = g.stream
+        for _ in range(3):
+            g.step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for i in range(frames):
+            with torch.cuda.stream(st):
+                flush.fill_(i & 0xFF)
+                e0.record(st)
+                g.step()
+                e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        if g.sync() != 0:
+            raise SystemExit(f"{key} variant failed")
+        ms = reduce_max(dist, sum(ts) / len(ts))
+        out[key] = {"value": reduce_sum(dist, units) / (ms * 1e-3), "unit": "rod-vertex substeps/s",
+                    "ms_per_frame": ms, "over_colours": out["batched"]["ms_per_frame"] / ms}
+        g.close()
+    return out
+
+
+def bench_convergence(V, np_):
+    """E9 (the paper's convergence test): a 12-vertex rod whose end bars are
+    pulled to twice its length at once; distance of the state after N
+    iterations (one substep) to the ordering's own limit, on the GPU."""
+    import dataclasses
+    from paper_1906_05260_gb300 import scenes as S
+    n = 12
+    off = np_.array([0, n], np_.int32)
+    pos = np_.zeros((n, 3))
+    pos[:, 0] = np_.arange(n) * 0.01
+    q = np_.tile(S.quat_from_z(np_.array([1.0, 0, 0])), (n - 1, 1))
+    sc = S.Scene(name="e9", rod_offsets=off, rest_pos=pos, rest_quat=q, radius=np_.full(n, 0.01),
+                 density=np_.array([1000.0]), c_stretch=np_.array([1e-9]), c_bend=np_.array([1e-7]),
+                 c_volume=np_.array([1e-9]), group=np_.zeros(1, np_.int32), gravity=np_.zeros(3),
+                 pin_vertex=np_.array([0, n - 1], np_.int32), pin_bone=np_.array([-1, -1], np_.int32),
+                 pin_offset=np_.array([[0, 0, 0], [2.0 * 0.01 * (n - 1), 0, 0]]), bones=None,
+                 planes=np_.zeros((0, 4)), contact_compliance=1e-9, contacts=False, volume=True,
+                 dt=1 / 60, substeps=1, iterations=1, frames=1)
+
+    def run(jacobi, iters):
+        g = V.Scene(dataclasses.replace(sc, jacobi=jacobi))
+        g.step(sc.dt, 1, iters)
+        x = g.get_state()["x4"][:, :3].astype(np_.float64)
+        g.close()
+        return x
+
+    out = {"workload": "E9: 12-vertex rod, bars pulled to 2x rest length at once, one substep of N iterations",
+           "metric": "max |x_N - x_limit| (m), limit = 4096 iterations (colours) / 16384 (Jacobi)"}
+    for jacobi, limit_iters, key in ((False, 4096, "colours"), (True, 16384, "jacobi")):
+        lim = run(jacobi, limit_iters)
+        out[key] = {str(it): float(np_.abs(run(jacobi, it) - lim).max()) for it in (1, 4, 16, 64, 256)}
     return out
 
 
@@ -551,8 +609,10 @@ def main():
     # ---- batching workload (4096 rods, 20 x 8, no contacts): batched vs plain and
     # the shared-memory rod kernel's roofline
     batching = None
+    convergence = None
     if not args.no_batching:
         batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
+        convergence = bench_convergence(V, np)
 
     # ---- many scenes at once: the multi-scene step against per-scene graphs
     multi = None
@@ -602,6 +662,7 @@ def main():
         "plain": plain,
         "graph_batched": graph,
         "batching": batching,
+        "convergence": convergence,
         "multi_scene": multi,
         "serving": serving,
     }
