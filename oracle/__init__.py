@@ -36,6 +36,7 @@ class _Desc(C.Structure):
         ("bone_quat", _dp), ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("contacts", C.c_int), ("volume", C.c_int),
         ("surface_bending", C.c_int), ("jacobi", C.c_int),
+        ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
     ]
 
 
@@ -83,6 +84,8 @@ def lib():
         L.vo_constraint_rms.argtypes = [C.c_void_p, _dp]
         L.vo_laplacian_constraint.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                               _dp, _dp]
+        L.vo_polar_rotation.argtypes = [_dp, _dp]
+        L.vo_shape_match.argtypes = [C.c_void_p]
         L.vo_laplacian_compliance.restype = C.c_double
         L.vo_laplacian_compliance.argtypes = [C.c_void_p, C.c_int]
         _lib = L
@@ -149,6 +152,10 @@ class OracleScene:
         desc.volume = int(bool(scene.volume))
         desc.surface_bending = int(bool(getattr(scene, "surface_bending", False)))
         desc.jacobi = int(bool(getattr(scene, "jacobi", False)))
+        if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
+            desc.n_bundles = len(scene.bundle_offsets) - 1
+            desc.bundle_offsets = i(scene.bundle_offsets)
+            desc.bundle_rods = i(scene.bundle_rods)
         h = L.vo_create(C.byref(desc))
         if not h:
             raise ValueError("vo_create rejected the scene")
@@ -247,6 +254,10 @@ class OracleScene:
         lib().vo_colouring(self._h, sc.ctypes.data_as(_ip), vc.ctypes.data_as(_ip))
         return sc, vc
 
+    def shape_match(self):
+        """Apply the bundles' shape matching (Sec. 7.3) to the current state once."""
+        lib().vo_shape_match(self._h)
+
     def laplacian_compliance(self, i):
         return float(lib().vo_laplacian_compliance(self._h, int(i)))
 
@@ -254,6 +265,14 @@ class OracleScene:
         out = np.zeros(6)
         lib().vo_constraint_rms(self._h, _d(out)[1])
         return dict(zip(["S", "V", "X", "G", "B", "Vb"], out))
+
+
+def polar_rotation(A):
+    """The rotation maximising trace(R^T A) (3x3, row-major)."""
+    a = np.ascontiguousarray(A, dtype=np.float64).reshape(9)
+    r = np.zeros(9)
+    lib().vo_polar_rotation(_d(a)[1], _d(r)[1])
+    return r.reshape(3, 3)
 
 
 def laplacian_constraint(s_prev, s, s_next, la, lb):

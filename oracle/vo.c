@@ -55,6 +55,8 @@ struct vo_scene {
     double *lam_vtx;   /* 5 per vertex: B(3), Vb(2)    */
     double *lam_lap;   /* 1 per vertex: surface bending */
     int surface, jacobi;
+    int nbund;
+    int *bund_off, *bund_rods;
     /* Jacobi pass: summed corrections and the number of constraints acting */
     double *jdx, *jds, *jdth;
     int *jcx, *jcs, *jcq;
@@ -646,6 +648,166 @@ static void colour_sweep(vo_scene *S, int colour, double h)
 }
 
 /* ------------------------------------------------------------------------ */
+/* scale-invariant shape matching of rod bundles (Sec. 7.3, "Bundling")      */
+/* ------------------------------------------------------------------------ */
+
+/* Largest eigenpair of a symmetric 4x4 matrix by cyclic Jacobi rotations. */
+static void sym4_top_eigenvector(const double *M, double *v)
+{
+    double a[16], V[16];
+    memcpy(a, M, sizeof a);
+    for (int i = 0; i < 16; ++i) V[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) off += a[4 * p + q] * a[4 * p + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                double apq = a[4 * p + q];
+                if (fabs(apq) < 1e-300) continue;
+                double theta = (a[4 * q + q] - a[4 * p + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 4; ++k) {  /* columns p, q */
+                    double akp = a[4 * k + p], akq = a[4 * k + q];
+                    a[4 * k + p] = c * akp - sn * akq;
+                    a[4 * k + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) {  /* rows p, q */
+                    double apk = a[4 * p + k], aqk = a[4 * q + k];
+                    a[4 * p + k] = c * apk - sn * aqk;
+                    a[4 * q + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double vkp = V[4 * k + p], vkq = V[4 * k + q];
+                    V[4 * k + p] = c * vkp - sn * vkq;
+                    V[4 * k + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    int best = 0;
+    for (int i = 1; i < 4; ++i)
+        if (a[5 * i] > a[5 * best]) best = i;
+    for (int k = 0; k < 4; ++k) v[k] = V[4 * k + best];
+}
+
+/*
+ * R* = argmax over rotations of trace(R^T A) (Umeyama's optimal rotation, which
+ * the paper obtains with an iterative method).  Horn's closed form: with
+ * M = A^T (source x target correlations), the unit quaternion maximising it is
+ * the top eigenvector of the 4x4 matrix N built from M.
+ */
+static void polar_quat(const double *A, double *qo)
+{
+    double Sxx = A[0], Syx = A[1], Szx = A[2], Sxy = A[3], Syy = A[4], Szy = A[5], Sxz = A[6], Syz = A[7],
+           Szz = A[8];  /* S_ab = M[a][b] = A[b][a] */
+    double N[16] = {Sxx + Syy + Szz, Syz - Szy,        Szx - Sxz,        Sxy - Syx,
+                    Syz - Szy,       Sxx - Syy - Szz,  Sxy + Syx,        Szx + Sxz,
+                    Szx - Sxz,       Sxy + Syx,        -Sxx + Syy - Szz, Syz + Szy,
+                    Sxy - Syx,       Szx + Sxz,        Syz + Szy,        -Sxx - Syy + Szz};
+    double v[4];
+    sym4_top_eigenvector(N, v);  /* (w, x, y, z) */
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    qo[0] = v[1] / n;
+    qo[1] = v[2] / n;
+    qo[2] = v[3] / n;
+    qo[3] = v[0] / n;
+}
+
+int vo_polar_rotation(const double *A, double *R)
+{
+    double q[4];
+    polar_quat(A, q);
+    rotmat(q, R);
+    return 0;
+}
+
+/*
+ * One bundle cross-section (vertex k of every rod of the bundle), Sec. 7.3:
+ * T_i = [s_i R_i, c_i] with c_i the vertex position, s_i its scale and R_i the
+ * frame of segment k; rest T_bar_i with s_bar = 1.  T* = [s* R*, c*] minimises
+ * sum_i |T* T_bar_i - T_i|^2:
+ *   A  = sum_i [s_i R_i, c_i - mu][R_bar_i, c_bar_i - mu_bar]^T,
+ *   R* = argmax trace(R^T A),
+ *   s* = sum_i sum(R* B_bar_i o B_i) / sum_i sum(B_bar_i o B_bar_i) = <R*, A> / sum_i (3 + |c_bar_i - mu_bar|^2),
+ *   c* = mu - s* R* mu_bar,
+ * then T_i <- T* T_bar_i: c_i = s* R* c_bar_i + c*, s_i = s*, frame R* R_bar_i.
+ * Readings: the last vertex of a rod has no frame of its own (rods have one
+ * segment fewer than vertices), so the last cross-section uses positions and
+ * scales only (no R terms in A or in the denominator) and sets no frame; a
+ * cross-section with a pinned vertex is left to its pins.
+ */
+static void match_cross_section(vo_scene *S, const int *rods, int m, int k)
+{
+    int N = S->off[rods[0] + 1] - S->off[rods[0]];
+    double mu[3] = {0, 0, 0}, mub[3] = {0, 0, 0};
+    for (int i = 0; i < m; ++i) {
+        int v = S->off[rods[i]] + k;
+        if (S->pin_of_v[v] >= 0) return;
+        for (int c = 0; c < 3; ++c) {
+            mu[c] += S->x[3 * v + c] / m;
+            mub[c] += S->xbar[3 * v + c] / m;
+        }
+    }
+    const int framed = k < N - 1;
+    double A[9] = {0}, den = 0.0;
+    for (int i = 0; i < m; ++i) {
+        int r = rods[i], v = S->off[r] + k;
+        double Ri[9] = {0}, Rb[9] = {0}, d[3], db[3];
+        if (framed) {
+            int g = S->off[r] - r + k;
+            rotmat(S->q + 4 * g, Ri);
+            rotmat(S->qbar + 4 * g, Rb);
+        }
+        for (int c = 0; c < 3; ++c) {
+            d[c] = S->x[3 * v + c] - mu[c];
+            db[c] = S->xbar[3 * v + c] - mub[c];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int c = 0; c < 3; ++c) acc += S->s[v] * Ri[3 * a + c] * Rb[3 * b + c];
+                A[3 * a + b] += acc + d[a] * db[b];
+            }
+        den += (framed ? 3.0 : 0.0) + dot3(db, db);
+    }
+    double qs[4], Rs[9];
+    polar_quat(A, qs);
+    rotmat(qs, Rs);
+    double num = 0.0;
+    for (int j = 0; j < 9; ++j) num += Rs[j] * A[j];
+    double ss = num / den;
+    for (int i = 0; i < m; ++i) {
+        int r = rods[i], v = S->off[r] + k;
+        double db[3], rdb[3];
+        for (int c = 0; c < 3; ++c) db[c] = S->xbar[3 * v + c] - mub[c];
+        matvec3(Rs, db, rdb);
+        for (int c = 0; c < 3; ++c) S->x[3 * v + c] = mu[c] + ss * rdb[c];
+        S->s[v] = ss;
+        if (framed) {
+            int g = S->off[r] - r + k;
+            double qn[4];
+            qmul(qs, S->qbar + 4 * g, qn);
+            qnormalize(qn);
+            memcpy(S->q + 4 * g, qn, sizeof qn);
+        }
+    }
+}
+
+int vo_shape_match(vo_scene *S)
+{
+    for (int b = 0; b < S->nbund; ++b) {
+        const int *rods = S->bund_rods + S->bund_off[b];
+        int m = S->bund_off[b + 1] - S->bund_off[b];
+        if (m < 1) continue;
+        int N = S->off[rods[0] + 1] - S->off[rods[0]];
+        for (int k = 0; k < N; ++k) match_cross_section(S, rods, m, k);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* broadphase (Sec. 7.1)                                                     */
 /* ------------------------------------------------------------------------ */
 
@@ -1101,6 +1263,24 @@ vo_scene *vo_create(const vo_desc *d)
     S->volume = d->volume;
     S->surface = d->surface_bending;
     S->jacobi = d->jacobi;
+    S->nbund = d->n_bundles > 0 ? d->n_bundles : 0;
+    S->bund_off = xcalloc((size_t)S->nbund + 1, sizeof(int));
+    if (S->nbund) {
+        memcpy(S->bund_off, d->bundle_offsets, sizeof(int) * ((size_t)S->nbund + 1));
+        int nbr = S->bund_off[S->nbund];
+        S->bund_rods = xcalloc((size_t)nbr, sizeof(int));
+        memcpy(S->bund_rods, d->bundle_rods, sizeof(int) * (size_t)nbr);
+        for (int b = 0; b < S->nbund; ++b)  /* one vertex count per bundle */
+            for (int i = S->bund_off[b]; i < S->bund_off[b + 1]; ++i) {
+                int r0 = S->bund_rods[S->bund_off[b]], r = S->bund_rods[i];
+                if (r < 0 || r >= nr || S->off[r + 1] - S->off[r] != S->off[r0 + 1] - S->off[r0]) {
+                    vo_destroy(S);
+                    return NULL;
+                }
+            }
+    } else {
+        S->bund_rods = xcalloc(1, sizeof(int));
+    }
 
     /* state starts at rest (Sec. 4: the rest pose is the initial pose) */
     S->x = xcalloc(3 * (size_t)nv, sizeof(double));
@@ -1138,6 +1318,7 @@ void vo_destroy(vo_scene *S)
                     S->pin_of_v, S->pin_bone, S->pin_off, S->bq0, S->bt0, S->bq1, S->bt1, S->bq,
                     S->bt, S->planes, S->x, S->s, S->v, S->sd, S->q, S->w, S->xp, S->sp, S->qp,
                     S->lam_seg, S->lam_vtx, S->lam_lap, S->jdx, S->jds, S->jdth, S->jcx, S->jcs, S->jcq,
+                    S->bund_off, S->bund_rods,
                     S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(S);
@@ -1269,6 +1450,8 @@ int vo_step(vo_scene *S, double dt, int substeps, int iterations)
             }
             if ((S->contacts && S->npairs > 0) || S->np > 0) contact_pass(S, h);
         }
+        /* bundles: shape matching as a post-process after the iterations (Sec. 7.3) */
+        if (S->nbund > 0 && iterations > 0) vo_shape_match(S);
         /* velocity update: reading (not written out in the paper): the
          * position-based difference of the substep's start and end states,
          * omega from the relative rotation q q_prev^* (double cover resolved). */

@@ -48,6 +48,9 @@ typedef struct vo_desc {
     int surface_bending;         /* scale-Laplacian constraints on/off            */
     int jacobi;                  /* rod constraints: 0 four-colour Gauss-Seidel,  */
                                  /* 1 Jacobi with averaging (Sec. 7 engine)       */
+    int n_bundles;               /* rod bundles for shape matching (Sec. 7.3)     */
+    const int *bundle_offsets;   /* [n_bundles+1] CSR into bundle_rods            */
+    const int *bundle_rods;      /* rods of each bundle, all of one vertex count  */
 } vo_desc;
 
 vo_scene *vo_create(const vo_desc *d);
@@ -83,6 +86,11 @@ int vo_laplacian_constraint(double s_prev, double s, double s_next, double la, d
                             double *J);
 /* Compliance of the surface-bending constraint at vertex i (0 at rod ends). */
 double vo_laplacian_compliance(const vo_scene *s, int i);
+/* Rotation R (row-major 3x3) maximising trace(R^T A): the rotational part
+ * of the polar decomposition of A, by Horn's quaternion eigenvector. */
+int vo_polar_rotation(const double *A, double *R);
+/* Apply the bundles' shape matching (Sec. 7.3) to the current state once. */
+int vo_shape_match(vo_scene *s);
 /* Barycentric coordinate of the closest sphere of a tapered capsule (App. D). */
 double vo_pill_project(const double *c1, double r1, const double *c2, double r2,
                        const double *x);

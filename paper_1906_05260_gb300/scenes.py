@@ -103,6 +103,8 @@ class Scene:
     mesh: Optional[Mesh] = None
     surface_bending: bool = False     # scale-Laplacian constraints (Sec. 5, E_bending)
     jacobi: bool = False              # rod constraints by Jacobi with averaging (Sec. 7 engine)
+    bundle_offsets: Optional[np.ndarray] = None  # int32 [n_bundles+1] CSR into bundle_rods (Sec. 7.3)
+    bundle_rods: Optional[np.ndarray] = None     # int32 rods of each bundle (equal vertex counts)
 
     @property
     def n_rods(self) -> int:
@@ -354,6 +356,68 @@ def muscle_rig(seed: int = 1, n_rods: int = 200, mesh_verts: int = 200_000, n_bo
         iterations=4, frames=frames, mesh=mesh)
 
 
+def bundled_muscles(seed: int = 6, n_muscles: int = 24, fibers: int = 7, n_verts: int = 16, n_bones: int = 8,
+                    frames: int = 300) -> Scene:
+    """Muscles made of bundled fibre rods (Sec. 7.3, Sec. 7.5 muscles).
+
+    Bones as in muscle_rig.  Each muscle spans a random bone gap and holds
+    `fibers` rods of `n_verts` vertices in a hexagonal pattern (one central
+    fibre, the others 22 mm around it) whose ends are pinned to the two bones;
+    radius profile r(t) = r0 (0.5 + sin(pi t)), r0 = 8 mm.  The fibres of a
+    muscle form one bundle (one shape-matching cross-section per vertex index)
+    and one collision group (no intra-muscle contacts); muscles collide with
+    each other.  Stretch / bend compliances log-uniform [1e-8, 1e-5] per muscle.
+    """
+    rng = np.random.default_rng(seed)
+    spacing = 0.3
+    bones = _bone_track(rng, n_bones, spacing)
+    gap = rng.integers(0, n_bones - 1, n_muscles)
+    n_rods = n_muscles * fibers
+    off = (np.arange(n_rods + 1) * n_verts).astype(np.int32)
+    nv = int(off[-1])
+    pos = np.zeros((nv, 3))
+    rad = np.zeros(nv)
+    ring = [np.zeros(2)] + [0.022 * np.array([math.cos(a), math.sin(a)])
+                            for a in np.arange(fibers - 1) * 2 * math.pi / max(fibers - 1, 1)]
+    counts = np.zeros(n_bones, np.int64)
+    pin_v, pin_b, pin_o = [], [], []
+    group = np.zeros(n_rods, np.int32)
+    cs_m = _log_uniform(rng, 1e-8, 1e-5, n_muscles)
+    cb_m = _log_uniform(rng, 1e-8, 1e-5, n_muscles)
+    t = np.linspace(0.0, 1.0, n_verts)
+    for m in range(n_muscles):
+        s = counts[gap[m]]
+        counts[gap[m]] += 1
+        y0 = (s // 4 - 2) * 0.13
+        z0 = (s % 4 - 1.5) * 0.13
+        for f in range(fibers):
+            k = m * fibers + f
+            oyz = ring[f]
+            start_local = np.array([0.04, y0 + oyz[0], z0 + oyz[1]])
+            end_local = np.array([-0.04, y0 + oyz[0], z0 + oyz[1]])
+            A = bones.trans0[gap[m]] + start_local
+            B = bones.trans0[gap[m] + 1] + end_local
+            sl = slice(off[k], off[k + 1])
+            pos[sl] = A[None, :] + t[:, None] * (B - A)[None, :]
+            rad[sl] = 0.008 * (0.5 + np.sin(math.pi * t))
+            pin_v += [off[k], off[k + 1] - 1]
+            pin_b += [gap[m], gap[m] + 1]
+            pin_o += [start_local, end_local]
+            group[k] = m
+    ns = nv - n_rods
+    quat = np.tile(quat_from_z(np.array([1.0, 0.0, 0.0])), (ns, 1))
+    cs = np.repeat(cs_m, fibers)
+    cb = np.repeat(cb_m, fibers)
+    return Scene(
+        name="bundled_muscles", rod_offsets=off, rest_pos=pos, rest_quat=quat, radius=rad,
+        density=np.full(n_rods, 1000.0), c_stretch=cs, c_bend=cb, c_volume=cs.copy(), group=group,
+        gravity=GRAVITY.copy(), pin_vertex=np.array(pin_v, np.int32), pin_bone=np.array(pin_b, np.int32),
+        pin_offset=np.array(pin_o), bones=bones, planes=np.zeros((0, 4)), contact_compliance=1e-9,
+        contacts=True, volume=True, dt=1.0 / 60.0, substeps=10, iterations=4, frames=frames,
+        bundle_offsets=(np.arange(n_muscles + 1) * fibers).astype(np.int32),
+        bundle_rods=np.arange(n_rods, dtype=np.int32))
+
+
 def batching(seed: int = 2, n_rods: int = 4096, nmin: int = 4, nmax: int = 256,
              seg_len: float = 0.01, frames: int = 300) -> Scene:
     """Independent rods of log-uniform 4..256 vertices with random initial bends.
@@ -505,6 +569,7 @@ WORKLOADS = {
     "muscle_rig": muscle_rig,
     "batching": batching,
     "hair": hair,
+    "bundled_muscles": bundled_muscles,
 }
 
 

@@ -785,3 +785,134 @@ def test_jacobi_converges_more_slowly_than_colouring():
         d = dist[jacobi]
         assert all(a > b for a, b in zip(d, d[1:])), (jacobi, d)
     assert all(g < j for g, j in zip(dist[False][1:], dist[True][1:])), dist
+
+
+# --------------------------------------------------------------------------
+# Scale-invariant shape matching of bundles (Sec. 7.3)
+# --------------------------------------------------------------------------
+
+def test_polar_rotation_matches_svd():
+    """Horn's quaternion eigenvector against numpy's SVD polar factor U diag(1,1,det) V^T."""
+    rng = np.random.default_rng(31)
+    for _ in range(50):
+        A = rng.normal(size=(3, 3)) * rng.uniform(0.01, 10)
+        U, _, Vt = np.linalg.svd(A)
+        D = np.diag([1.0, 1.0, np.sign(np.linalg.det(U @ Vt))])
+        np.testing.assert_allclose(oracle.polar_rotation(A), U @ D @ Vt, atol=1e-12)
+
+
+def _free_bundle_scene():
+    sc = S.bundled_muscles(n_muscles=3, fibers=7, n_verts=9, n_bones=3)
+    return dataclasses.replace(sc, pin_vertex=np.zeros(0, np.int32), pin_bone=np.zeros(0, np.int32),
+                               pin_offset=np.zeros((0, 3)), gravity=np.zeros(3), contacts=False)
+
+
+def test_shape_match_keeps_an_exact_similarity_fixed():
+    """A state that is a similarity s R (.) + t of the rest pose (positions,
+    scales s, frames R q_bar) is a fixed point of the post-process."""
+    rng = np.random.default_rng(32)
+    sc = _free_bundle_scene()
+    qR = _rand_quat(rng)
+    R = np.stack([_rot(qR, e) for e in np.eye(3)], axis=1)
+    s, t = 1.17, np.array([0.3, -0.2, 0.5])
+    o = oracle.OracleScene(sc)
+    x = sc.rest_pos @ R.T * s + t
+    q = S.quat_mul(np.tile(qR, (sc.ns, 1)), sc.rest_quat)
+    o.set_state(x=x, s=np.full(sc.nv, s), q=q)
+    o.shape_match()
+    st = o.get_state()
+    np.testing.assert_allclose(st["x"], x, atol=1e-12)
+    np.testing.assert_allclose(st["s"], s, atol=1e-12)
+    np.testing.assert_allclose(np.abs((st["q"] * q).sum(1)), 1.0, atol=1e-12)
+
+
+def test_shape_match_projects_onto_similarities_and_is_idempotent():
+    """After the post-process every cross-section is an exact similarity of its
+    rest (all pairwise distances scaled by one factor, equal scales), and a
+    second application changes nothing."""
+    rng = np.random.default_rng(33)
+    sc = _free_bundle_scene()
+    o = oracle.OracleScene(sc)
+    x = sc.rest_pos + rng.normal(size=sc.rest_pos.shape) * 3e-3
+    q = S.quat_mul(S.axis_angle_quat(rng.normal(size=(sc.ns, 3)) * 0.1), sc.rest_quat)
+    o.set_state(x=x, s=rng.uniform(0.9, 1.1, sc.nv), q=q)
+    o.shape_match()
+    a = o.get_state()
+    n_v = int(sc.rod_offsets[1] - sc.rod_offsets[0])
+    for b in range(len(sc.bundle_offsets) - 1):
+        rods = sc.bundle_rods[sc.bundle_offsets[b]:sc.bundle_offsets[b + 1]]
+        for k in range(n_v):
+            v = sc.rod_offsets[rods] + k
+            d = np.linalg.norm(a["x"][v][:, None] - a["x"][v][None], axis=2)
+            d0 = np.linalg.norm(sc.rest_pos[v][:, None] - sc.rest_pos[v][None], axis=2)
+            ratio = d[d0 > 0] / d0[d0 > 0]
+            np.testing.assert_allclose(ratio, ratio.mean(), rtol=1e-10)
+            np.testing.assert_allclose(a["s"][v], a["s"][v][0], rtol=1e-12)
+            np.testing.assert_allclose(ratio.mean(), a["s"][v][0], rtol=1e-10)
+    o.shape_match()
+    b2 = o.get_state()
+    np.testing.assert_allclose(b2["x"], a["x"], atol=1e-12)
+    np.testing.assert_allclose(b2["s"], a["s"], atol=1e-12)
+
+
+def test_shape_match_minimises_the_bundle_energy():
+    """Sec. 7.3's energy sum_i |T* T_bar_i - T_i|^2 with T_i = [s_i R_i, c_i]:
+    the post-process's T* (read back from the projected state) scores no worse
+    than nearby similarities."""
+    rng = np.random.default_rng(34)
+    sc = _free_bundle_scene()
+    o = oracle.OracleScene(sc)
+    x = sc.rest_pos + rng.normal(size=sc.rest_pos.shape) * 3e-3
+    q = S.quat_mul(S.axis_angle_quat(rng.normal(size=(sc.ns, 3)) * 0.1), sc.rest_quat)
+    sv = rng.uniform(0.9, 1.1, sc.nv)
+    o.set_state(x=x, s=sv, q=q)
+    o.shape_match()
+    a = o.get_state()
+    rods = sc.bundle_rods[:7]
+    k = 3
+    v = sc.rod_offsets[rods] + k
+    g = sc.rod_offsets[rods] - rods + k
+
+    def mats(qs):
+        return np.stack([np.stack([_rot(qq, e) for e in np.eye(3)], axis=1) for qq in qs])
+
+    Ri, Rb = mats(q[g]), mats(sc.rest_quat[g])
+    Ti = [np.hstack([sv[vi] * Ri[j], x[vi][:, None]]) for j, vi in enumerate(v)]
+    Tb = [np.vstack([np.hstack([Rb[j], sc.rest_pos[vi][:, None]]), [0, 0, 0, 1]]) for j, vi in enumerate(v)]
+
+    def energy(s, R, c):
+        Ts = np.vstack([np.hstack([s * R, c[:, None]]), [0, 0, 0, 1]])
+        return sum(np.sum(((Ts @ Tb[j])[:3] - Ti[j]) ** 2) for j in range(len(v)))
+
+    # T* from the projected state: c_i = s* R* c_bar_i + c*, frames R* R_bar
+    s_star = a["s"][v][0]
+    Rs = mats(a["q"][g])[0] @ Rb[0].T
+    c_star = a["x"][v][0] - s_star * Rs @ sc.rest_pos[v][0]
+    e0 = energy(s_star, Rs, c_star)
+    for _ in range(50):
+        dq = S.axis_angle_quat(rng.normal(size=3) * 1e-3)
+        dR = np.stack([_rot(dq, e) for e in np.eye(3)], axis=1)
+        e1 = energy(s_star * (1 + rng.normal() * 1e-3), dR @ Rs, c_star + rng.normal(size=3) * 1e-4)
+        assert e1 >= e0 - 1e-12
+
+
+def test_bundle_cross_sections_are_similarities_after_each_step():
+    """Stepping pinned, animated muscles: every unpinned cross-section ends the
+    substep as a similarity of its rest arrangement (the post-process runs
+    after the iterations), while rods stay pinned to the bones."""
+    sc = S.bundled_muscles(n_muscles=4, fibers=7, n_verts=10, n_bones=4)
+    o = oracle.OracleScene(sc)
+    for f in range(2):
+        o.set_bones(*sc.bone_pose((f + 1) * sc.dt))
+        assert o.step() == 0
+    st = o.get_state()
+    n_v = 10
+    for b in range(len(sc.bundle_offsets) - 1):
+        rods = sc.bundle_rods[sc.bundle_offsets[b]:sc.bundle_offsets[b + 1]]
+        for k in range(1, n_v - 1):
+            v = sc.rod_offsets[rods] + k
+            d = np.linalg.norm(st["x"][v][:, None] - st["x"][v][None], axis=2)
+            d0 = np.linalg.norm(sc.rest_pos[v][:, None] - sc.rest_pos[v][None], axis=2)
+            ratio = d[d0 > 0] / d0[d0 > 0]
+            np.testing.assert_allclose(ratio, ratio.mean(), rtol=1e-9)
+            np.testing.assert_allclose(st["s"][v], st["s"][v][0], rtol=1e-9)
