@@ -98,6 +98,14 @@ typedef struct viper_scene_desc {
     int flags;                   /* VIPER_FLAG_*                                        */
     int max_pairs;               /* candidate-pair capacity; 0 selects 32 per segment   */
     void *stream;                /* cudaStream_t for all work; NULL: a new stream      */
+    /* Bundles (Sec. 7.3 scale-invariant shape matching): after each substep's
+     * iterations every cross-section of a bundle (vertex k of each of its
+     * rods, frame of segment k) is projected onto the similarity of its rest
+     * arrangement that fits it best; cross-sections with a pinned vertex are
+     * left to the pins.  A bundle holds 1..32 rods of one vertex count. */
+    int n_bundles;
+    const int *bundle_offsets;   /* [n_bundles+1] CSR into bundle_rods                    */
+    const int *bundle_rods;      /* rod ids                                               */
 } viper_scene_desc;
 
 /*

@@ -30,7 +30,7 @@
 
 namespace viper {
 
-enum BatchKind : int { K_ELEM = 0, K_PILL, K_EMIT, K_SCAN, K_ROD, K_CONTACT, K_END, K_MESH, K_KINDS };
+enum BatchKind : int { K_ELEM = 0, K_PILL, K_EMIT, K_SCAN, K_ROD, K_CONTACT, K_END, K_MESH, K_BUNDLE, K_KINDS };
 
 // One scene of a batched frame, as the device sees it.
 struct BatchScene {
@@ -335,6 +335,17 @@ __global__ void __launch_bounds__(kElemThreads) batch_contact_kernel(BatchArgs A
     }
 }
 
+// Bundle shape matching after the substep's last contact pass (see
+// match_cross_section), one warp per cross-section.
+__global__ void __launch_bounds__(kElemThreads) batch_bundle_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_BUNDLE, sb, local, nblk);
+    const int warps = kElemThreads / 32;
+    for (int c = local * warps + (threadIdx.x >> 5); c < sb.P.n_xs; c += nblk * warps) match_cross_section(sb.P, c);
+}
+
 // Velocity update after the last contact pass.
 __global__ void __launch_bounds__(kElemThreads) batch_finish_kernel(BatchArgs A, int apply)
 {
@@ -470,7 +481,7 @@ int stage_reserve(viper_batch::Stage &S, size_t bytes)
 
 // Launch shape of one sequence: blocks per kernel kind over all its scenes.
 struct Shape {
-    int tot[K_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int tot[K_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int threads = 0, smem = 16;
     bool cp = false, fused_grid = true;
 };
@@ -510,6 +521,7 @@ void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_bat
     cnt[K_CONTACT] = cp ? std::min(64, std::max(1, cdiv(ns + (s->n_planes > 0 ? nv : 0), kElemThreads))) : 0;
     cnt[K_END] = it.n_mesh > 0 ? std::max(1, cdiv(ns, kElemThreads)) : 1;
     cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
+    cnt[K_BUNDLE] = cp ? cdiv(s->P.n_xs, kElemThreads / 32) : 0;
 }
 
 void shape_add(Shape &sh, const viper_scene *s, bool cp)
@@ -568,6 +580,8 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
                 go(PROF_ROD, [&] { launch(batch_rod_kernel<false>, tot[K_ROD], threads, smem, st, A, 1, 0, 1, tau); });
                 contact();
             }
+            if (tot[K_BUNDLE] > 0)
+                go(PROF_ELEM, [&] { launch(batch_bundle_kernel, tot[K_BUNDLE], kElemThreads, 0, st, A); });
         }
         go(PROF_ELEM, [&] { launch(batch_finish_kernel, tot[K_ELEM], kElemThreads, 0, st, A, 1); });
     } else {

@@ -284,6 +284,17 @@ int rebuild(viper_scene *s, bool keep_state)
     if ((rc = upload(s, s->d_sperm, s->h_sperm))) return rc;
     if ((rc = upload(s, s->d_sinv, s->h_sinv))) return rc;
 
+    // bundle members in internal numbering
+    if (P.n_xs > 0) {
+        std::vector<int> xv(s->u_xs_vert.size()), xg(s->u_xs_seg.size());
+        for (size_t i = 0; i < xv.size(); ++i) {
+            xv[i] = s->h_vinv[s->u_xs_vert[i]];
+            xg[i] = s->u_xs_seg[i] >= 0 ? s->h_sinv[s->u_xs_seg[i]] : -1;
+        }
+        if ((rc = upload(s, const_cast<int *>(P.xs_vert), xv))) return rc;
+        if ((rc = upload(s, const_cast<int *>(P.xs_seg), xg))) return rc;
+    }
+
     // schedule buffers (sized for the largest schedule seen)
     size_t nslots = S.slots.size();
     static_assert(sizeof(int4) == 16, "int4");
@@ -328,7 +339,12 @@ int rebuild(viper_scene *s, bool keep_state)
 // The whole frame in one persistent launch (frame.cu).
 void substeps_frame(viper_scene *s, int substeps, int iterations) { launch_frame(s, substeps, iterations); }
 
-bool contact_path(const viper_scene *s) { return (s->flags & VIPER_FLAG_CONTACTS) || s->n_planes > 0; }
+// Contacts, half-planes or bundles: the substep is split so that work can run
+// between the sweeps (contact passes) and after the last one (shape matching).
+bool contact_path(const viper_scene *s)
+{
+    return (s->flags & VIPER_FLAG_CONTACTS) || s->n_planes > 0 || s->P.n_xs > 0;
+}
 
 // Enqueue one frame on s->stream.
 void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
@@ -355,6 +371,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
                     launch_apply(s, 0, nv);
                 }
             }
+            if (iterations > 0) launch_bundles(s);
             launch_finish(s, 0, nv, 0, ns, false);
         } else if (!cp) {
             launch_rod_full(s, iterations);
@@ -389,6 +406,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
                 }
                 launch_contacts(s);
             }
+            if (iterations > 0) launch_bundles(s);
             launch_finish(s, 0, nv, 0, ns, iterations > 0);
         }
     }
@@ -529,6 +547,17 @@ static int validate(const viper_scene_desc *d)
     if (d->n_planes < 0 || (d->n_planes > 0 && !d->planes)) return VIPER_EINVAL;
     if (!(d->contact_compliance >= 0)) return VIPER_EINVAL;
     if (d->max_pairs < 0) return VIPER_EINVAL;
+    if (d->n_bundles < 0 || (d->n_bundles > 0 && (!d->bundle_offsets || !d->bundle_rods))) return VIPER_EINVAL;
+    for (int b = 0; b < d->n_bundles; ++b) {
+        const int o0 = d->bundle_offsets[b], o1 = d->bundle_offsets[b + 1];
+        if (o0 < 0 || o1 - o0 < 1 || o1 - o0 > 32) return VIPER_EINVAL;
+        for (int i = o0; i < o1; ++i) {
+            const int r = d->bundle_rods[i], r0 = d->bundle_rods[o0];
+            if (r < 0 || r >= d->n_rods) return VIPER_EINVAL;
+            if (d->rod_offsets[r + 1] - d->rod_offsets[r] != d->rod_offsets[r0 + 1] - d->rod_offsets[r0])
+                return VIPER_EINVAL;
+        }
+    }
     return VIPER_OK;
 }
 
@@ -552,7 +581,8 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
     b += 16 * (ns + nv) + 8 * ns + 4 * nv;  // plain multipliers
     b += (16 + 8 + 88) * 3 * nv;          // schedule + slot multipliers (upper bound)
     b += 16 * (nv > ns ? nv : ns) + 4 * nv;  // staging
-    bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0;
+    bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;
+    if (d->n_bundles > 0) b += (size_t)d->bundle_offsets[d->n_bundles] * 48 * 64;  // cross-sections (bound)
     if (cp) {
         b += 36 * nv + 4 * nv * (size_t)(d->n_planes > 0 ? d->n_planes : 0);
         if (d->flags & VIPER_FLAG_CONTACTS) {
@@ -705,7 +735,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.jacobi = (d->flags & VIPER_FLAG_JACOBI) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
     P.bp_rbar_stride = 4;
-    const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0;
+    const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;
     const bool pills = (d->flags & VIPER_FLAG_CONTACTS) != 0;
 #define A(ptr, n)                                  \
     if ((rc = dalloc(s, &(ptr), (size_t)(n)))) return fail(rc)
@@ -785,6 +815,57 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
             pl[k] = make_float4((float)(nx / nn), (float)(ny / nn), (float)(nz / nn), (float)(d->planes[4 * k + 3] / nn));
         }
         if ((rc = upload(s, const_cast<float4 *>(P.planes), pl))) return fail(rc);
+    }
+
+    // ---- bundle cross-sections (Sec. 7.3): vertex k of every rod of a bundle with the
+    // frame of segment k (none for the last vertex); rest data in FP64, caller numbering
+    if (d->n_bundles > 0) {
+        std::vector<int> xs_off(1, 0);
+        std::vector<float4> rel, qbar, mub;
+        for (int b = 0; b < d->n_bundles; ++b) {
+            const int o0 = d->bundle_offsets[b], m = d->bundle_offsets[b + 1] - o0;
+            const int N = s->h_rod_n[d->bundle_rods[o0]];
+            for (int k = 0; k < N; ++k) {
+                bool pinned = false;
+                double mu[3] = {0, 0, 0};
+                for (int i = 0; i < m; ++i) {
+                    const int v = s->h_off[d->bundle_rods[o0 + i]] + k;
+                    if (pin_of_v[v] >= 0) pinned = true;
+                    for (int c = 0; c < 3; ++c) mu[c] += d->rest_pos[3 * v + c] / m;
+                }
+                if (pinned) continue;  // left to its pins
+                const bool framed = k < N - 1;
+                double den = 0;
+                for (int i = 0; i < m; ++i) {
+                    const int r = d->bundle_rods[o0 + i], v = s->h_off[r] + k, g = s->h_off[r] - r + k;
+                    double db[3];
+                    for (int c = 0; c < 3; ++c) db[c] = d->rest_pos[3 * v + c] - mu[c];
+                    den += (framed ? 3.0 : 0.0) + db[0] * db[0] + db[1] * db[1] + db[2] * db[2];
+                    s->u_xs_vert.push_back(v);
+                    s->u_xs_seg.push_back(framed ? g : -1);
+                    rel.push_back(make_float4((float)db[0], (float)db[1], (float)db[2], 0.f));
+                    qbar.push_back(framed ? make_float4((float)qn[4 * g], (float)qn[4 * g + 1], (float)qn[4 * g + 2],
+                                                        (float)qn[4 * g + 3])
+                                          : make_float4(0.f, 0.f, 0.f, 1.f));
+                }
+                mub.push_back(make_float4((float)mu[0], (float)mu[1], (float)mu[2], (float)den));
+                xs_off.push_back(xs_off.back() + m);
+            }
+        }
+        P.n_xs = (int)mub.size();
+        if (P.n_xs > 0) {
+            const size_t nm = s->u_xs_vert.size();
+            if ((rc = dalloc(s, const_cast<int **>(&P.xs_off), xs_off.size()))) return fail(rc);
+            if ((rc = dalloc(s, const_cast<int **>(&P.xs_vert), nm))) return fail(rc);
+            if ((rc = dalloc(s, const_cast<int **>(&P.xs_seg), nm))) return fail(rc);
+            if ((rc = dalloc(s, const_cast<float4 **>(&P.xs_rel), nm))) return fail(rc);
+            if ((rc = dalloc(s, const_cast<float4 **>(&P.xs_qbar), nm))) return fail(rc);
+            if ((rc = dalloc(s, const_cast<float4 **>(&P.xs_mub), mub.size()))) return fail(rc);
+            if ((rc = upload(s, const_cast<int *>(P.xs_off), xs_off))) return fail(rc);
+            if ((rc = upload(s, const_cast<float4 *>(P.xs_rel), rel))) return fail(rc);
+            if ((rc = upload(s, const_cast<float4 *>(P.xs_qbar), qbar))) return fail(rc);
+            if ((rc = upload(s, const_cast<float4 *>(P.xs_mub), mub))) return fail(rc);
+        }
     }
 
     if ((rc = rebuild(s, false))) return fail(rc);

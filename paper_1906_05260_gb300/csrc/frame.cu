@@ -291,6 +291,7 @@ static void *pick(bool barriers, bool pills)
 int frame_configure(viper_scene *s)
 {
     if (s->resident_nv != s->nv || s->n_items <= 0 || s->block_threads > 32 * kFrameWarps) return VIPER_EINVAL;
+    if (s->P.n_xs > 0) return VIPER_EINVAL;  // bundle shape matching runs between launches
     const bool pills = (s->flags & VIPER_FLAG_CONTACTS) != 0;
     const bool barriers = pills || s->n_planes > 0;
     int maxyw = 0;

@@ -1057,6 +1057,99 @@ __device__ __forceinline__ void contact_planes(const Params &P, int v, float at)
     }
 }
 
+// ================================================================ bundles
+// Rotation maximising trace(R^T A) (A row-major 3x3) by the iterative
+// rotation extraction of Mueller et al. 2016 ("A Robust Method to Extract the
+// Rotational Part of Deformations"): with r_k, a_k the columns of R(q) and A,
+// turn q by the axis-angle w = sum_k r_k x a_k / (|sum_k r_k . a_k| + eps)
+// until the step vanishes.  Starts from the identity.
+__device__ __forceinline__ float4 extract_rotation(const float *A)
+{
+    float4 q = make_float4(0.f, 0.f, 0.f, 1.f);
+#pragma unroll 1
+    for (int it = 0; it < 32; ++it) {
+        const V3 r0 = qrot(q, v3(1.f, 0.f, 0.f)), r1 = qrot(q, v3(0.f, 1.f, 0.f)), r2 = qrot(q, v3(0.f, 0.f, 1.f));
+        const V3 a0 = v3(A[0], A[3], A[6]), a1 = v3(A[1], A[4], A[7]), a2 = v3(A[2], A[5], A[8]);
+        const V3 num = cross(r0, a0) + cross(r1, a1) + cross(r2, a2);
+        const float den = fabsf(dot(r0, a0) + dot(r1, a1) + dot(r2, a2)) + 1e-20f;
+        const V3 w = (1.f / den) * num;
+        const float ang = sqrtf(dot(w, w));
+        if (!(ang > 1e-7f)) break;
+        const float sh = sinf(0.5f * ang) / ang;
+        q = qnormalize(qmul(make_float4(sh * w.x, sh * w.y, sh * w.z, cosf(0.5f * ang)), q));
+    }
+    return q;
+}
+
+// Shape matching of bundle cross-section c (Sec. 7.3) by one warp, member i
+// on lane i (at most 32): T_i = [s_i R_i, c_i] (world position, scale, frame),
+// A = sum_i [s_i R_i, c_i - mu][R_bar_i, c_bar_i - mu_bar]^T (warp sums),
+// R* = argmax trace(R^T A), s* = <R*, A> / sum_i |B_bar_i|^2, then
+// c_i = mu + s* R* (c_bar_i - mu_bar), s_i = s*, frame R* R_bar_i.  The
+// member's pending contact corrections are applied first.
+__device__ __forceinline__ void match_cross_section(const Params &P, int c)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int o0 = P.xs_off[c], m = P.xs_off[c + 1] - o0;
+    const bool mine = lane < m;
+    int v = 0, g = -1;
+    float4 x = make_float4(0.f, 0.f, 0.f, 1.f), org = x, rel = make_float4(0.f, 0.f, 0.f, 0.f), qb = org, q = org;
+    if (mine) {
+        v = P.xs_vert[o0 + lane];
+        g = P.xs_seg[o0 + lane];
+        x = apply_pending(P, v, P.X[v]);
+        org = P.rod_origin[P.rod_of_v[v]];
+        rel = P.xs_rel[o0 + lane];
+        qb = P.xs_qbar[o0 + lane];
+        if (g >= 0) q = P.Q[g];
+    }
+    const V3 cw = mine ? xyz(x) + xyz(org) : v3(0.f, 0.f, 0.f);
+    V3 mu = cw;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu.x += __shfl_xor_sync(full, mu.x, o);
+        mu.y += __shfl_xor_sync(full, mu.y, o);
+        mu.z += __shfl_xor_sync(full, mu.z, o);
+    }
+    mu = (1.f / m) * mu;
+    float A[9];
+    {
+        const V3 d = cw - mu;
+        const V3 rb = xyz(rel);
+        const float dd[3] = {d.x, d.y, d.z}, bb[3] = {rb.x, rb.y, rb.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) A[3 * a + b] = mine ? dd[a] * bb[b] : 0.f;
+        if (mine && g >= 0) {  // s R R_bar^T, column by column
+            const V3 e[3] = {v3(1.f, 0.f, 0.f), v3(0.f, 1.f, 0.f), v3(0.f, 0.f, 1.f)};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                // column b of R R_bar^T = R (R_bar^T e_b)
+                const V3 col = qrot(q, qrot(qconj(qb), e[b]));
+                A[b] += x.w * col.x;
+                A[3 + b] += x.w * col.y;
+                A[6 + b] += x.w * col.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) A[k] += __shfl_xor_sync(full, A[k], o);
+    const float4 qs = extract_rotation(A);
+    const V3 r0 = qrot(qs, v3(1.f, 0.f, 0.f)), r1 = qrot(qs, v3(0.f, 1.f, 0.f)), r2 = qrot(qs, v3(0.f, 0.f, 1.f));
+    const float num = r0.x * A[0] + r0.y * A[3] + r0.z * A[6] + r1.x * A[1] + r1.y * A[4] + r1.z * A[7] +
+                      r2.x * A[2] + r2.y * A[5] + r2.z * A[8];
+    const float ss = num / P.xs_mub[c].w;
+    if (mine) {
+        const V3 cn = mu + ss * qrot(qs, xyz(rel));
+        P.X[v] = make_float4(cn.x - org.x, cn.y - org.y, cn.z - org.z, ss);
+        if (g >= 0) P.Q[g] = qnormalize(qmul(qs, qb));
+    }
+}
+
 // ================================================================ skinning
 // LBS frame of segment g (Sec. 7.4): the 3x4 similarity T_j Tbar_j^-1 =
 // [s_m R_j Rbar_j^T | c_m - s_m R_j Rbar_j^T cbar_m] in world coordinates,

@@ -103,6 +103,14 @@ __global__ void lap_colour_kernel(Params P, const int *__restrict__ list, int n)
     *sn = c;
 }
 
+// Bundle shape matching (Sec. 7.3), one warp per cross-section.
+__global__ void bundle_kernel(Params P)
+{
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < P.n_xs; c += warps)
+        match_cross_section(P, c);
+}
+
 // ------------------------------------------------------------------ shared-memory rods
 template <bool FULL>
 __global__ void __launch_bounds__(256) rod_kernel(Params P, int n_iter, int first, int apply)
@@ -154,6 +162,14 @@ void launch_colour(viper_scene *s, int colour, const int *list, int n)
         vtx_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
     else
         lap_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
+    s->launches++;
+}
+
+void launch_bundles(viper_scene *s)
+{
+    if (s->P.n_xs <= 0) return;
+    ProfScope ps(s, PROF_ELEM);
+    bundle_kernel<<<grid_for(s->P.n_xs, 8), 256, 0, s->ls>>>(s->P);
     s->launches++;
 }
 

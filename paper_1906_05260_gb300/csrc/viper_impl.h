@@ -40,6 +40,12 @@ struct Params {
     const float4 *RV2;
     int surface;
     int jacobi;  // rod constraints by Jacobi with averaging instead of four-colour Gauss-Seidel
+    // bundle cross-sections (shape matching): members xs_off[c] .. xs_off[c+1] with
+    // vertex, frame segment (-1: none), rest offset from the rest mean, rest frame;
+    // xs_mub[c] = (rest mean, sum of the rest members' squared norms)
+    int n_xs;
+    const int *xs_off, *xs_vert, *xs_seg;
+    const float4 *xs_rel, *xs_qbar, *xs_mub;
     const float2 *RS1;
     const int *seg_v0, *vtx_seg, *seg_group;
     // Vertex positions are stored relative to a per-rod FP32 origin (the rod's
@@ -151,6 +157,7 @@ struct viper_scene {
     std::vector<float2> u_RS1;
     std::vector<int> u_group;  // per caller rod
     std::vector<float4> u_origin;  // per caller rod: FP32 rest centroid
+    std::vector<int> u_xs_vert, u_xs_seg;  // bundle cross-section members, caller numbering
     // pinned, mapped host mirror of the device error word (read without a stream sync)
     int *h_err = nullptr;
     int *d_herr = nullptr;  // its device address
@@ -198,6 +205,7 @@ void launch_broadphase(viper_scene *s);
 void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s);
 void launch_contacts(viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
+void launch_bundles(viper_scene *s);
 void launch_state_out(viper_scene *s, int which, float4 *dst);
 void launch_state_in(viper_scene *s, int which, const float4 *src);
 void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);

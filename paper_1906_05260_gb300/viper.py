@@ -44,7 +44,7 @@ class Desc(C.Structure):
         ("pin_bone", _ip), ("pin_offset", _dp), ("n_bones", C.c_int), ("bone_quat", _dp),
         ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("flags", C.c_int), ("max_pairs", C.c_int),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
     ]
 
 
@@ -226,6 +226,10 @@ def make_desc(scene, stream_handle=None, max_pairs=0):
                   | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0))
     desc.max_pairs = int(max_pairs)
     desc.stream = stream_handle
+    if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
+        desc.n_bundles = len(scene.bundle_offsets) - 1
+        desc.bundle_offsets = i(scene.bundle_offsets)
+        desc.bundle_rods = i(scene.bundle_rods)
     return desc, keep
 
 

@@ -389,3 +389,60 @@ def test_jacobi_needs_the_shared_memory_solvers(V):
     assert V.lib().viper_set_solver(g.handle, V.SOLVER_PLAIN, 4, 256) == V.EINVAL
     g.frame()  # the scene keeps its previous solver
     assert g.sync() == 0
+
+
+# --------------------------------------------------------------------------
+# bundles: scale-invariant shape matching (Sec. 7.3)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_bundled_muscles(V, solver):
+    sc = S.bundled_muscles(n_muscles=12)
+    g, o = _pair(V, sc, solver)
+    for _ in range(2):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    st = g.get_state()
+    e = assert_parity(sc, st, o.get_state(), POS_TOL_1, what="bundled muscles, 2 frames")
+    print("bundled_muscles 2 frames errors vs FP64:", e)
+    # every unpinned cross-section leaves the substep as a similarity of its rest
+    n_v = int(sc.rod_offsets[1] - sc.rod_offsets[0])
+    worst = 0.0
+    for b in range(len(sc.bundle_offsets) - 1):
+        rods = sc.bundle_rods[sc.bundle_offsets[b]:sc.bundle_offsets[b + 1]]
+        for k in range(1, n_v - 1):
+            v = sc.rod_offsets[rods] + k
+            x = st["x4"][v, :3].astype(np.float64)
+            d = np.linalg.norm(x[:, None] - x[None], axis=2)
+            d0 = np.linalg.norm(sc.rest_pos[v][:, None] - sc.rest_pos[v][None], axis=2)
+            ratio = d[d0 > 0] / d0[d0 > 0]
+            worst = max(worst, float(np.abs(ratio / ratio.mean() - 1).max()))
+    print("bundle cross-sections: worst relative deviation from a similarity", worst)
+    assert worst < 1e-4
+
+
+def test_bundles_in_a_multi_scene_step(V):
+    scenes = [S.bundled_muscles(n_muscles=8), S.muscle_rig(seed=1, n_rods=40, mesh_verts=0)]
+    a = [V.Scene(sc) for sc in scenes]
+    b = [V.Scene(sc) for sc in scenes]
+    B = V.Batch()
+    for f in range(2):
+        B.step(a, [sc.bone_pose((f + 1) * sc.dt) for sc in scenes], None, scenes[0].dt, 10, 4)
+    B.synchronize()
+    for f in range(2):
+        for o, sc in zip(b, scenes):
+            o.set_bones(*sc.bone_pose((f + 1) * sc.dt))
+            o.step(sc.dt, 10, 4)
+    for ga, gb in zip(a, b):
+        assert ga.sync() == 0 and gb.sync() == 0
+        sa, sb = ga.get_state(), gb.get_state()
+        scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
+        assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
+        assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4
+
+
+def test_bundles_refuse_the_frame_solver(V):
+    g = V.Scene(S.bundled_muscles(n_muscles=2))
+    assert V.lib().viper_set_solver(g.handle, V.SOLVER_FRAME, 4, 256) == V.EINVAL
+    g.frame()
+    assert g.sync() == 0
