@@ -36,7 +36,7 @@ class _Desc(C.Structure):
         ("bone_quat", _dp), ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("contacts", C.c_int), ("volume", C.c_int),
         ("surface_bending", C.c_int), ("jacobi", C.c_int),
-        ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
+        ("warm_start", C.c_int), ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
     ]
 
 
@@ -85,6 +85,7 @@ def lib():
         L.vo_laplacian_constraint.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                               _dp, _dp]
         L.vo_polar_rotation.argtypes = [_dp, _dp]
+        L.vo_set_activation.argtypes = [C.c_void_p, _dp]
         L.vo_shape_match.argtypes = [C.c_void_p]
         L.vo_laplacian_compliance.restype = C.c_double
         L.vo_laplacian_compliance.argtypes = [C.c_void_p, C.c_int]
@@ -152,6 +153,7 @@ class OracleScene:
         desc.volume = int(bool(scene.volume))
         desc.surface_bending = int(bool(getattr(scene, "surface_bending", False)))
         desc.jacobi = int(bool(getattr(scene, "jacobi", False)))
+        desc.warm_start = int(bool(getattr(scene, "warm_start", False)))
         if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
             desc.n_bundles = len(scene.bundle_offsets) - 1
             desc.bundle_offsets = i(scene.bundle_offsets)
@@ -253,6 +255,16 @@ class OracleScene:
         sc = np.zeros(self.ns, np.int32); vc = np.zeros(self.nv, np.int32)
         lib().vo_colouring(self._h, sc.ctypes.data_as(_ip), vc.ctypes.data_as(_ip))
         return sc, vc
+
+    def set_activation(self, a=None):
+        """Muscle activation per rod in [0, 0.9] (None: back to rest)."""
+        if a is None:
+            rc = lib().vo_set_activation(self._h, None)
+        else:
+            arr = np.ascontiguousarray(a, dtype=np.float64)
+            rc = lib().vo_set_activation(self._h, arr.ctypes.data_as(_dp))
+        if rc != 0:
+            raise ValueError("activation outside [0, 0.9]")
 
     def shape_match(self):
         """Apply the bundles' shape matching (Sec. 7.3) to the current state once."""

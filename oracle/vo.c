@@ -57,6 +57,9 @@ struct vo_scene {
     int surface, jacobi;
     int nbund;
     int *bund_off, *bund_rods;
+    /* original rest lengths / radii and densities (activation rescales them) */
+    double *lbar0, *rbar0, *rho;
+    int warm;
     /* Jacobi pass: summed corrections and the number of constraints acting */
     double *jdx, *jds, *jdth;
     int *jcx, *jcs, *jcq;
@@ -1157,6 +1160,53 @@ static void darboux_rest(vo_scene *S)
     }
 }
 
+/*
+ * Quantities derived from the rest lengths and radii: segment masses
+ * M = pi r_m^2 rho l (Sec. 4: mass uniform over the rod, midpoint rule), lumped
+ * to the end vertices, and the rest Darboux vectors.
+ * reading: each vertex takes half of each adjacent segment's position weight
+ * pi r^2 rho l and scale weight pi r^4 rho l / 2 (App. B), since the paper
+ * applies the midpoint update rule to the end points.
+ */
+static void derive_rest(vo_scene *S)
+{
+    int nv = S->nv, ns = S->ns;
+    double *mass = xcalloc((size_t)nv, sizeof(double));
+    double *jsc = xcalloc((size_t)nv, sizeof(double));
+    for (int g = 0; g < ns; ++g) {
+        int a = S->seg_v0[g], r = S->rod_of_s[g];
+        S->rm[g] = 0.5 * (S->rbar[a] + S->rbar[a + 1]);
+        S->mseg[g] = VO_PI * S->rm[g] * S->rm[g] * S->rho[r] * S->lbar[g];
+        double ms = S->mseg[g] * S->rm[g] * S->rm[g] / 2.0;
+        mass[a] += 0.5 * S->mseg[g];
+        mass[a + 1] += 0.5 * S->mseg[g];
+        jsc[a] += 0.5 * ms;
+        jsc[a + 1] += 0.5 * ms;
+    }
+    for (int i = 0; i < nv; ++i) {
+        S->minv[i] = (S->pin_of_v[i] >= 0) ? 0.0 : 1.0 / mass[i];
+        S->sinv[i] = 1.0 / jsc[i];
+    }
+    free(mass);
+    free(jsc);
+    darboux_rest(S);
+}
+
+int vo_set_activation(vo_scene *S, const double *a)
+{
+    for (int r = 0; r < S->n_rods; ++r) {
+        double ar = a ? a[r] : 0.0;
+        if (!(ar >= 0.0 && ar <= 0.9)) return -1;
+    }
+    for (int r = 0; r < S->n_rods; ++r) {
+        double ar = a ? a[r] : 0.0;
+        for (int v = S->off[r]; v < S->off[r + 1]; ++v) S->rbar[v] = S->rbar0[v] / sqrt(1.0 - ar);
+        for (int v = S->off[r]; v < S->off[r + 1] - 1; ++v) S->lbar[v - r] = (1.0 - ar) * S->lbar0[v - r];
+    }
+    derive_rest(S);
+    return 0;
+}
+
 vo_scene *vo_create(const vo_desc *d)
 {
     if (!d || d->n_rods <= 0 || !d->rod_offsets) return NULL;
@@ -1205,25 +1255,16 @@ vo_scene *vo_create(const vo_desc *d)
     }
     for (int c = 0; c < 3; ++c) S->g[c] = d->gravity[c];
 
-    /* rest lengths, segment masses M = pi r_m^2 rho l (Sec. 4: mass uniform
-     * over the rod, midpoint rule), lumped to the end vertices.
-     * reading: each vertex takes half of each adjacent segment's position
-     * weight pi r^2 rho l and scale weight pi r^4 rho l / 2 (App. B), since
-     * the paper applies the midpoint update rule to the end points. */
-    double *mass = xcalloc((size_t)nv, sizeof(double));
-    double *jsc = xcalloc((size_t)nv, sizeof(double));
+    S->lbar0 = xcalloc((size_t)ns, sizeof(double));
+    S->rbar0 = xcalloc((size_t)nv, sizeof(double));
+    S->rho = xcalloc((size_t)nr, sizeof(double));
+    memcpy(S->rbar0, S->rbar, sizeof(double) * nv);
+    memcpy(S->rho, d->density, sizeof(double) * nr);
     for (int g = 0; g < ns; ++g) {
-        int a = S->seg_v0[g], r = S->rod_of_s[g];
+        int a = S->seg_v0[g];
         double e[3] = {S->xbar[3 * (a + 1)] - S->xbar[3 * a], S->xbar[3 * (a + 1) + 1] - S->xbar[3 * a + 1],
                        S->xbar[3 * (a + 1) + 2] - S->xbar[3 * a + 2]};
-        S->lbar[g] = norm3(e);
-        S->rm[g] = 0.5 * (S->rbar[a] + S->rbar[a + 1]);
-        S->mseg[g] = VO_PI * S->rm[g] * S->rm[g] * d->density[r] * S->lbar[g];
-        double ms = S->mseg[g] * S->rm[g] * S->rm[g] / 2.0;
-        mass[a] += 0.5 * S->mseg[g];
-        mass[a + 1] += 0.5 * S->mseg[g];
-        jsc[a] += 0.5 * ms;
-        jsc[a + 1] += 0.5 * ms;
+        S->lbar0[g] = S->lbar[g] = norm3(e);
     }
     S->pin_of_v = xcalloc((size_t)nv, sizeof(int));
     for (int i = 0; i < nv; ++i) S->pin_of_v[i] = -1;
@@ -1234,13 +1275,7 @@ vo_scene *vo_create(const vo_desc *d)
         S->pin_bone[p] = d->pin_bone[p];
         for (int c = 0; c < 3; ++c) S->pin_off[3 * p + c] = d->pin_offset[3 * p + c];
     }
-    for (int i = 0; i < nv; ++i) {
-        S->minv[i] = (S->pin_of_v[i] >= 0) ? 0.0 : 1.0 / mass[i];
-        S->sinv[i] = 1.0 / jsc[i];
-    }
-    free(mass);
-    free(jsc);
-    darboux_rest(S);
+    derive_rest(S);
 
     S->nb = d->n_bones;
     S->bq0 = xcalloc(4 * (size_t)S->nb, sizeof(double));
@@ -1263,6 +1298,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->volume = d->volume;
     S->surface = d->surface_bending;
     S->jacobi = d->jacobi;
+    S->warm = d->warm_start;
     S->nbund = d->n_bundles > 0 ? d->n_bundles : 0;
     S->bund_off = xcalloc((size_t)S->nbund + 1, sizeof(int));
     if (S->nbund) {
@@ -1318,7 +1354,7 @@ void vo_destroy(vo_scene *S)
                     S->pin_of_v, S->pin_bone, S->pin_off, S->bq0, S->bt0, S->bq1, S->bt1, S->bq,
                     S->bt, S->planes, S->x, S->s, S->v, S->sd, S->q, S->w, S->xp, S->sp, S->qp,
                     S->lam_seg, S->lam_vtx, S->lam_lap, S->jdx, S->jds, S->jdth, S->jcx, S->jcs, S->jcq,
-                    S->bund_off, S->bund_rods,
+                    S->bund_off, S->bund_rods, S->lbar0, S->rbar0, S->rho,
                     S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(S);
@@ -1404,10 +1440,54 @@ static int state_finite(const vo_scene *S)
     return 1;
 }
 
+/*
+ * Warm start from the bones (Sec. 7.5 muscle simulation): each vertex of a rod
+ * whose two ends are pinned to bones b0, b1 moves, before the frame's first
+ * substep, by linear blend skinning with those two bones' transforms relative
+ * to their previous poses, T_b = [R1 R0^T, t1 - R1 R0^T t0].  Reading: the
+ * weights are (1 - t, t), t the vertex's arclength fraction along the rest rod;
+ * positions only (velocities and frames are left to the simulation).
+ */
+static void warm_start(vo_scene *S)
+{
+    for (int r = 0; r < S->n_rods; ++r) {
+        int v0 = S->off[r], v1 = S->off[r + 1] - 1;
+        int p0 = S->pin_of_v[v0], p1 = S->pin_of_v[v1];
+        if (p0 < 0 || p1 < 0) continue;
+        int b[2] = {S->pin_bone[p0], S->pin_bone[p1]};
+        if (b[0] < 0 || b[1] < 0) continue;
+        double M[2][9], t[2][3];
+        for (int k = 0; k < 2; ++k) {
+            double R0[9], R1[9], rt[3];
+            rotmat(S->bq0 + 4 * b[k], R0);
+            rotmat(S->bq1 + 4 * b[k], R1);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 3; ++c) acc += R1[3 * i + c] * R0[3 * j + c];
+                    M[k][3 * i + j] = acc;
+                }
+            matvec3(M[k], S->bt0 + 3 * b[k], rt);
+            for (int c = 0; c < 3; ++c) t[k][c] = S->bt1[3 * b[k] + c] - rt[c];
+        }
+        double len = 0.0;
+        for (int v = v0; v < v1; ++v) len += S->lbar0[v - r];
+        double acc_l = 0.0;
+        for (int v = v0; v <= v1; ++v) {
+            if (v > v0) acc_l += S->lbar0[v - 1 - r];
+            double w1 = acc_l / len, w0 = 1.0 - w1, y0[3], y1[3];
+            matvec3(M[0], S->x + 3 * v, y0);
+            matvec3(M[1], S->x + 3 * v, y1);
+            for (int c = 0; c < 3; ++c) S->x[3 * v + c] = w0 * (y0[c] + t[0][c]) + w1 * (y1[c] + t[1][c]);
+        }
+    }
+}
+
 int vo_step(vo_scene *S, double dt, int substeps, int iterations)
 {
     if (substeps <= 0 || iterations < 0 || !(dt > 0)) return -1;
     double h = dt / substeps;
+    if (S->warm) warm_start(S);
     for (int k = 0; k < substeps; ++k) {
         animate_bones(S, (double)(k + 1) / substeps);
         /* prediction step (Sec. 6, App. B) with uniform gravity: the

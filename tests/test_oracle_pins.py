@@ -916,3 +916,94 @@ def test_bundle_cross_sections_are_similarities_after_each_step():
             ratio = d[d0 > 0] / d0[d0 > 0]
             np.testing.assert_allclose(ratio, ratio.mean(), rtol=1e-9)
             np.testing.assert_allclose(st["s"][v], st["s"][v][0], rtol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Muscle activation and the bone-driven warm start (Sec. 7.5)
+# --------------------------------------------------------------------------
+
+def test_zero_activation_is_the_rest_state():
+    sc = S.muscle_rig(n_rods=6, mesh_verts=0)
+    a, b = oracle.OracleScene(sc), oracle.OracleScene(sc)
+    b.set_activation(np.zeros(sc.n_rods))
+    for f in range(2):
+        for o in (a, b):
+            o.set_bones(*sc.bone_pose((f + 1) * sc.dt))
+            assert o.step() == 0
+    np.testing.assert_array_equal(a.get_state()["x"], b.get_state()["x"])
+    with pytest.raises(ValueError):
+        b.set_activation(np.full(sc.n_rods, 0.95))
+
+
+def test_activation_keeps_mass_and_rest_volume():
+    sc = _one_rod_scene(n=10, r=0.02, lbar=0.01)
+    o = oracle.OracleScene(sc)
+    m0 = [o.vertex_inverse_inertia(i)[0] for i in range(sc.nv)]
+    lb0, _ = o.rest()
+    o.set_activation(np.array([0.4]))
+    m1 = [o.vertex_inverse_inertia(i)[0] for i in range(sc.nv)]
+    lb1, _ = o.rest()
+    np.testing.assert_allclose(m1, m0, rtol=1e-12)
+    np.testing.assert_allclose(lb1, 0.6 * lb0, rtol=1e-12)
+
+
+def test_activated_free_rod_shortens_and_bulges():
+    """A free, straight rod (no pins, no gravity) with activation a relaxes to
+    (1 - a) of its length and 1/sqrt(1 - a) of its radius: fibre shortening
+    bulges the muscle at constant volume."""
+    a = 0.3
+    sc = dataclasses.replace(_one_rod_scene(n=10, r=0.01, lbar=0.01, cs=1e-8, cb=1e-6, cv=1e-8),
+                             substeps=10, iterations=8)
+    o = oracle.OracleScene(sc)
+    o.set_activation(np.array([a]))
+    for _ in range(40):
+        assert o.step() == 0
+    st = o.get_state()
+    length = np.linalg.norm(np.diff(st["x"], axis=0), axis=1).sum()
+    L0 = 0.01 * (sc.nv - 1)
+    np.testing.assert_allclose(length, (1 - a) * L0, rtol=2e-2)
+    radius = st["s"] * sc.radius / math.sqrt(1 - a)
+    np.testing.assert_allclose(radius[1:-1], sc.radius[1:-1] / math.sqrt(1 - a), rtol=2e-2)
+
+
+def _translating_bones_scene(d0, d1, warm):
+    """One rod pinned at both ends to two bones; the bones translate by d0, d1."""
+    sc = dataclasses.replace(S.muscle_rig(n_rods=1, n_bones=2, mesh_verts=0), warm_start=warm,
+                             gravity=np.zeros(3))
+    q0, t0 = sc.bones.pose(0.0)
+    return sc, q0, t0, t0 + np.stack([d0, d1])
+
+
+def test_warm_start_blends_the_two_bone_motions_by_arclength():
+    """Bones translating by d0 and d1: before any solving (one substep, no
+    iterations, zero velocity and gravity) every vertex moves by
+    (1 - t) d0 + t d1, t its arclength fraction; without the warm start only
+    the pinned ends move."""
+    d0, d1 = np.array([0.05, 0.0, 0.01]), np.array([-0.02, 0.03, 0.0])
+    for warm in (True, False):
+        sc, q0, t0, t1 = _translating_bones_scene(d0, d1, warm)
+        o = oracle.OracleScene(sc)
+        o.set_bones(q0, t1)
+        assert o.step(dt=1 / 60, substeps=1, iterations=0) == 0
+        x = o.get_state()["x"]
+        seg = np.linalg.norm(np.diff(sc.rest_pos, axis=0), axis=1)
+        t = np.concatenate([[0.0], np.cumsum(seg)]) / seg.sum()
+        expect = sc.rest_pos + (1 - t)[:, None] * d0 + t[:, None] * d1 if warm else sc.rest_pos.copy()
+        if not warm:
+            expect[0] += d0
+            expect[-1] += d1
+        np.testing.assert_allclose(x, expect, atol=1e-12)
+
+
+def test_warm_start_lowers_the_residual_of_fast_bone_motion():
+    """Sec. 7.5: initialising from the bones speeds up convergence in fast
+    motion -- after a frame in which the bones jump, the constraint residual is
+    smaller with the warm start."""
+    res = {}
+    for warm in (False, True):
+        sc, q0, t0, t1 = _translating_bones_scene(np.array([0.08, 0.02, 0.0]), np.array([0.05, -0.04, 0.03]), warm)
+        o = oracle.OracleScene(sc)
+        o.set_bones(q0, t1)
+        assert o.step(dt=1 / 60, substeps=2, iterations=2) == 0
+        res[warm] = o.constraint_rms()["S"]
+    assert res[True] < 0.5 * res[False], res
