@@ -57,6 +57,12 @@ extern "C" {
  * four-colour Gauss-Seidel sweep.  Needs every rod in shared memory (at most
  * resident_max vertices) and a non-plain solver: VIPER_EINVAL otherwise. */
 #define VIPER_FLAG_JACOBI 8
+/* Warm start from the bones (Sec. 7.5 muscles): before a frame's first substep,
+ * every rod pinned at both ends to bones b0, b1 moves by linear blend skinning
+ * with the two bones' transforms from their previous to their target pose,
+ * T_b(p) = R1 R0^T (p - t0) + t1, weighted (1 - t, t) by the vertex's rest
+ * arclength fraction t.  Positions only; other rods are left as they are. */
+#define VIPER_FLAG_WARM_START 16
 
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
 #define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,
@@ -166,6 +172,20 @@ int viper_prepare(viper_scene *scene, float dt, int substeps, int iterations);
 
 /* Bone poses to reach at the end of the next viper_step (host or device). */
 int viper_set_bones(viper_scene *scene, int n_bones, const float *quat, const float *trans);
+
+/*
+ * Muscle activation (Sec. 7.5, fibre shortening).  activation[r] in [0, 0.9]
+ * per rod in the caller's order (host memory, n_rods floats), or NULL for the
+ * original rest state.  Rod r's rest lengths become (1 - a_r) times the
+ * original ones and its rest radii 1/sqrt(1 - a_r) times theirs (rest volume
+ * and mass kept); masses, inertias, rest Darboux vectors and compliances are
+ * recomputed in FP64 on the host from the original rest data and uploaded on
+ * the scene stream, so the change applies to every step enqueued after the
+ * call (also within a viper_batch_step).  The radius scale s in the state is
+ * kept, so a rod's radius s * rbar changes with it.  VIPER_EINVAL for a value
+ * outside [0, 0.9] (nothing changed).  The array may be reused on return.
+ */
+int viper_set_activation(viper_scene *scene, const float *activation);
 
 /*
  * Linear blend skinning (Sec. 7.4) of n mesh vertices: out = sum_k w_k T_k

@@ -30,7 +30,7 @@
 
 namespace viper {
 
-enum BatchKind : int { K_ELEM = 0, K_PILL, K_EMIT, K_SCAN, K_ROD, K_CONTACT, K_END, K_MESH, K_BUNDLE, K_KINDS };
+enum BatchKind : int { K_ELEM = 0, K_PILL, K_EMIT, K_SCAN, K_ROD, K_CONTACT, K_END, K_MESH, K_BUNDLE, K_WARM, K_KINDS };
 
 // One scene of a batched frame, as the device sees it.
 struct BatchScene {
@@ -346,6 +346,17 @@ __global__ void __launch_bounds__(kElemThreads) batch_bundle_kernel(BatchArgs A)
     for (int c = local * warps + (threadIdx.x >> 5); c < sb.P.n_xs; c += nblk * warps) match_cross_section(sb.P, c);
 }
 
+// Warm start from the bones before the frame's first substep (scenes with a warm-start table).
+__global__ void __launch_bounds__(kElemThreads) batch_warm_kernel(BatchArgs A)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_WARM, sb, local, nblk);
+    const Params &P = sb.P;
+    const int v = local * blockDim.x + threadIdx.x;
+    if (v < P.nv) P.X[v] = warm_vertex(P, v, P.X[v]);
+}
+
 // Velocity update after the last contact pass.
 __global__ void __launch_bounds__(kElemThreads) batch_finish_kernel(BatchArgs A, int apply)
 {
@@ -481,7 +492,7 @@ int stage_reserve(viper_batch::Stage &S, size_t bytes)
 
 // Launch shape of one sequence: blocks per kernel kind over all its scenes.
 struct Shape {
-    int tot[K_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int tot[K_KINDS] = {};
     int threads = 0, smem = 16;
     bool cp = false, fused_grid = true;
 };
@@ -522,6 +533,7 @@ void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_bat
     cnt[K_END] = it.n_mesh > 0 ? std::max(1, cdiv(ns, kElemThreads)) : 1;
     cnt[K_MESH] = cdiv(it.n_mesh, kElemThreads * kMeshPerThread);
     cnt[K_BUNDLE] = cp ? cdiv(s->P.n_xs, kElemThreads / 32) : 0;
+    cnt[K_WARM] = s->P.warm ? cdiv(nv, kElemThreads) : 0;
 }
 
 void shape_add(Shape &sh, const viper_scene *s, bool cp)
@@ -569,6 +581,7 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
     auto contact = [&]() {
         go(PROF_CONTACT, [&] { launch(batch_contact_kernel, tot[K_CONTACT], kElemThreads, 0, st, A); });
     };
+    if (tot[K_WARM] > 0) go(PROF_ELEM, [&] { launch(batch_warm_kernel, tot[K_WARM], kElemThreads, 0, st, A); });
     if (cp && iterations > 0) {
         // per substep: [finish + predict + sweep 0] | grid | emit | contact | {sweep | contact} x (I - 1)
         for (int k = 0; k < substeps; ++k) {

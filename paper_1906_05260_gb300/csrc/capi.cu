@@ -180,6 +180,111 @@ int n_colours(const viper_scene *s) { return s->P.surface ? 7 : 4; }
 
 // (Re)build the internal layout and upload every internal-order table.  The
 // state is carried across in caller order through the staging buffer.
+// Rest tables in caller order, from the FP64 rest data kept in the scene
+// (Sec. 4 discretisation, App. A/B integrals), rounded to FP32.  Rod r's rest
+// lengths are scaled by (1 - a_r) and its rest radii by 1/sqrt(1 - a_r)
+// (muscle activation, Sec. 7.5; act null: a = 0, the original rest state).
+static void rest_tables(viper_scene *s, const double *act)
+{
+    const int nr = s->n_rods, nv = s->nv, ns = s->ns;
+    const std::vector<double> &qn = s->h_qn;
+    std::vector<double> lbar(ns), rbar(nv), rm(ns), mseg(ns), mass(nv, 0.0), jsc(nv, 0.0);
+    for (int r = 0; r < nr; ++r) {
+        const double a = act ? act[r] : 0.0;
+        for (int v = s->h_off[r]; v < s->h_off[r + 1]; ++v) rbar[v] = s->h_rbar0[v] / sqrt(1.0 - a);
+        for (int v = s->h_off[r]; v < s->h_off[r + 1] - 1; ++v) lbar[v - r] = (1.0 - a) * s->h_lbar0[v - r];
+    }
+    // segment masses M = pi r_m^2 rho l (mass uniform over the rod, midpoint
+    // rule), lumped half to each end vertex, as the scale inertia M r_m^2 / 2
+    for (int r = 0; r < nr; ++r)
+        for (int v = s->h_off[r]; v < s->h_off[r + 1] - 1; ++v) {
+            int g = v - r;
+            rm[g] = 0.5 * (rbar[v] + rbar[v + 1]);
+            mseg[g] = kPi * rm[g] * rm[g] * s->h_rho[r] * lbar[g];
+            mass[v] += 0.5 * mseg[g];
+            mass[v + 1] += 0.5 * mseg[g];
+            double ms = mseg[g] * rm[g] * rm[g] / 2.0;
+            jsc[v] += 0.5 * ms;
+            jsc[v + 1] += 0.5 * ms;
+        }
+    s->u_RV0.assign(nv, make_float4(0, 0, 0, 0));
+    s->u_RV1.assign(nv, make_float4(0, 0, 0, 0));
+    s->u_RV2.assign(nv, make_float4(0, 0, 0, 0));
+    s->u_RS0.resize(ns);
+    s->u_RS1.resize(ns);
+    for (int r = 0; r < nr; ++r) {
+        const double cs = s->h_cs[r], cb = s->h_cb[r], cv = s->h_cv[r];
+        const int v0 = s->h_off[r], n = s->h_rod_n[r];
+        for (int j = 0; j < n - 1; ++j) {
+            int g = v0 - r + j;
+            double m = rm[g], l = lbar[g];
+            double aS = cs / (kPi * m * m * l), aV = cv / (kPi * m * m * l);
+            double aX = cs / (2.0 * kPi * m * m * l), aG = cs / (0.5 * kPi * m * m * m * m * l);
+            s->u_RS0[g] = make_float4((float)l, (float)(1.0 / (mseg[g] * m * m)), (float)aS, (float)aV);
+            s->u_RS1[g] = make_float2((float)aX, (float)aG);
+        }
+        for (int i = 0; i < n; ++i) {
+            int v = v0 + i;
+            double ob[3] = {0, 0, 0}, aB = 0, aVb = 0;
+            if (i > 0 && i < n - 1) {
+                int gb = v - r, ga = gb - 1;
+                double ca[4] = {-qn[4 * ga], -qn[4 * ga + 1], -qn[4 * ga + 2], qn[4 * ga + 3]}, p[4];
+                qmul_d(ca, &qn[4 * gb], p);
+                if (p[3] < 0)
+                    for (int c = 0; c < 4; ++c) p[c] = -p[c];
+                double kap = 4.0 / (lbar[ga] + lbar[gb]);
+                for (int c = 0; c < 3; ++c) ob[c] = kap * p[c];
+                double lv = 0.5 * (lbar[ga] + lbar[gb]);
+                double rb = rbar[v];
+                double r4l = kPi * rb * rb * rb * rb * lv;
+                aB = cb / r4l;          // compliance (4, 4, 2) * aB: H = pi r^4 k_b diag(1/4, 1/4, 1/2)
+                aVb = cv / (0.25 * r4l);
+                // surface bending: K = 1/4 pi r^4 (k_x + k_y) lv with k_x = k_y = 1/c_b (Sec. 5 E_bending);
+                // Laplacian ((s_next - s)/l_b - (s - s_prev)/l_a)/lv
+                s->u_RV2[v] = make_float4((float)(1.0 / (lbar[ga] * lv)), (float)(1.0 / (lbar[gb] * lv)),
+                                          (float)(2.0 * cb / r4l), 0.f);
+            }
+            const int pin = s->h_pin_of_v[v];
+            float wx = pin >= 0 ? -(float)(pin + 1) : (float)(1.0 / mass[v]);
+            s->u_RV0[v] = make_float4((float)ob[0], (float)ob[1], (float)ob[2], (float)rbar[v]);
+            s->u_RV1[v] = make_float4(wx, (float)(1.0 / jsc[v]), (float)aB, (float)aVb);
+        }
+    }
+}
+
+// The rest tables (and the warm-start table) in internal order, uploaded on the scene's stream.
+static int upload_rest(viper_scene *s)
+{
+    const int nv = s->nv, ns = s->ns;
+    std::vector<float4> RV0(nv), RV1(nv), RV2(nv), RS0(ns), WS;
+    std::vector<float2> RS1(ns);
+    for (int vi = 0; vi < nv; ++vi) {
+        const int vu = s->h_vperm[vi];
+        RV0[vi] = s->u_RV0[vu];
+        RV1[vi] = s->u_RV1[vu];
+        RV2[vi] = s->u_RV2[vu];
+    }
+    for (int gi = 0; gi < ns; ++gi) {
+        const int gu = s->h_sperm[gi];
+        RS0[gi] = s->u_RS0[gu];
+        RS1[gi] = s->u_RS1[gu];
+    }
+    Params &P = s->P;
+    int rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.RV0), RV0))) return rc;
+    P.bp_rbar = reinterpret_cast<const float *>(P.RV0) + 3;  // RV0[v].w = rest radius
+    if ((rc = upload(s, const_cast<float4 *>(P.RV1), RV1))) return rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.RV2), RV2))) return rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.RS0), RS0))) return rc;
+    if ((rc = upload(s, const_cast<float2 *>(P.RS1), RS1))) return rc;
+    if (P.warm) {
+        WS.resize(nv);
+        for (int vi = 0; vi < nv; ++vi) WS[vi] = s->u_warm[s->h_vperm[vi]];
+        if ((rc = upload(s, const_cast<float4 *>(P.warm), WS))) return rc;
+    }
+    return VIPER_OK;
+}
+
 int rebuild(viper_scene *s, bool keep_state)
 {
     const int nr = s->n_rods, nv = s->nv, ns = s->ns;
@@ -239,8 +344,7 @@ int rebuild(viper_scene *s, bool keep_state)
     if (configure_rod_kernels(s->smem_full) != 0) return VIPER_EINVAL;
 
     // internal-order tables
-    std::vector<float4> RV0(nv), RV1(nv), RV2(nv), RS0(ns), LQ(ns), LC(ns);
-    std::vector<float2> RS1(ns);
+    std::vector<float4> LQ(ns), LC(ns);
     std::vector<int> seg_v0(ns), vtx_seg(nv), seg_group(ns), rod_of_v(nv);
     std::vector<float4> rod_origin(nr);
     for (int k = 0; k < nr; ++k) {
@@ -250,15 +354,10 @@ int rebuild(viper_scene *s, bool keep_state)
         for (int i = 0; i < n; ++i) {
             int vi = s->h_int_off[k] + i;
             rod_of_v[vi] = k;
-            RV0[vi] = s->u_RV0[s->h_vperm[vi]];
-            RV1[vi] = s->u_RV1[s->h_vperm[vi]];
-            RV2[vi] = s->u_RV2[s->h_vperm[vi]];
             vtx_seg[vi] = vi - k;
         }
         for (int j = 0; j < n - 1; ++j) {
             int gi = s->h_int_off[k] - k + j, gu = s->h_sperm[gi];
-            RS0[gi] = s->u_RS0[gu];
-            RS1[gi] = s->u_RS1[gu];
             LQ[gi] = s->u_LQ[gu];
             LC[gi] = s->u_LC[gu];
             seg_v0[gi] = s->h_int_off[k] + j;
@@ -267,12 +366,7 @@ int rebuild(viper_scene *s, bool keep_state)
     }
     Params &P = s->P;
     int rc;
-    if ((rc = upload(s, const_cast<float4 *>(P.RV0), RV0))) return rc;
-    P.bp_rbar = reinterpret_cast<const float *>(P.RV0) + 3;  // RV0[v].w = rest radius
-    if ((rc = upload(s, const_cast<float4 *>(P.RV1), RV1))) return rc;
-    if ((rc = upload(s, const_cast<float4 *>(P.RV2), RV2))) return rc;
-    if ((rc = upload(s, const_cast<float4 *>(P.RS0), RS0))) return rc;
-    if ((rc = upload(s, const_cast<float2 *>(P.RS1), RS1))) return rc;
+    if ((rc = upload_rest(s))) return rc;
     if ((rc = upload(s, s->LQ, LQ))) return rc;
     if ((rc = upload(s, s->LC, LC))) return rc;
     if ((rc = upload(s, const_cast<int *>(P.seg_v0), seg_v0))) return rc;
@@ -358,6 +452,7 @@ void enqueue_frame(viper_scene *s, float dt, int substeps, int iterations)
     const bool cp = contact_path(s);
     const bool pills = (s->flags & VIPER_FLAG_CONTACTS) != 0;
     const int nv = s->nv, ns = s->ns;
+    if (P.warm && s->mode != VIPER_SOLVER_FRAME) launch_warm(s);  // the frame kernel warm-starts itself
     if (s->mode == VIPER_SOLVER_FRAME) substeps_frame(s, substeps, iterations);
     for (int k = 0; k < substeps && s->mode != VIPER_SOLVER_FRAME; ++k) {
         P.tau = (float)((double)(k + 1) / substeps);
@@ -634,27 +729,27 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     *s->h_err = 0;
     if (cudaHostGetDevicePointer((void **)&s->d_herr, s->h_err, 0) != cudaSuccess) return fail(VIPER_ECUDA);
 
-    // ---- rest data in FP64, caller order (Sec. 4 discretisation, App. A/B integrals)
+    // ---- rest data in FP64, caller order (Sec. 4 discretisation), kept for activation
     std::vector<int> rod_of_v(nv), pin_of_v(nv, -1);
     for (int r = 0; r < nr; ++r)
         for (int v = s->h_off[r]; v < s->h_off[r + 1]; ++v) rod_of_v[v] = r;
     for (int p = 0; p < d->n_pins; ++p) pin_of_v[d->pin_vertex[p]] = p;
-    std::vector<double> lbar(ns), rm(ns), mseg(ns), mass(nv, 0.0), jsc(nv, 0.0);
-    std::vector<double> qn(4 * (size_t)ns);
+    s->h_pin_of_v = pin_of_v;
+    s->h_lbar0.assign(ns, 0.0);
+    s->h_rbar0.assign(d->radius, d->radius + nv);
+    s->h_qn.assign(4 * (size_t)ns, 0.0);
+    s->h_rho.assign(d->density, d->density + nr);
+    s->h_cs.assign(d->c_stretch, d->c_stretch + nr);
+    s->h_cb.assign(d->c_bend, d->c_bend + nr);
+    s->h_cv.assign(d->c_volume ? d->c_volume : d->c_stretch, (d->c_volume ? d->c_volume : d->c_stretch) + nr);
+    std::vector<double> &qn = s->h_qn;
     for (int r = 0; r < nr; ++r) {
         for (int v = s->h_off[r]; v < s->h_off[r + 1] - 1; ++v) {
             int g = v - r;
             double e[3];
             for (int c = 0; c < 3; ++c) e[c] = d->rest_pos[3 * (v + 1) + c] - d->rest_pos[3 * v + c];
-            lbar[g] = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-            if (!(lbar[g] > 0)) return fail(VIPER_EINVAL);
-            rm[g] = 0.5 * (d->radius[v] + d->radius[v + 1]);
-            mseg[g] = kPi * rm[g] * rm[g] * d->density[r] * lbar[g];
-            mass[v] += 0.5 * mseg[g];
-            mass[v + 1] += 0.5 * mseg[g];
-            double ms = mseg[g] * rm[g] * rm[g] / 2.0;
-            jsc[v] += 0.5 * ms;
-            jsc[v + 1] += 0.5 * ms;
+            s->h_lbar0[g] = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            if (!(s->h_lbar0[g] > 0)) return fail(VIPER_EINVAL);
             double nq = 0;
             for (int c = 0; c < 4; ++c) nq += d->rest_quat[4 * g + c] * d->rest_quat[4 * g + c];
             nq = sqrt(nq);
@@ -662,11 +757,6 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
             for (int c = 0; c < 4; ++c) qn[4 * g + c] = d->rest_quat[4 * g + c] / nq;
         }
     }
-    s->u_RV0.assign(nv, make_float4(0, 0, 0, 0));
-    s->u_RV1.assign(nv, make_float4(0, 0, 0, 0));
-    s->u_RV2.assign(nv, make_float4(0, 0, 0, 0));
-    s->u_RS0.resize(ns);
-    s->u_RS1.resize(ns);
     s->u_LQ.resize(ns);
     s->u_LC.resize(ns);
     s->u_group.resize(nr);
@@ -678,46 +768,29 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
             for (int k = 0; k < 3; ++k) c[k] += d->rest_pos[3 * v + k];
         double inv = 1.0 / s->h_rod_n[r];
         s->u_origin[r] = make_float4((float)(c[0] * inv), (float)(c[1] * inv), (float)(c[2] * inv), 0.f);
-    }
-    for (int r = 0; r < nr; ++r) {
-        const double cs = d->c_stretch[r], cb = d->c_bend[r], cv = d->c_volume ? d->c_volume[r] : d->c_stretch[r];
-        const int v0 = s->h_off[r], n = s->h_rod_n[r];
-        for (int j = 0; j < n - 1; ++j) {
-            int g = v0 - r + j, v = v0 + j;
-            double m = rm[g], l = lbar[g];
-            double aS = cs / (kPi * m * m * l), aV = cv / (kPi * m * m * l);
-            double aX = cs / (2.0 * kPi * m * m * l), aG = cs / (0.5 * kPi * m * m * m * m * l);
-            s->u_RS0[g] = make_float4((float)l, (float)(1.0 / (mseg[g] * m * m)), (float)aS, (float)aV);
-            s->u_RS1[g] = make_float2((float)aX, (float)aG);
+        for (int v = s->h_off[r]; v < s->h_off[r + 1] - 1; ++v) {
+            int g = v - r;
             s->u_LQ[g] = make_float4((float)qn[4 * g], (float)qn[4 * g + 1], (float)qn[4 * g + 2], (float)qn[4 * g + 3]);
             s->u_LC[g] = make_float4((float)(0.5 * (d->rest_pos[3 * v] + d->rest_pos[3 * v + 3])),
                                      (float)(0.5 * (d->rest_pos[3 * v + 1] + d->rest_pos[3 * v + 4])),
                                      (float)(0.5 * (d->rest_pos[3 * v + 2] + d->rest_pos[3 * v + 5])), 0.f);
         }
-        for (int i = 0; i < n; ++i) {
-            int v = v0 + i;
-            double ob[3] = {0, 0, 0}, aB = 0, aVb = 0;
-            if (i > 0 && i < n - 1) {
-                int gb = v - r, ga = gb - 1;
-                double ca[4] = {-qn[4 * ga], -qn[4 * ga + 1], -qn[4 * ga + 2], qn[4 * ga + 3]}, p[4];
-                qmul_d(ca, &qn[4 * gb], p);
-                if (p[3] < 0)
-                    for (int c = 0; c < 4; ++c) p[c] = -p[c];
-                double kap = 4.0 / (lbar[ga] + lbar[gb]);
-                for (int c = 0; c < 3; ++c) ob[c] = kap * p[c];
-                double lv = 0.5 * (lbar[ga] + lbar[gb]);
-                double rb = d->radius[v];
-                double r4l = kPi * rb * rb * rb * rb * lv;
-                aB = cb / r4l;          // compliance (4, 4, 2) * aB: H = pi r^4 k_b diag(1/4, 1/4, 1/2)
-                aVb = cv / (0.25 * r4l);
-                // surface bending: K = 1/4 pi r^4 (k_x + k_y) lv with k_x = k_y = 1/c_b (Sec. 5 E_bending);
-                // Laplacian ((s_next - s)/l_b - (s - s_prev)/l_a)/lv
-                s->u_RV2[v] = make_float4((float)(1.0 / (lbar[ga] * lv)), (float)(1.0 / (lbar[gb] * lv)),
-                                          (float)(2.0 * cb / r4l), 0.f);
+    }
+    rest_tables(s, nullptr);
+    // warm start (Sec. 7.5): rods pinned at both ends to bones, with the rest
+    // arclength fraction of each vertex
+    if (d->flags & VIPER_FLAG_WARM_START) {
+        s->u_warm.assign(nv, make_float4(-1.f, -1.f, 0.f, 0.f));
+        for (int r = 0; r < nr; ++r) {
+            const int v0 = s->h_off[r], v1 = s->h_off[r + 1] - 1;
+            const int p0 = pin_of_v[v0], p1 = pin_of_v[v1];
+            if (p0 < 0 || p1 < 0 || d->pin_bone[p0] < 0 || d->pin_bone[p1] < 0) continue;
+            double len = 0, acc = 0;
+            for (int v = v0; v < v1; ++v) len += s->h_lbar0[v - r];
+            for (int v = v0; v <= v1; ++v) {
+                if (v > v0) acc += s->h_lbar0[v - 1 - r];
+                s->u_warm[v] = make_float4((float)d->pin_bone[p0], (float)d->pin_bone[p1], (float)(acc / len), 0.f);
             }
-            float wx = pin_of_v[v] >= 0 ? -(float)(pin_of_v[v] + 1) : (float)(1.0 / mass[v]);
-            s->u_RV0[v] = make_float4((float)ob[0], (float)ob[1], (float)ob[2], (float)d->radius[v]);
-            s->u_RV1[v] = make_float4(wx, (float)(1.0 / jsc[v]), (float)aB, (float)aVb);
         }
     }
 
@@ -745,6 +818,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(P.Q, ns); A(P.W, ns); A(P.Qp, ns);
     AC(P.RV0, float4, nv); AC(P.RV1, float4, nv); AC(P.RV2, float4, nv);
     AC(P.RS0, float4, ns); AC(P.RS1, float2, ns);
+    if (!s->u_warm.empty()) AC(P.warm, float4, nv);
     AC(P.seg_v0, int, ns); AC(P.vtx_seg, int, nv); AC(P.seg_group, int, ns);
     AC(P.rod_of_v, int, nv); AC(P.rod_origin, float4, nr);
     A(s->LQ, ns); A(s->LC, ns); A(s->frames, 3 * (size_t)ns);
@@ -1017,6 +1091,21 @@ int viper_set_bones(viper_scene *s, int n, const float *quat, const float *trans
     VCHECK(cudaMemcpyAsync(const_cast<float4 *>(s->P.bq1), quat, sizeof(float4) * n, cudaMemcpyDefault, s->stream));
     VCHECK(cudaMemcpyAsync(const_cast<float *>(s->P.bt1), trans, sizeof(float) * 3 * n, cudaMemcpyDefault, s->stream));
     return VIPER_OK;
+}
+
+int viper_set_activation(viper_scene *s, const float *activation)
+{
+    if (!s) return VIPER_EINVAL;
+    std::vector<double> a;
+    if (activation) {
+        a.resize(s->n_rods);
+        for (int r = 0; r < s->n_rods; ++r) {
+            a[r] = activation[r];
+            if (!(a[r] >= 0.0 && a[r] <= 0.9)) return VIPER_EINVAL;
+        }
+    }
+    rest_tables(s, activation ? a.data() : nullptr);
+    return upload_rest(s);
 }
 
 int viper_skin(viper_scene *s, int n, const float *rest4, const int *idx4, const float *w4, float *out4)

@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
     const float at = P.contact_alpha * P.inv_h2;
 
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
-        sX[i] = P.X[item.x + i];
+        const float4 x = P.X[item.x + i];
+        sX[i] = P.warm ? warm_vertex(P, item.x + i, x) : x;  // warm start from the bones
         sV[i] = P.V[item.x + i];
     }
     for (int j = threadIdx.x; j < item.w; j += blockDim.x) {

@@ -75,6 +75,32 @@ __device__ __forceinline__ V3 pin_target(const Params &P, int pin, float tau)
     return (qrot(q, xyz(pd)) + tr) - o;
 }
 
+// Warm start from the bones (Sec. 7.5): before a frame's first substep, vertex
+// v of a rod pinned at both ends to bones b0, b1 moves by linear blend skinning
+// with those bones' transforms relative to their previous poses,
+// T_b(p) = R1 R0^T (p - t0) + t1, with weights (1 - t, t), t the vertex's rest
+// arclength fraction.  Positions only (scale, velocities and frames unchanged).
+__device__ __forceinline__ float4 warm_vertex(const Params &P, int v, float4 x)
+{
+    const float4 wv = P.warm[v];
+    if (wv.x < 0.f) return x;
+    const float4 o = P.rod_origin[P.rod_of_v[v]];
+    const V3 p = {x.x + o.x, x.y + o.y, x.z + o.z};
+    V3 acc = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int b = __float2int_rn(k ? wv.y : wv.x);
+        const float wk = k ? wv.z : 1.f - wv.z;
+        const float *t0 = P.bt0 + 3 * b, *t1 = P.bt1 + 3 * b;
+        const V3 y = qrot(P.bq1[b], qrot(qconj(P.bq0[b]), p - v3(t0[0], t0[1], t0[2]))) + v3(t1[0], t1[1], t1[2]);
+        acc = acc + wk * y;
+    }
+    x.x = acc.x - o.x;
+    x.y = acc.y - o.y;
+    x.z = acc.z - o.z;
+    return x;
+}
+
 __device__ __forceinline__ float4 to_world(const Params &P, int v, float4 x)
 {
     float4 o = P.rod_origin[P.rod_of_v[v]];

@@ -39,6 +39,12 @@ __global__ void finish_kernel(Params P, int v0, int v1, int s0, int s1, int appl
     }
 }
 
+__global__ void warm_kernel(Params P)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x)
+        P.X[v] = warm_vertex(P, v, P.X[v]);
+}
+
 __global__ void apply_kernel(Params P, int v0, int v1)
 {
     for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x)
@@ -162,6 +168,14 @@ void launch_colour(viper_scene *s, int colour, const int *list, int n)
         vtx_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
     else
         lap_colour_kernel<<<grid_for(n, 128), 128, 0, s->ls>>>(s->P, list, n);
+    s->launches++;
+}
+
+void launch_warm(viper_scene *s)
+{
+    if (!s->P.warm) return;
+    ProfScope ps(s, PROF_ELEM);
+    warm_kernel<<<grid_for(s->nv, 256), 256, 0, s->ls>>>(s->P);
     s->launches++;
 }
 

@@ -47,6 +47,9 @@ struct Params {
     const int *xs_off, *xs_vert, *xs_seg;
     const float4 *xs_rel, *xs_qbar, *xs_mub;
     const float2 *RS1;
+    // warm start from the bones per vertex: (bone b0, bone b1, rest arclength
+    // fraction t, 0); b0 < 0: not warm-started; null: no warm start
+    const float4 *warm;
     const int *seg_v0, *vtx_seg, *seg_group;
     // Vertex positions are stored relative to a per-rod FP32 origin (the rod's
     // rest centroid) so that differences along a rod keep full precision far
@@ -157,6 +160,10 @@ struct viper_scene {
     std::vector<float2> u_RS1;
     std::vector<int> u_group;  // per caller rod
     std::vector<float4> u_origin;  // per caller rod: FP32 rest centroid
+    std::vector<float4> u_warm;    // warm-start table per caller vertex (empty: off)
+    // FP64 rest data in caller order, kept to recompute the rest tables under activation
+    std::vector<double> h_lbar0, h_rbar0, h_qn, h_rho, h_cs, h_cb, h_cv;
+    std::vector<int> h_pin_of_v;
     std::vector<int> u_xs_vert, u_xs_seg;  // bundle cross-section members, caller numbering
     // pinned, mapped host mirror of the device error word (read without a stream sync)
     int *h_err = nullptr;
@@ -206,6 +213,7 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
 void launch_contacts(viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
 void launch_bundles(viper_scene *s);
+void launch_warm(viper_scene *s);
 void launch_state_out(viper_scene *s, int which, float4 *dst);
 void launch_state_in(viper_scene *s, int which, const float4 *src);
 void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);

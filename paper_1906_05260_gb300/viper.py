@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libviper.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
-FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI = 1, 2, 4, 8
+FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI, FLAG_WARM_START = 1, 2, 4, 8, 16
 SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
 SOLVER_AUTO = -1
 PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE, PROF_PAIRS = 0, 1, 2, 3, 4, 5, 6
@@ -87,6 +87,7 @@ def lib():
         L.viper_autotune.argtypes = [vp, C.c_float, C.c_int, C.c_int, _ip]
         L.viper_step.argtypes = [vp, C.c_float, C.c_int, C.c_int]
         L.viper_set_bones.argtypes = [vp, C.c_int, vp, vp]
+        L.viper_set_activation.argtypes = [vp, vp]
         L.viper_skin.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.viper_get_state.argtypes = [vp, vp, vp, vp, vp]
         L.viper_set_state.argtypes = [vp, vp, vp, vp, vp]
@@ -223,7 +224,8 @@ def make_desc(scene, stream_handle=None, max_pairs=0):
     desc.contact_compliance = float(scene.contact_compliance)
     desc.flags = ((FLAG_CONTACTS if scene.contacts else 0) | (FLAG_VOLUME if scene.volume else 0)
                   | (FLAG_SURFACE_BENDING if getattr(scene, "surface_bending", False) else 0)
-                  | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0))
+                  | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0)
+                  | (FLAG_WARM_START if getattr(scene, "warm_start", False) else 0))
     desc.max_pairs = int(max_pairs)
     desc.stream = stream_handle
     if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
@@ -331,6 +333,17 @@ class Scene:
         """quat [nb,4], trans [nb,3]: numpy (host) or torch CUDA tensors."""
         q, t = _ptr_f32(quat), _ptr_f32(trans)
         _check(lib().viper_set_bones(self._h, int(self.scene.bones.n), q[1], t[1]), "viper_set_bones")
+
+    def set_activation(self, a=None):
+        """Muscle activation per rod in [0, 0.9] (None: the original rest state)."""
+        if a is None:
+            rc = lib().viper_set_activation(self._h, None)
+        else:
+            arr = np.ascontiguousarray(a, dtype=np.float32)
+            if arr.shape != (self.scene.n_rods,):
+                raise ValueError("one activation per rod")
+            rc = lib().viper_set_activation(self._h, arr.ctypes.data_as(C.c_void_p))
+        _check(rc, "viper_set_activation")
 
     def frame(self):
         """One frame of the scene's schedule with bones set to their pose at the frame end."""

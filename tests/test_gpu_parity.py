@@ -446,3 +446,125 @@ def test_bundles_refuse_the_frame_solver(V):
     assert V.lib().viper_set_solver(g.handle, V.SOLVER_FRAME, 4, 256) == V.EINVAL
     g.frame()
     assert g.sync() == 0
+
+
+# ---------------------------------------------------------------- muscle activation, warm start (Sec. 7.5)
+
+def _activation(sc, seed=3):
+    """Per-rod activations in [0, 0.6], multiples of 1/64 (exact in FP32)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 39, sc.n_rods) / 64.0
+
+
+def _activated(sc, a):
+    """The scene with the rest radii the activation gives (for the radius comparison)."""
+    rod_of_v = np.repeat(np.arange(sc.n_rods), np.diff(sc.rod_offsets))
+    return dataclasses.replace(sc, radius=sc.radius / np.sqrt(1.0 - a[rod_of_v]))
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
+@pytest.mark.parametrize("seeds,contacts", [((2, 3), True), ((7, 8), False)], ids=["contacts", "no-contacts"])
+def test_activation_matches_oracle(V, solver, seeds, contacts):
+    """Activated muscles against the oracle, 3 frames.  With contacts the scene
+    is one whose activated (thicker) rods do not start in deep, near-parallel
+    overlaps: there the narrowphase's probe comparisons are decided by rounding
+    (an FP64 oracle with only those comparisons rounded to FP32 moves by
+    3.6e-4 L in a frame on scene 7 with activation 8), so that case runs
+    without contacts."""
+    sc = dataclasses.replace(S.muscle_rig(seed=seeds[0], n_rods=40, mesh_verts=0), contacts=contacts)
+    a = _activation(sc, seeds[1])
+    g, o = _pair(V, sc, solver)
+    g.set_activation(a)
+    o.set_activation(a)
+    # rest radii on the device: rbar0 / sqrt(1 - a), rounded once to FP32
+    _, rb = g.predicted()
+    ref = _activated(sc, a).radius
+    assert np.abs(rb - ref).max() <= 1e-6 * ref.max()
+    for _ in range(3):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(_activated(sc, a), g.get_state(), o.get_state(), POS_TOL_1,
+                      what=f"activated muscle_rig {seeds}, contacts {contacts}, 3 frames")
+    print(f"activated muscle_rig {seeds} contacts {contacts}, 3 frames errors vs FP64:", e)
+
+
+def test_activation_reset_restores_the_rest_tables_bitwise(V):
+    sc = S.muscle_rig(seed=2, n_rods=40, mesh_verts=0)
+    a, b = V.Scene(sc), V.Scene(sc)
+    a.set_activation(_activation(sc))
+    a.set_activation(None)
+    for _ in range(2):
+        a.frame(); b.frame()
+    sa, sb = a.get_state(), b.get_state()
+    for key in ("x4", "v4", "q4", "w4"):
+        np.testing.assert_array_equal(sa[key], sb[key], err_msg=key)
+    with pytest.raises(RuntimeError):
+        a.set_activation(np.full(sc.n_rods, 0.95, np.float32))
+
+
+def _jump_scene(warm):
+    """One rod between two bones that jump (translate) within a frame, no gravity."""
+    sc = dataclasses.replace(S.muscle_rig(seed=1, n_rods=1, n_bones=2, mesh_verts=0), warm_start=warm,
+                             gravity=np.zeros(3))
+    q0, t0 = sc.bones.pose(0.0)
+    return sc, q0, t0 + np.array([[0.05, 0.0, 0.01], [-0.02, 0.03, 0.0]])
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
+def test_warm_start_blend_before_the_first_substep(V, solver):
+    """Translating bones, one substep without iterations: every vertex moves by
+    (1 - t) d0 + t d1 exactly as in the oracle."""
+    sc, q0, t1 = _jump_scene(True)
+    g, o = _pair(V, sc, solver)
+    for x in (g, o):
+        x.set_bones(q0, t1)
+        x.step(1 / 60, 1, 0)
+    assert g.sync() == 0
+    xg = g.get_state()["x4"][:, :3].astype(np.float64)
+    xo = o.get_state()["x"]
+    assert np.abs(xg - xo).max() < 1e-6, np.abs(xg - xo).max()
+    assert np.abs(xo - sc.rest_pos).max() > 1e-2  # the blend moved the interior
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
+def test_warm_start_muscle_rig_matches_oracle(V, solver):
+    sc = dataclasses.replace(S.muscle_rig(seed=2, n_rods=40, mesh_verts=0), warm_start=True)
+    a = _activation(sc, 3)
+    g, o = _pair(V, sc, solver)
+    g.set_activation(a)
+    o.set_activation(a)
+    for f in range(3):
+        g.frame(); o.frame()
+        assert g.sync() == 0
+        e = assert_parity(_activated(sc, a), g.get_state(), o.get_state(), POS_TOL_1,
+                          what=f"warm-started, activated muscle_rig, {f + 1} frames")
+    print("warm-started activated muscle_rig 3 frames errors vs FP64:", e)
+
+
+def test_warm_start_and_activation_in_a_multi_scene_step(V):
+    warm = dataclasses.replace(S.muscle_rig(seed=2, n_rods=40, mesh_verts=0), warm_start=True)
+    scenes = [warm, S.muscle_rig(seed=1, n_rods=40, mesh_verts=0)]
+    act = _activation(warm, 3)
+    a = [V.Scene(sc) for sc in scenes]
+    b = [V.Scene(sc) for sc in scenes]
+    a[0].set_activation(act)
+    b[0].set_activation(act)
+    B = V.Batch()
+    counts = []
+    for f in range(2):
+        c0 = B.launch_count()
+        B.step(a, [sc.bone_pose((f + 1) * sc.dt) for sc in scenes], None, warm.dt, 10, 4)
+        counts.append(B.launch_count() - c0)
+    B.synchronize()
+    # per substep 2 I + 2, velocity update and frame end, one warm-start launch (no mesh: no skinning)
+    assert counts == [10 * (2 * 4 + 2) + 2 + 1] * 2, counts
+    for f in range(2):
+        for o, sc in zip(b, scenes):
+            o.set_bones(*sc.bone_pose((f + 1) * sc.dt))
+            o.step(sc.dt, 10, 4)
+    for ga, gb in zip(a, b):
+        assert ga.sync() == 0 and gb.sync() == 0
+        sa, sb = ga.get_state(), gb.get_state()
+        scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
+        assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
+        assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4
