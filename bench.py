@@ -17,6 +17,7 @@ independent seeded scene (weak scaling; no data-path collective).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -386,6 +387,98 @@ def bench_multi_scene(V, torch, flush, dist, frames, n_scenes=64, rank=0):
     return out
 
 
+def bench_muscles(V, torch, flush, dist, frames, rank=0):
+    """Muscle features on the headline rig and on bundled muscles (Sec. 7.3, 7.5):
+    per-frame time with a time-varying activation (rest tables recomputed on the
+    host and uploaded every frame, inside the timed region) and the bone-driven
+    warm start, against the same rig without them; bundled fibre muscles with
+    shape matching after every substep."""
+    from paper_1906_05260_gb300 import scenes as S
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def time_scene(sc, per_frame=None):
+        g = V.Scene(sc)
+        mesh = V.Mesh(sc.mesh) if sc.mesh is not None else None
+        st = g.stream
+
+        def one(f):
+            if per_frame is not None:
+                per_frame(g, f)
+            g.frame()
+            if mesh is not None:
+                g.skin(mesh)
+
+        for f in range(3):
+            one(f)
+        torch.cuda.synchronize()
+        ts, tw = [], []
+        l0 = g.launch_count()
+        for i in range(frames):
+            with torch.cuda.stream(st):
+                flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(st):
+                e0.record(st)
+                one(3 + i)
+                e1.record(st)
+            e1.synchronize()
+            tw.append((time.perf_counter() - t0) * 1e3)
+            ts.append(e0.elapsed_time(e1))
+        rc = g.sync()
+        if rc != 0:
+            raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
+        ms = reduce_max(dist, sum(ts) / len(ts))
+        wall = reduce_max(dist, sum(tw) / len(tw))
+        units = reduce_sum(dist, sc.nv * sc.substeps)
+        out = {"value": units / (ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": ms,
+               "wall_ms_per_frame": wall, "launches_per_frame": (g.launch_count() - l0) / frames}
+        g.close()
+        return out
+
+    base = S.muscle_rig(seed=1 + rank)
+    warm = dataclasses.replace(base, warm_start=True)
+    phase = np.random.default_rng(7).uniform(0, 2 * math.pi, base.n_rods)
+
+    # the activation of every frame: inputs, generated before timing
+    acts = [(0.3 * (0.5 + 0.5 * np.sin(2 * math.pi * f / 60.0 + phase))).astype(np.float32)
+            for f in range(frames + 3)]
+
+    def activate(g, f):
+        g.set_activation(acts[f])
+
+    res = {"workload": f"muscle_rig {base.n_rods} rods / {base.nv} vertices, {base.mesh.n} mesh vertices, "
+                       "10 substeps x 4 iterations + LBS",
+           "plain_rig": time_scene(base),
+           "activation_and_warm_start": time_scene(warm, activate)}
+    # the activation update alone: upload + device recompute of the rest tables
+    g = V.Scene(warm)
+    st = g.stream
+    for f in range(3):
+        activate(g, f)
+    torch.cuda.synchronize()
+    ta = []
+    for i in range(frames):
+        with torch.cuda.stream(st):
+            e0.record(st)
+            activate(g, i)
+            e1.record(st)
+        e1.synchronize()
+        ta.append(e0.elapsed_time(e1))
+    g.close()
+    res["set_activation_us"] = 1e3 * reduce_max(dist, sum(ta) / len(ta))
+    res["activation_and_warm_start"]["note"] = ("per-rod activation 0.3 (1 + sin) / 2 set every frame: the rods "
+                                                "thicken and shorten, so contacts and pairs change too; "
+                                                "(n_rods floats uploaded, rest tables recomputed on the device), warm start from the bones")
+    bm = S.bundled_muscles(n_muscles=96)
+    res["bundled_muscles"] = time_scene(bm)
+    res["bundled_muscles"]["workload"] = (f"{bm.n_rods // 7} muscles x 7 fibre rods x 16 vertices "
+                                          f"({bm.nv} vertices), shape matching of every cross-section per substep, "
+                                          "contacts between muscles, 10 substeps x 4 iterations")
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +489,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-muscles", action="store_true")
     ap.add_argument("--serving", type=float, default=10.0,
                     help="seconds of the real-time serving load (0 disables)")
     args = ap.parse_args()
@@ -614,6 +708,11 @@ def main():
         batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
         convergence = bench_convergence(V, np)
 
+    # ---- muscle features: activation + warm start, bundled muscles
+    muscles = None
+    if not args.no_muscles:
+        muscles = bench_muscles(V, torch, flush, dist, max(10, K // 2), rank=rank)
+
     # ---- many scenes at once: the multi-scene step against per-scene graphs
     multi = None
     if not args.no_multi:
@@ -664,6 +763,7 @@ def main():
         "batching": batching,
         "convergence": convergence,
         "multi_scene": multi,
+        "muscles": muscles,
         "serving": serving,
     }
     if rank == 0:

@@ -181,19 +181,16 @@ int n_colours(const viper_scene *s) { return s->P.surface ? 7 : 4; }
 // (Re)build the internal layout and upload every internal-order table.  The
 // state is carried across in caller order through the staging buffer.
 // Rest tables in caller order, from the FP64 rest data kept in the scene
-// (Sec. 4 discretisation, App. A/B integrals), rounded to FP32.  Rod r's rest
-// lengths are scaled by (1 - a_r) and its rest radii by 1/sqrt(1 - a_r)
-// (muscle activation, Sec. 7.5; act null: a = 0, the original rest state).
-static void rest_tables(viper_scene *s, const double *act)
+// (Sec. 4 discretisation, App. A/B integrals), rounded to FP32; also the unit
+// rest Darboux direction of every interior vertex (h_pdir), which muscle
+// activation rescales on the device.
+static void rest_tables(viper_scene *s)
 {
     const int nr = s->n_rods, nv = s->nv, ns = s->ns;
     const std::vector<double> &qn = s->h_qn;
-    std::vector<double> lbar(ns), rbar(nv), rm(ns), mseg(ns), mass(nv, 0.0), jsc(nv, 0.0);
-    for (int r = 0; r < nr; ++r) {
-        const double a = act ? act[r] : 0.0;
-        for (int v = s->h_off[r]; v < s->h_off[r + 1]; ++v) rbar[v] = s->h_rbar0[v] / sqrt(1.0 - a);
-        for (int v = s->h_off[r]; v < s->h_off[r + 1] - 1; ++v) lbar[v - r] = (1.0 - a) * s->h_lbar0[v - r];
-    }
+    const std::vector<double> &lbar = s->h_lbar0, &rbar = s->h_rbar0;
+    std::vector<double> rm(ns), mseg(ns), mass(nv, 0.0), jsc(nv, 0.0);
+    s->h_pdir.assign(3 * (size_t)nv, 0.0);
     // segment masses M = pi r_m^2 rho l (mass uniform over the rod, midpoint
     // rule), lumped half to each end vertex, as the scale inertia M r_m^2 / 2
     for (int r = 0; r < nr; ++r)
@@ -233,7 +230,10 @@ static void rest_tables(viper_scene *s, const double *act)
                 if (p[3] < 0)
                     for (int c = 0; c < 4; ++c) p[c] = -p[c];
                 double kap = 4.0 / (lbar[ga] + lbar[gb]);
-                for (int c = 0; c < 3; ++c) ob[c] = kap * p[c];
+                for (int c = 0; c < 3; ++c) {
+                    ob[c] = kap * p[c];
+                    s->h_pdir[3 * (size_t)v + c] = p[c];
+                }
                 double lv = 0.5 * (lbar[ga] + lbar[gb]);
                 double rb = rbar[v];
                 double r4l = kPi * rb * rb * rb * rb * lv;
@@ -282,6 +282,47 @@ static int upload_rest(viper_scene *s)
         for (int vi = 0; vi < nv; ++vi) WS[vi] = s->u_warm[s->h_vperm[vi]];
         if ((rc = upload(s, const_cast<float4 *>(P.warm), WS))) return rc;
     }
+    return VIPER_OK;
+}
+
+// FP64 rest data that the activation kernel rescales, in internal order:
+// per vertex (rest radius, rest Darboux direction), per segment the rest
+// length, per rod (density, c_s, c_b, c_v); internal rod offsets and the
+// internal -> caller rod map.  Allocated on the first activation.
+static int upload_act_base(viper_scene *s)
+{
+    const int nr = s->n_rods, nv = s->nv, ns = s->ns;
+    int rc;
+    if (!s->d_act) {
+        if ((rc = dalloc(s, &s->d_act_v, 4 * (size_t)nv))) return rc;
+        if ((rc = dalloc(s, &s->d_act_s, (size_t)ns))) return rc;
+        if ((rc = dalloc(s, &s->d_act_r, 4 * (size_t)nr))) return rc;
+        if ((rc = dalloc(s, &s->d_int_off, (size_t)nr + 1))) return rc;
+        if ((rc = dalloc(s, &s->d_rod_perm, (size_t)nr))) return rc;
+        if ((rc = dalloc(s, &s->d_act, (size_t)nr))) return rc;
+        if (cudaHostAlloc((void **)&s->h_act, sizeof(float) * nr, cudaHostAllocDefault) != cudaSuccess)
+            return VIPER_ENOMEM;
+        if (cudaEventCreateWithFlags(&s->ev_act, cudaEventDisableTiming) != cudaSuccess) return VIPER_ECUDA;
+    }
+    std::vector<double> bv(4 * (size_t)nv), bs(ns), br(4 * (size_t)nr);
+    for (int vi = 0; vi < nv; ++vi) {
+        const int vu = s->h_vperm[vi];
+        bv[4 * (size_t)vi] = s->h_rbar0[vu];
+        for (int c = 0; c < 3; ++c) bv[4 * (size_t)vi + 1 + c] = s->h_pdir[3 * (size_t)vu + c];
+    }
+    for (int gi = 0; gi < ns; ++gi) bs[gi] = s->h_lbar0[s->h_sperm[gi]];
+    for (int k = 0; k < nr; ++k) {
+        const int r = s->h_rod_perm[k];
+        br[4 * (size_t)k] = s->h_rho[r];
+        br[4 * (size_t)k + 1] = s->h_cs[r];
+        br[4 * (size_t)k + 2] = s->h_cb[r];
+        br[4 * (size_t)k + 3] = s->h_cv[r];
+    }
+    if ((rc = upload(s, s->d_act_v, bv))) return rc;
+    if ((rc = upload(s, s->d_act_s, bs))) return rc;
+    if ((rc = upload(s, s->d_act_r, br))) return rc;
+    if ((rc = upload(s, s->d_int_off, s->h_int_off))) return rc;
+    if ((rc = upload(s, s->d_rod_perm, s->h_rod_perm))) return rc;
     return VIPER_OK;
 }
 
@@ -421,6 +462,10 @@ int rebuild(viper_scene *s, bool keep_state)
                                    s->stream));
             launch_state_in(s, w, s->stage4);
         }
+    }
+    if (s->act_on) {  // the activation in d_act, on the re-uploaded tables in the new order
+        if ((rc = upload_act_base(s))) return rc;
+        launch_activation(s);
     }
     VCHECK(cudaStreamSynchronize(s->stream));
     if (s->gexec) {
@@ -776,7 +821,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
                                      (float)(0.5 * (d->rest_pos[3 * v + 2] + d->rest_pos[3 * v + 5])), 0.f);
         }
     }
-    rest_tables(s, nullptr);
+    rest_tables(s);
     // warm start (Sec. 7.5): rods pinned at both ends to bones, with the rest
     // arclength fraction of each vertex
     if (d->flags & VIPER_FLAG_WARM_START) {
@@ -974,6 +1019,8 @@ void viper_scene_destroy(viper_scene *s)
         cudaStreamSynchronize(s->side);
         cudaStreamDestroy(s->side);
     }
+    if (s->ev_act) cudaEventDestroy(s->ev_act);
+    if (s->h_act) cudaFreeHost(s->h_act);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -1096,16 +1143,23 @@ int viper_set_bones(viper_scene *s, int n, const float *quat, const float *trans
 int viper_set_activation(viper_scene *s, const float *activation)
 {
     if (!s) return VIPER_EINVAL;
-    std::vector<double> a;
-    if (activation) {
-        a.resize(s->n_rods);
-        for (int r = 0; r < s->n_rods; ++r) {
-            a[r] = activation[r];
-            if (!(a[r] >= 0.0 && a[r] <= 0.9)) return VIPER_EINVAL;
-        }
+    int rc = VIPER_OK;
+    if (!activation) {  // the original tables, as computed at creation
+        if (s->act_on) rc = upload_rest(s);
+        s->act_on = false;
+        return rc;
     }
-    rest_tables(s, activation ? a.data() : nullptr);
-    return upload_rest(s);
+    for (int r = 0; r < s->n_rods; ++r)
+        if (!(activation[r] >= 0.f && activation[r] <= 0.9f)) return VIPER_EINVAL;
+    if (!s->d_act && (rc = upload_act_base(s))) return rc;
+    // pinned staging: wait until the previous activation has been copied out of it
+    VCHECK(cudaEventSynchronize(s->ev_act));
+    memcpy(s->h_act, activation, sizeof(float) * s->n_rods);
+    VCHECK(cudaMemcpyAsync(s->d_act, s->h_act, sizeof(float) * s->n_rods, cudaMemcpyHostToDevice, s->stream));
+    VCHECK(cudaEventRecord(s->ev_act, s->stream));
+    launch_activation(s);
+    s->act_on = true;
+    return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;
 }
 
 int viper_skin(viper_scene *s, int n, const float *rest4, const int *idx4, const float *w4, float *out4)

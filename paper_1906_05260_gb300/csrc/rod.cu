@@ -45,6 +45,64 @@ __global__ void warm_kernel(Params P)
         P.X[v] = warm_vertex(P, v, P.X[v]);
 }
 
+// Muscle activation (Sec. 7.5, fibre shortening): the rest tables of internal
+// vertex v (and of the segment that starts at v) from the FP64 rest data with
+// rod k's rest lengths scaled by (1 - a_k) and rest radii by 1/sqrt(1 - a_k).
+// The formulas are those of the scene's creation (Sec. 4 discretisation,
+// App. A/B): segment mass M = pi r_m^2 rho l lumped half to each end, scale
+// inertia M r_m^2 / 2, rest Darboux vector 4 / (l_a + l_b) times the unit
+// direction, stretch / bend / volume compliances from the rescaled geometry.
+// Pinned vertices keep their pin code.  Computed in FP64, rounded once to FP32.
+__global__ void activation_kernel(Params P, const double *__restrict__ bv, const double *__restrict__ bs,
+                                  const double *__restrict__ br, const int *__restrict__ int_off,
+                                  const int *__restrict__ rod_perm, const float *__restrict__ act)
+{
+    const double kPi = 3.14159265358979323846;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= P.nv) return;
+    const int k = P.rod_of_v[v], v0 = int_off[k], n = int_off[k + 1] - v0, i = v - v0;
+    const double a = (double)act[rod_perm[k]];
+    const double rs = 1.0 / sqrt(1.0 - a), ls = 1.0 - a;
+    const double rho = br[4 * k], cs = br[4 * k + 1], cb = br[4 * k + 2], cv = br[4 * k + 3];
+    const int g0 = v0 - k;  // first segment of rod k
+    double mass = 0.0, jsc = 0.0;
+    double l_seg[2] = {0.0, 0.0};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int j = i - 1 + side;  // segment j joins vertices j, j + 1 of the rod
+        if (j < 0 || j >= n - 1) continue;
+        const double rm = 0.5 * (bv[4 * (size_t)(v0 + j)] * rs + bv[4 * (size_t)(v0 + j + 1)] * rs);
+        const double l = ls * bs[g0 + j];
+        const double m = kPi * rm * rm * rho * l;
+        mass += 0.5 * m;
+        jsc += 0.5 * (m * rm * rm / 2.0);
+        l_seg[side] = l;
+        if (side == 1) {
+            const double aS = cs / (kPi * rm * rm * l), aV = cv / (kPi * rm * rm * l);
+            const double aX = cs / (2.0 * kPi * rm * rm * l), aG = cs / (0.5 * kPi * rm * rm * rm * rm * l);
+            const_cast<float4 *>(P.RS0)[g0 + j] = make_float4((float)l, (float)(1.0 / (m * rm * rm)), (float)aS, (float)aV);
+            const_cast<float2 *>(P.RS1)[g0 + j] = make_float2((float)aX, (float)aG);
+        }
+    }
+    const double rb = bv[4 * (size_t)v] * rs;
+    double ob[3] = {0.0, 0.0, 0.0}, aB = 0.0, aVb = 0.0;
+    float4 rv2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i > 0 && i < n - 1) {
+        const double la = l_seg[0], lb = l_seg[1];
+        const double kap = 4.0 / (la + lb), lv = 0.5 * (la + lb);
+        for (int c = 0; c < 3; ++c) ob[c] = kap * bv[4 * (size_t)v + 1 + c];
+        const double r4l = kPi * rb * rb * rb * rb * lv;
+        aB = cb / r4l;
+        aVb = cv / (0.25 * r4l);
+        rv2 = make_float4((float)(1.0 / (la * lv)), (float)(1.0 / (lb * lv)), (float)(2.0 * cb / r4l), 0.f);
+    }
+    const float wx_old = P.RV1[v].x;
+    const float wx = wx_old < 0.f ? wx_old : (float)(1.0 / mass);
+    const_cast<float4 *>(P.RV0)[v] = make_float4((float)ob[0], (float)ob[1], (float)ob[2], (float)rb);
+    const_cast<float4 *>(P.RV1)[v] = make_float4(wx, (float)(1.0 / jsc), (float)aB, (float)aVb);
+    const_cast<float4 *>(P.RV2)[v] = rv2;
+}
+
 __global__ void apply_kernel(Params P, int v0, int v1)
 {
     for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x)
@@ -176,6 +234,13 @@ void launch_warm(viper_scene *s)
     if (!s->P.warm) return;
     ProfScope ps(s, PROF_ELEM);
     warm_kernel<<<grid_for(s->nv, 256), 256, 0, s->ls>>>(s->P);
+    s->launches++;
+}
+
+void launch_activation(viper_scene *s)
+{
+    activation_kernel<<<grid_for(s->nv, 256), 256, 0, s->stream>>>(s->P, s->d_act_v, s->d_act_s, s->d_act_r,
+                                                                  s->d_int_off, s->d_rod_perm, s->d_act);
     s->launches++;
 }
 

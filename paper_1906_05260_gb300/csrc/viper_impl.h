@@ -164,6 +164,16 @@ struct viper_scene {
     // FP64 rest data in caller order, kept to recompute the rest tables under activation
     std::vector<double> h_lbar0, h_rbar0, h_qn, h_rho, h_cs, h_cb, h_cv;
     std::vector<int> h_pin_of_v;
+    std::vector<double> h_pdir;  // unit rest Darboux direction per caller vertex (3; zero at rod ends)
+    // muscle activation: the rest tables recomputed on the device (launch_activation)
+    double *d_act_v = nullptr;   // per internal vertex: rest radius, rest Darboux direction
+    double *d_act_s = nullptr;   // per internal segment: rest length
+    double *d_act_r = nullptr;   // per internal rod: density, c_s, c_b, c_v
+    int *d_int_off = nullptr, *d_rod_perm = nullptr;
+    float *d_act = nullptr;      // activation per caller rod
+    float *h_act = nullptr;      // pinned staging of the activation
+    cudaEvent_t ev_act = nullptr;
+    bool act_on = false;
     std::vector<int> u_xs_vert, u_xs_seg;  // bundle cross-section members, caller numbering
     // pinned, mapped host mirror of the device error word (read without a stream sync)
     int *h_err = nullptr;
@@ -214,6 +224,7 @@ void launch_contacts(viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
 void launch_bundles(viper_scene *s);
 void launch_warm(viper_scene *s);
+void launch_activation(viper_scene *s);
 void launch_state_out(viper_scene *s, int which, float4 *dst);
 void launch_state_in(viper_scene *s, int which, const float4 *src);
 void launch_predicted_out(viper_scene *s, float4 *dst, float *rbar);
