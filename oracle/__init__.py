@@ -36,7 +36,7 @@ class _Desc(C.Structure):
         ("bone_quat", _dp), ("bone_trans", _dp), ("n_planes", C.c_int), ("planes", _dp),
         ("contact_compliance", C.c_double), ("contacts", C.c_int), ("volume", C.c_int),
         ("surface_bending", C.c_int), ("jacobi", C.c_int),
-        ("warm_start", C.c_int), ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
+        ("volume_vector", C.c_int), ("warm_start", C.c_int), ("n_bundles", C.c_int), ("bundle_offsets", _ip), ("bundle_rods", _ip),
     ]
 
 
@@ -153,6 +153,7 @@ class OracleScene:
         desc.volume = int(bool(scene.volume))
         desc.surface_bending = int(bool(getattr(scene, "surface_bending", False)))
         desc.jacobi = int(bool(getattr(scene, "jacobi", False)))
+        desc.volume_vector = int(bool(getattr(scene, "volume_vector", False)))
         desc.warm_start = int(bool(getattr(scene, "warm_start", False)))
         if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
             desc.n_bundles = len(scene.bundle_offsets) - 1
@@ -323,7 +324,8 @@ def narrowphase(a1, ra1, a2, ra2, b1, rb1, b2, rb2):
 
 
 def segment_constraint(kind, xa, xb, sa, sb, q, lbar):
-    rows = 3 if kind == 0 else 1
+    """kind 0 S, 1 V, 2 X, 3 G, 4 V in the printed vector form."""
+    rows = 3 if kind in (0, 4) else 1
     Cv = np.zeros(rows); Jxa = np.zeros((rows, 3)); Jxb = np.zeros((rows, 3))
     Jsa = np.zeros(rows); Jsb = np.zeros(rows); Jth = np.zeros((rows, 3))
     args = [_d(a)[1] for a in (Cv, Jxa, Jxb, Jsa, Jsb, Jth)]

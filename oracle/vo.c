@@ -51,10 +51,11 @@ struct vo_scene {
     double *x, *s, *v, *sd, *q, *w;
     /* per-substep scratch */
     double *xp, *sp, *qp;
-    double *lam_seg;   /* 6 per segment: S(3), V, X, G */
+    double *lam_seg;   /* 8 per segment: S(3), V (1, or 3 in the vector form), X, G */
     double *lam_vtx;   /* 5 per vertex: B(3), Vb(2)    */
     double *lam_lap;   /* 1 per vertex: surface bending */
     int surface, jacobi;
+    int vvec;  /* volume constraint in the printed vector form */
     int nbund;
     int *bund_off, *bund_rods;
     /* original rest lengths / radii and densities (activation rescales them) */
@@ -195,6 +196,9 @@ static void solve_k(int k, double *A, double *b, double *x)
  *     gives the scalar s^2 d3.grad c; reading: C = s_m^2 d3.(xb-xa)/lbar - 1.
  *  X  cross-section scale, Eq. stretch_xy:   C = s_m - 1
  *  G  scale gradient, Eq. surface_stretch:   C = (sb - sa)/lbar
+ *  Vv volume, the vector form printed in Sec. 5 / App. A (first term of the
+ *     integrated E_vol):  C = s_m^2 (xb - xa)/lbar - d3, since at rest
+ *     s_bar = 1 and R Rbar^T grad_z c_bar = d3; its d3 component is V.
  */
 int vo_segment_constraint(int kind, const double *xa, const double *xb, double sa, double sb,
                           const double *q, double lbar, double *C, double *Jxa, double *Jxb,
@@ -204,7 +208,7 @@ int vo_segment_constraint(int kind, const double *xa, const double *xb, double s
     d3_of(q, d3);
     for (int i = 0; i < 3; ++i) dx[i] = xb[i] - xa[i];
     double sm = 0.5 * (sa + sb);
-    int rows = (kind == 0) ? 3 : 1;
+    int rows = (kind == 0 || kind == 4) ? 3 : 1;
     memset(Jxa, 0, sizeof(double) * 3 * rows);
     memset(Jxb, 0, sizeof(double) * 3 * rows);
     memset(Jth, 0, sizeof(double) * 3 * rows);
@@ -230,6 +234,17 @@ int vo_segment_constraint(int kind, const double *xa, const double *xb, double s
         Jsb[0] = sm * e / lbar;
         cross3(d3, dx, cr);  /* d(d3.dx)/dtheta = (d3 x dx)^T */
         for (int c = 0; c < 3; ++c) Jth[c] = sm * sm * cr[c] / lbar;
+    } else if (kind == 4) {
+        double S[9];
+        skew(d3, S);
+        for (int r = 0; r < 3; ++r) {
+            C[r] = sm * sm * dx[r] / lbar - d3[r];
+            Jxa[r * 3 + r] = -sm * sm / lbar;
+            Jxb[r * 3 + r] = sm * sm / lbar;
+            Jsa[r] = sm * dx[r] / lbar;
+            Jsb[r] = sm * dx[r] / lbar;
+            for (int c = 0; c < 3; ++c) Jth[r * 3 + c] = S[r * 3 + c];
+        }
     } else if (kind == 2) {
         C[0] = sm - 1.0;
         Jsa[0] = 0.5;
@@ -478,18 +493,19 @@ static void project_segment(vo_scene *S, int g, int kind, double h)
     int k = vo_segment_constraint(kind, S->x + 3 * a, S->x + 3 * (a + 1), S->s[a], S->s[a + 1],
                                   S->q + 4 * g, S->lbar[g], C, Jxa, Jxb, Jsa, Jsb, Jth);
     seg_alpha(S, g, al);
-    for (int r = 0; r < k; ++r) alpha[r] = al[kind];
+    for (int r = 0; r < k; ++r) alpha[r] = al[kind == 4 ? 1 : kind];
     blk_t b[5];
     b[0].type = BLK_POS;   b[0].idx = a;     memcpy(b[0].J, Jxa, sizeof(double) * 3 * k);
     b[1].type = BLK_POS;   b[1].idx = a + 1; memcpy(b[1].J, Jxb, sizeof(double) * 3 * k);
     b[2].type = BLK_SCALE; b[2].idx = a;     memcpy(b[2].J, Jsa, sizeof(double) * k);
     b[3].type = BLK_SCALE; b[3].idx = a + 1; memcpy(b[3].J, Jsb, sizeof(double) * k);
     b[4].type = BLK_ROT;   b[4].idx = g;     memcpy(b[4].J, Jth, sizeof(double) * 3 * k);
-    static const int lam_off[4] = {0, 3, 4, 5};
-    xpbd_solve(S, k, C, b, 5, alpha, S->lam_seg + 6 * g + lam_off[kind], h);
+    static const int lam_off[5] = {0, 3, 6, 7, 3};
+    xpbd_solve(S, k, C, b, 5, alpha, S->lam_seg + 8 * g + lam_off[kind], h);
     if (S->jacobi) {
         /* blocks acting per kind: positions, scales, frame */
-        static const int acts[4][5] = {{1, 1, 0, 0, 1}, {1, 1, 1, 1, 1}, {0, 0, 1, 1, 0}, {0, 0, 1, 1, 0}};
+        static const int acts[5][5] = {{1, 1, 0, 0, 1}, {1, 1, 1, 1, 1}, {0, 0, 1, 1, 0}, {0, 0, 1, 1, 0},
+                                       {1, 1, 1, 1, 1}};
         accumulate_blocks(S, b, 5, acts[kind]);
     } else {
         apply_blocks(S, b, 5);
@@ -592,7 +608,7 @@ static void jacobi_pass(vo_scene *S, double h)
     memset(S->jcq, 0, sizeof(int) * (size_t)S->ns);
     for (int g = 0; g < S->ns; ++g) {
         project_segment(S, g, 0, h);
-        if (S->volume) project_segment(S, g, 1, h);
+        if (S->volume) project_segment(S, g, S->vvec ? 4 : 1, h);
         project_segment(S, g, 2, h);
         project_segment(S, g, 3, h);
     }
@@ -631,7 +647,7 @@ static void colour_sweep(vo_scene *S, int colour, double h)
             for (int j = colour; j < n - 1; j += 2) {
                 int g = v0 - r + j;
                 project_segment(S, g, 0, h);
-                if (S->volume) project_segment(S, g, 1, h);
+                if (S->volume) project_segment(S, g, S->vvec ? 4 : 1, h);
                 project_segment(S, g, 2, h);
                 project_segment(S, g, 3, h);
             }
@@ -1298,6 +1314,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->volume = d->volume;
     S->surface = d->surface_bending;
     S->jacobi = d->jacobi;
+    S->vvec = d->volume_vector;
     S->warm = d->warm_start;
     S->nbund = d->n_bundles > 0 ? d->n_bundles : 0;
     S->bund_off = xcalloc((size_t)S->nbund + 1, sizeof(int));
@@ -1331,7 +1348,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->xp = xcalloc(3 * (size_t)nv, sizeof(double));
     S->sp = xcalloc((size_t)nv, sizeof(double));
     S->qp = xcalloc(4 * (size_t)ns, sizeof(double));
-    S->lam_seg = xcalloc(6 * (size_t)ns, sizeof(double));
+    S->lam_seg = xcalloc(8 * (size_t)ns, sizeof(double));
     S->lam_vtx = xcalloc(5 * (size_t)nv, sizeof(double));
     S->lam_lap = xcalloc((size_t)nv, sizeof(double));
     S->jdx = xcalloc(3 * (size_t)nv, sizeof(double));
@@ -1510,7 +1527,7 @@ int vo_step(vo_scene *S, double dt, int substeps, int iterations)
             apply_dtheta(S->q + 4 * g, dth);
         }
         /* multipliers start at zero each substep (App. C: lambda^0 = 0) */
-        memset(S->lam_seg, 0, sizeof(double) * 6 * (size_t)S->ns);
+        memset(S->lam_seg, 0, sizeof(double) * 8 * (size_t)S->ns);
         memset(S->lam_vtx, 0, sizeof(double) * 5 * (size_t)S->nv);
         memset(S->lam_lap, 0, sizeof(double) * (size_t)S->nv);
         memset(S->lam_plane, 0, sizeof(double) * (size_t)S->nv * (size_t)(S->np ? S->np : 1));
@@ -1648,7 +1665,7 @@ int vo_constraint_rms(const vo_scene *S, double *out6)
         int a = S->seg_v0[g];
         for (int kind = 0; kind < 4; ++kind) {
             double C[3], J1[9], J2[9], J3[3], J4[3], J5[9];
-            int k = vo_segment_constraint(kind, S->x + 3 * a, S->x + 3 * (a + 1), S->s[a], S->s[a + 1],
+            int k = vo_segment_constraint(kind == 1 && S->vvec ? 4 : kind, S->x + 3 * a, S->x + 3 * (a + 1), S->s[a], S->s[a + 1],
                                           S->q + 4 * g, S->lbar[g], C, J1, J2, J3, J4, J5);
             for (int r = 0; r < k; ++r) acc[kind] += C[r] * C[r];
             cntf[kind] += k;

@@ -48,6 +48,8 @@ typedef struct vo_desc {
     int surface_bending;         /* scale-Laplacian constraints on/off            */
     int jacobi;                  /* rod constraints: 0 four-colour Gauss-Seidel,  */
                                  /* 1 Jacobi with averaging (Sec. 7 engine)       */
+    int volume_vector;           /* volume constraint in the printed vector form  */
+                                 /* (Sec. 5) instead of the determinant's scalar  */
     int warm_start;              /* bone-driven LBS initialisation per frame      */
                                  /* (Sec. 7.5 muscle simulation)                  */
     int n_bundles;               /* rod bundles for shape matching (Sec. 7.3)     */

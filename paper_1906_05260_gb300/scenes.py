@@ -103,6 +103,7 @@ class Scene:
     mesh: Optional[Mesh] = None
     surface_bending: bool = False     # scale-Laplacian constraints (Sec. 5, E_bending)
     jacobi: bool = False              # rod constraints by Jacobi with averaging (Sec. 7 engine)
+    volume_vector: bool = False       # volume constraint in the printed vector form (Sec. 5)
     warm_start: bool = False          # bone-driven LBS initialisation per frame (Sec. 7.5)
     bundle_offsets: Optional[np.ndarray] = None  # int32 [n_bundles+1] CSR into bundle_rods (Sec. 7.3)
     bundle_rods: Optional[np.ndarray] = None     # int32 rods of each bundle (equal vertex counts)

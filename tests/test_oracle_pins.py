@@ -37,7 +37,7 @@ def _perturb_rot(q, dth):
 # Jacobians vs central finite differences (Sec. 5, App. A constraints)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
 def test_segment_jacobians_match_finite_differences(kind):
     rng = np.random.default_rng(10 + kind)
     for _ in range(20):
@@ -64,7 +64,7 @@ def test_segment_jacobians_match_finite_differences(kind):
         np.testing.assert_allclose(r["Jsa"], fd, rtol=1e-6, atol=1e-7)
         fd = (C_of(sb_=sb + eps) - C_of(sb_=sb - eps)) / (2 * eps)
         np.testing.assert_allclose(r["Jsb"], fd, rtol=1e-6, atol=1e-7)
-        assert rows == (3 if kind == 0 else 1)
+        assert rows == (3 if kind in (0, 4) else 1)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
@@ -139,6 +139,34 @@ def test_volume_value_is_deformation_determinant():
         # the oracle's V uses the midpoint scale; at the midpoint s(z) = s_m
         r = oracle.segment_constraint(1, c0, c1, s0, s1, q, lbar)
         np.testing.assert_allclose(r["C"][0] + 1.0, det, rtol=1e-7)
+
+
+def test_vector_volume_form():
+    """The printed vector volume term (Sec. 5, App. A): its component along d3
+    is the determinant's scalar form; it vanishes on a volume-preserving
+    stretch along the frame (s = 1/sqrt(lambda)) where stretch alone does not;
+    unlike the scalar form it also measures shear across the frame."""
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        q = _rand_quat(rng)
+        d3 = _rot(q, [0, 0, 1])
+        lbar = rng.uniform(0.2, 1.0)
+        c0 = rng.normal(size=3)
+        c1 = c0 + lbar * rng.uniform(0.5, 1.5) * (d3 + 0.3 * rng.normal(size=3))
+        s0, s1 = rng.uniform(0.6, 1.4, 2)
+        cv = oracle.segment_constraint(4, c0, c1, s0, s1, q, lbar)["C"]
+        cs = oracle.segment_constraint(1, c0, c1, s0, s1, q, lbar)["C"][0]
+        np.testing.assert_allclose(cv @ d3, cs, rtol=1e-12, atol=1e-12)
+        lam = rng.uniform(0.5, 2.0)
+        s = 1.0 / math.sqrt(lam)
+        cv = oracle.segment_constraint(4, c0, c0 + lam * lbar * d3, s, s, q, lbar)["C"]
+        np.testing.assert_allclose(cv, 0.0, atol=1e-12)
+        e1 = _rot(q, [1, 0, 0])
+        gam = rng.uniform(0.05, 0.5)
+        cv = oracle.segment_constraint(4, c0, c0 + lbar * (d3 + gam * e1), 1.0, 1.0, q, lbar)["C"]
+        cs = oracle.segment_constraint(1, c0, c0 + lbar * (d3 + gam * e1), 1.0, 1.0, q, lbar)["C"][0]
+        np.testing.assert_allclose(cv, gam * e1, atol=1e-12)
+        assert abs(cs) < 1e-12
 
 
 def test_darboux_of_uniform_twist_and_bend():
@@ -433,7 +461,8 @@ def test_quaternions_stay_unit():
     np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-12)
 
 
-def test_volume_held_and_rod_thins_when_stretched():
+@pytest.mark.parametrize("vector_form", [False, True], ids=["scalar", "vector"])
+def test_volume_held_and_rod_thins_when_stretched(vector_form):
     """A rod pinned at both ends at 1.3x its rest length (E1, E8).  With a stiff
     volume term and enough iterations the solver reaches the closed form
     s = 1/sqrt(1.3) (segment volume = rest volume); softer volume compliance
@@ -442,7 +471,8 @@ def test_volume_held_and_rod_thins_when_stretched():
     def run(cv, iters=100, volume=True):
         n = 10
         sc = _one_rod_scene(n=n, r=0.01, lbar=0.01, cs=1e-5, cb=1e-5, cv=cv)
-        sc = dataclasses.replace(sc, volume=volume, pin_vertex=np.array([0, n - 1], np.int32),
+        sc = dataclasses.replace(sc, volume=volume, volume_vector=vector_form,
+                                 pin_vertex=np.array([0, n - 1], np.int32),
                                  pin_bone=np.array([-1, -1], np.int32),
                                  pin_offset=np.array([[0, 0, 0], [1.3 * 0.01 * (n - 1), 0, 0]]))
         o = oracle.OracleScene(sc)
