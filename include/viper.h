@@ -63,6 +63,12 @@ extern "C" {
  * T_b(p) = R1 R0^T (p - t0) + t1, weighted (1 - t, t) by the vertex's rest
  * arclength fraction t.  Positions only; other rods are left as they are. */
 #define VIPER_FLAG_WARM_START 16
+/* With VIPER_FLAG_VOLUME: the volume constraint in the vector form printed in
+ * Sec. 5 / App. A, C = s_m^2 (xb - xa)/lbar - d3 (three multipliers), instead of
+ * the scalar s_m^2 d3.(xb - xa)/lbar - 1 that the determinant gives.  Runs on the
+ * plain solver only (a scene created with it starts there; viper_set_solver to
+ * another solver returns VIPER_EINVAL; viper_batch_step steps it with viper_step). */
+#define VIPER_FLAG_VOLUME_VECTOR 32
 
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */
 #define VIPER_SOLVER_BATCHED 1 /* rods staged in shared memory for a whole substep,

@@ -791,7 +791,7 @@ int viper_batch_step(viper_batch *B, const viper_batch_item *items, int n, float
         viper_scene *s = items[i].scene;
         st[i] = scene_poll_latched(s);
         if (st[i] == VIPER_ENONFINITE) continue;
-        if (s->resident_nv == s->nv && s->n_items > 0)
+        if (s->resident_nv == s->nv && s->n_items > 0 && !s->P.vvec)
             groups[{scene_contact_path(s) ? 1 : 0, s->block_threads}].push_back(i);
         else
             single.push_back(i);

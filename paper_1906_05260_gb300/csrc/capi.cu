@@ -371,6 +371,7 @@ int rebuild(viper_scene *s, bool keep_state)
     s->smem_iter = std::max(S.smem_iter, 16);
     s->resident_nv = s->h_int_off[S.n_resident_rods];
     s->resident_ns = s->resident_nv - S.n_resident_rods;
+    if (s->P.vvec && s->mode != VIPER_SOLVER_PLAIN) return VIPER_EINVAL;
     if (s->P.jacobi) {
         // Jacobi runs only in the shared-memory sweep, with 3 float4 of records per
         // vertex and per segment behind the 2 (y + w) float4 of state
@@ -851,6 +852,8 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.volume = (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
     P.surface = (d->flags & VIPER_FLAG_SURFACE_BENDING) ? 1 : 0;
     P.jacobi = (d->flags & VIPER_FLAG_JACOBI) ? 1 : 0;
+    P.vvec = (d->flags & VIPER_FLAG_VOLUME_VECTOR) && (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
+    if (P.vvec) s->mode = VIPER_SOLVER_PLAIN;  // the vector volume form runs on the plain path only
     P.contact_alpha = (float)d->contact_compliance;
     P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;
@@ -869,6 +872,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(s->LQ, ns); A(s->LC, ns); A(s->frames, 3 * (size_t)ns);
     A(s->d_vperm, nv); A(s->d_sperm, ns); A(s->d_sinv, ns);
     A(P.lamS, ns); A(P.lamS2, ns); A(P.lamB, nv); A(P.lamB2, nv); A(P.lamL, nv);
+    if (P.vvec) A(P.lamV2, ns);
     A(s->stage4, std::max(nv, ns)); A(s->stage1, nv);
     for (int c = 0; c < 7; ++c) A(s->col_list[c], std::max(nv, ns));
     A(P.err, 1);

@@ -187,6 +187,7 @@ __device__ __forceinline__ void predict_segment_at(const Params &P, int g, bool 
     if (plain_lam) {
         P.lamS[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         P.lamS2[g] = make_float2(0.f, 0.f);
+        if (P.vvec) P.lamV2[g] = make_float2(0.f, 0.f);
     }
 }
 

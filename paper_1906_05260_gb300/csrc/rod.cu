@@ -120,13 +120,15 @@ __global__ void seg_colour_kernel(Params P, const int *__restrict__ list, int n)
     float4 ra = P.RV1[a], rb = P.RV1[a + 1];
     float4 lam = P.lamS[g];
     float2 lam2 = P.lamS2[g];
+    float2 lv = P.vvec ? P.lamV2[g] : make_float2(0.f, 0.f);
     project_segment(xa, xb, q, inv_mass(ra), inv_mass(rb), ra.y, rb.y, P.RS0[g], P.RS1[g], lam, lam2, P.inv_h2,
-                    P.volume != 0);
+                    P.volume != 0, P.vvec ? &lv : nullptr);
     P.X[a] = xa;
     P.X[a + 1] = xb;
     P.Q[g] = q;
     P.lamS[g] = lam;
     P.lamS2[g] = lam2;
+    if (P.vvec) P.lamV2[g] = lv;
 }
 
 __global__ void vtx_colour_kernel(Params P, const int *__restrict__ list, int n)

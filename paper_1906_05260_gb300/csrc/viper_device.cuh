@@ -92,6 +92,7 @@ __device__ __forceinline__ float inv_mass(float4 rv1) { return fmaxf(rv1.x, 0.f)
 //  V  C = s_m^2 d3.(xb - xa)/l - 1        (determinant of grad p, App. A)
 //  X  C = s_m - 1                         (Eq. stretch_xy)
 //  G  C = (sb - sa)/l                     (Eq. surface_stretch)
+//  Vv C = s_m^2 (xb - xa)/l - d3          (V in the printed vector form; plain path)
 
 // Increments of one segment constraint: positions and scales of both ends and
 // the frame's world rotation increment (applied as rotate_by).
@@ -148,6 +149,43 @@ __device__ __forceinline__ void seg_volume(const float4 &xa, const float4 &xb, c
     d.dth = (a * dl) * jt;
 }
 
+// V in the vector form printed in Sec. 5 / App. A: C = s_m^2 (xb - xa)/l - d3
+// (its d3 component is the scalar V).  J_xb = -J_xa = (s_m^2/l) I,
+// J_sa = J_sb = u = s_m (xb - xa)/l, J_theta = [d3]x, so the effective matrix is
+// D + (w_sa + w_sb) u u^T with D = (w_p + at) I + a (I - d3 d3^T),
+// w_p = (w_a + w_b) s_m^4/l^2: solved by the Sherman-Morrison formula on D's
+// closed-form inverse.  Multipliers (lw, lv.x, lv.y); compliance alpha_V.
+__device__ __forceinline__ void seg_volume_vec(const float4 &xa, const float4 &xb, const float4 &q, float wa,
+                                               float wb, float wsa, float wsb, float4 rs0, float inv_l, float &lw,
+                                               float2 &lv, float inv_h2, SegDelta &d)
+{
+    V3 d3 = qd3(q);
+    V3 dx = xyz(xb) - xyz(xa);
+    float sm = 0.5f * (xa.w + xb.w);
+    float jx = sm * sm * inv_l;
+    V3 C = jx * dx - d3;
+    V3 u = (sm * inv_l) * dx;
+    float a = 4.f * rs0.y / (sm * sm);
+    float at = rs0.w * inv_h2;
+    float ws = wsa + wsb;
+    float wp = (wa + wb) * jx * jx;
+    V3 rhs = -C - at * v3(lw, lv.x, lv.y);
+    const float i_perp = 1.f / (wp + at + a), i_par = 1.f / (wp + at);
+    float rn = dot(rhs, d3), un = dot(u, d3);
+    V3 Dr = (rhs - rn * d3) * i_perp + d3 * (rn * i_par);
+    V3 Du = (u - un * d3) * i_perp + d3 * (un * i_par);
+    V3 dl = Dr - Du * (ws * dot(u, Dr) / (1.f + ws * dot(u, Du)));
+    lw += dl.x;
+    lv.x += dl.y;
+    lv.y += dl.z;
+    float ud = dot(u, dl);
+    d.dxa = (-wa * jx) * dl;
+    d.dxb = (wb * jx) * dl;
+    d.dsa = wsa * ud;
+    d.dsb = wsb * ud;
+    d.dth = a * cross(dl, d3);
+}
+
 // X on the end scales (sa, sb).
 __device__ __forceinline__ void seg_xsection(float sa, float sb, float wsa, float wsb, float2 rs1, float2 &lam2,
                                              float inv_h2, float &dsa, float &dsb)
@@ -173,9 +211,11 @@ __device__ __forceinline__ void seg_gradient(float sa, float sb, float wsa, floa
 }
 
 // Gauss-Seidel: S, V, X, G, each evaluated at the state the previous one left.
+// lamv: the two further multipliers of V in the vector form (null: the scalar form).
 __device__ __forceinline__ void project_segment(float4 &xa, float4 &xb, float4 &q, float wa, float wb,
                                                 float wsa, float wsb, float4 rs0, float2 rs1,
-                                                float4 &lam, float2 &lam2, float inv_h2, bool volume)
+                                                float4 &lam, float2 &lam2, float inv_h2, bool volume,
+                                                float2 *lamv = nullptr)
 {
     const float inv_l = 1.f / rs0.x;
     SegDelta d;
@@ -184,7 +224,10 @@ __device__ __forceinline__ void project_segment(float4 &xa, float4 &xb, float4 &
     add_to(xb, d.dxb);
     rotate_by(q, d.dth);
     if (volume) {
-        seg_volume(xa, xb, q, wa, wb, wsa, wsb, rs0, inv_l, lam, inv_h2, d);
+        if (lamv)
+            seg_volume_vec(xa, xb, q, wa, wb, wsa, wsb, rs0, inv_l, lam.w, *lamv, inv_h2, d);
+        else
+            seg_volume(xa, xb, q, wa, wb, wsa, wsb, rs0, inv_l, lam, inv_h2, d);
         add_to(xa, d.dxa);
         add_to(xb, d.dxb);
         xa.w += d.dsa;

@@ -40,6 +40,7 @@ struct Params {
     const float4 *RV2;
     int surface;
     int jacobi;  // rod constraints by Jacobi with averaging instead of four-colour Gauss-Seidel
+    int vvec;    // volume constraint in the printed vector form (plain path; multipliers in lamV2)
     // bundle cross-sections (shape matching): members xs_off[c] .. xs_off[c+1] with
     // vertex, frame segment (-1: none), rest offset from the rest mean, rest frame;
     // xs_mub[c] = (rest mean, sum of the rest members' squared norms)
@@ -63,6 +64,7 @@ struct Params {
     float2 *lamS2;
     float *lamB2;
     float *lamL;  // surface bending
+    float2 *lamV2;  // the two further multipliers of the vector volume form
     // shared-memory path
     const int4 *items;
     const int2 *slots;

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libviper.so")
 OK = 0
 EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
 FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI, FLAG_WARM_START = 1, 2, 4, 8, 16
+FLAG_VOLUME_VECTOR = 32
 SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
 SOLVER_AUTO = -1
 PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE, PROF_PAIRS = 0, 1, 2, 3, 4, 5, 6
@@ -225,7 +226,8 @@ def make_desc(scene, stream_handle=None, max_pairs=0):
     desc.flags = ((FLAG_CONTACTS if scene.contacts else 0) | (FLAG_VOLUME if scene.volume else 0)
                   | (FLAG_SURFACE_BENDING if getattr(scene, "surface_bending", False) else 0)
                   | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0)
-                  | (FLAG_WARM_START if getattr(scene, "warm_start", False) else 0))
+                  | (FLAG_WARM_START if getattr(scene, "warm_start", False) else 0)
+                  | (FLAG_VOLUME_VECTOR if getattr(scene, "volume_vector", False) else 0))
     desc.max_pairs = int(max_pairs)
     desc.stream = stream_handle
     if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
@@ -277,8 +279,11 @@ class Scene:
         self.t = 0.0
         _live.add(self)
         # auto: the graph-replayed shared-memory path (measured fastest on contact scenes;
-        # the persistent frame kernel is an explicit option)
-        self.set_solver(SOLVER_BATCHED if solver == SOLVER_AUTO else solver, block_warps, resident_max)
+        # the persistent frame kernel is an explicit option); the vector volume form
+        # runs on the plain path only
+        if solver == SOLVER_AUTO:
+            solver = SOLVER_PLAIN if (scene.volume and getattr(scene, "volume_vector", False)) else SOLVER_BATCHED
+        self.set_solver(solver, block_warps, resident_max)
         if scene.init_pos is not None or scene.init_quat is not None:
             x4 = self.get_state()["x4"]
             q4 = None

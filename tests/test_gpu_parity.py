@@ -568,3 +568,55 @@ def test_warm_start_and_activation_in_a_multi_scene_step(V):
         scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
         assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
         assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4
+
+
+# ---------------------------------------------------------------- the printed vector volume form
+
+@pytest.mark.parametrize("frames,tol", [(1, "one"), (100, "hundred")])
+def test_vector_volume_plain_small(V, frames, tol):
+    sc = dataclasses.replace(S.plain_small(), volume_vector=True)
+    g, o = _pair(V, sc, V.SOLVER_AUTO)
+    assert g.solver == V.SOLVER_PLAIN
+    for _ in range(frames):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    if frames == 1:
+        e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="vector volume, plain_small 1 frame")
+    else:
+        e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_100, rad_tol=1e-4, ang_tol=1e-3,
+                          what="vector volume, plain_small 100 frames")
+    print(f"vector volume plain_small {frames} frames errors vs FP64:", e)
+
+
+def test_vector_volume_muscle_rig(V):
+    sc = dataclasses.replace(S.muscle_rig(seed=2, n_rods=40, mesh_verts=0), volume_vector=True)
+    g, o = _pair(V, sc, V.SOLVER_AUTO)
+    for _ in range(2):
+        g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="vector volume, muscle_rig 2 frames")
+    print("vector volume muscle_rig 2 frames errors vs FP64:", e)
+    # the two forms give different trajectories (shear is resisted by the vector form)
+    o2 = oracle.OracleScene(dataclasses.replace(sc, volume_vector=False))
+    for _ in range(2):
+        o2.frame()
+    assert np.abs(o2.get_state()["x"] - o.get_state()["x"]).max() > 1e-6
+
+
+def test_vector_volume_stays_on_the_plain_solver(V):
+    sc = dataclasses.replace(S.muscle_rig(seed=2, n_rods=20, mesh_verts=0), volume_vector=True)
+    g = V.Scene(sc)
+    for mode in (V.SOLVER_BATCHED, V.SOLVER_FRAME):
+        assert V.lib().viper_set_solver(g.handle, mode, 4, 256) == V.EINVAL
+    assert g.solver == V.SOLVER_PLAIN
+    # in a multi-scene step it is stepped by viper_step on its own stream
+    a, b = V.Scene(sc), V.Scene(sc)
+    B = V.Batch()
+    for f in range(2):
+        B.step([a], [sc.bone_pose((f + 1) * sc.dt)], None, sc.dt, 10, 4)
+        b.set_bones(*sc.bone_pose((f + 1) * sc.dt))
+        b.step(sc.dt, 10, 4)
+    B.synchronize()
+    assert a.sync() == 0 and b.sync() == 0
+    for key in ("x4", "v4", "q4", "w4"):
+        np.testing.assert_array_equal(a.get_state()[key], b.get_state()[key], err_msg=key)
