@@ -387,6 +387,52 @@ def bench_multi_scene(V, torch, flush, dist, frames, n_scenes=64, rank=0):
     return out
 
 
+def time_scene(V, torch, flush, dist, sc, frames, per_frame=None, solver=None):
+    """Frame time of one scene (bones set per frame, LBS when it has a mesh):
+    device time between CUDA events on its stream, L2 flushed between frames,
+    and the host wall clock of the same frames."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    g = V.Scene(sc) if solver is None else V.Scene(sc, solver=solver)
+    mesh = V.Mesh(sc.mesh) if sc.mesh is not None else None
+    st = g.stream
+
+    def one(f):
+        if per_frame is not None:
+            per_frame(g, f)
+        g.frame()
+        if mesh is not None:
+            g.skin(mesh)
+
+    for f in range(3):
+        one(f)
+    torch.cuda.synchronize()
+    ts, tw = [], []
+    l0 = g.launch_count()
+    for i in range(frames):
+        with torch.cuda.stream(st):
+            flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(st):
+            e0.record(st)
+            one(3 + i)
+            e1.record(st)
+        e1.synchronize()
+        tw.append((time.perf_counter() - t0) * 1e3)
+        ts.append(e0.elapsed_time(e1))
+    rc = g.sync()
+    if rc != 0:
+        raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
+    ms = reduce_max(dist, sum(ts) / len(ts))
+    wall = reduce_max(dist, sum(tw) / len(tw))
+    units = reduce_sum(dist, sc.nv * sc.substeps)
+    out = {"value": units / (ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": ms,
+           "wall_ms_per_frame": wall, "launches_per_frame": (g.launch_count() - l0) / frames}
+    g.close()
+    return out
+
+
 def bench_muscles(V, torch, flush, dist, frames, rank=0):
     """Muscle features on the headline rig and on bundled muscles (Sec. 7.3, 7.5):
     per-frame time with a time-varying activation (rest tables recomputed on the
@@ -397,45 +443,8 @@ def bench_muscles(V, torch, flush, dist, frames, rank=0):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
-    def time_scene(sc, per_frame=None):
-        g = V.Scene(sc)
-        mesh = V.Mesh(sc.mesh) if sc.mesh is not None else None
-        st = g.stream
-
-        def one(f):
-            if per_frame is not None:
-                per_frame(g, f)
-            g.frame()
-            if mesh is not None:
-                g.skin(mesh)
-
-        for f in range(3):
-            one(f)
-        torch.cuda.synchronize()
-        ts, tw = [], []
-        l0 = g.launch_count()
-        for i in range(frames):
-            with torch.cuda.stream(st):
-                flush.fill_(i & 0xFF)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            with torch.cuda.stream(st):
-                e0.record(st)
-                one(3 + i)
-                e1.record(st)
-            e1.synchronize()
-            tw.append((time.perf_counter() - t0) * 1e3)
-            ts.append(e0.elapsed_time(e1))
-        rc = g.sync()
-        if rc != 0:
-            raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
-        ms = reduce_max(dist, sum(ts) / len(ts))
-        wall = reduce_max(dist, sum(tw) / len(tw))
-        units = reduce_sum(dist, sc.nv * sc.substeps)
-        out = {"value": units / (ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": ms,
-               "wall_ms_per_frame": wall, "launches_per_frame": (g.launch_count() - l0) / frames}
-        g.close()
-        return out
+    def timed_scene(sc, per_frame=None, solver=None):
+        return time_scene(V, torch, flush, dist, sc, frames, per_frame, solver)
 
     base = S.muscle_rig(seed=1 + rank)
     warm = dataclasses.replace(base, warm_start=True)
@@ -450,8 +459,8 @@ def bench_muscles(V, torch, flush, dist, frames, rank=0):
 
     res = {"workload": f"muscle_rig {base.n_rods} rods / {base.nv} vertices, {base.mesh.n} mesh vertices, "
                        "10 substeps x 4 iterations + LBS",
-           "plain_rig": time_scene(base),
-           "activation_and_warm_start": time_scene(warm, activate)}
+           "plain_rig": timed_scene(base),
+           "activation_and_warm_start": timed_scene(warm, activate)}
     # the activation update alone: upload + device recompute of the rest tables
     g = V.Scene(warm)
     st = g.stream
@@ -472,7 +481,11 @@ def bench_muscles(V, torch, flush, dist, frames, rank=0):
                                                 "thicken and shorten, so contacts and pairs change too; "
                                                 "(n_rods floats uploaded, rest tables recomputed on the device), warm start from the bones")
     bm = S.bundled_muscles(n_muscles=96)
-    res["bundled_muscles"] = time_scene(bm)
+    res["bundled_muscles"] = timed_scene(bm)
+    # the printed vector volume form (plain solver only) against the scalar form on the plain solver
+    res["volume_forms_plain_solver"] = {
+        "scalar": timed_scene(base, solver=V.SOLVER_PLAIN),
+        "vector": timed_scene(dataclasses.replace(base, volume_vector=True), solver=V.SOLVER_PLAIN)}
     res["bundled_muscles"]["workload"] = (f"{bm.n_rods // 7} muscles x 7 fibre rods x 16 vertices "
                                           f"({bm.nv} vertices), shape matching of every cross-section per substep, "
                                           "contacts between muscles, 10 substeps x 4 iterations")

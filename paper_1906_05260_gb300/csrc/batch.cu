@@ -207,7 +207,12 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
 // the grid, cell counts (in shared memory when the grid spans at most
 // kGridSmemCells cells, else in cell_count), the exclusive cell scan into
 // cell_start, and the scatter into cell order with the sphere / group copies.
-constexpr int kGridThreads = 1024, kGridSmemCells = 12288, kGridMaxPills = 1 << 16;
+// Up to kGridThreads x kGridRegPills pills, each thread keeps its pills'
+// spheres in registers from the first phase to the scatter: the
+// loads of a batch of 8 pills are issued together, so the phase waits for two
+// memory latencies per batch instead of two per pill, and the later phases
+// read nothing from memory.
+constexpr int kGridThreads = 512, kGridSmemCells = 12288, kGridMaxPills = 1 << 16, kGridRegPills = 16;
 
 __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
 {
@@ -222,7 +227,35 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
     if (t < 8) s_bounds[t] = 0u;
     __syncthreads();
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
-    for (int g = t; g < ns; g += bd) bound_pill(P, g, mn, mx, mr);
+    const bool reg = ns <= bd * kGridRegPills;  // uniform over the CTA
+    float4 sph[kGridRegPills];
+    if (reg) {
+#pragma unroll
+        for (int b = 0; b < kGridRegPills; b += 8) {
+            int av[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int g = t + (b + k) * bd;
+                av[k] = g < ns ? P.seg_v0[g] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int a = av[k];
+                sph[b + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (a >= 0) {
+                    const float ra = P.bp_rbar[(size_t)a * P.bp_rbar_stride];
+                    const float rb = P.bp_rbar[(size_t)(a + 1) * P.bp_rbar_stride];
+                    const float4 sp = pill_sphere(P.Xpred[a], ra, P.Xpred[a + 1], rb);
+                    sph[b + k] = sp;
+                    mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
+                    mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
+                    mr = fmaxf(mr, sp.w);
+                }
+            }
+        }
+    } else {
+        for (int g = t; g < ns; g += bd) bound_pill(P, g, mn, mx, mr);
+    }
     merge_bounds_to(s_bounds, mn, mx, mr);
     __syncthreads();
     bool ok;
@@ -238,10 +271,16 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         if (!ok) atomicOr(P.err, ERR_NONFINITE);
     }
     __syncthreads();
-    for (int g = t; g < ns; g += bd) {
-        const int cell = bp_cell(G, P.spheres[g]);
-        P.cell_of[g] = cell;
-        atomicAdd(cnt + cell, 1);
+    if (reg) {
+#pragma unroll
+        for (int k = 0; k < kGridRegPills; ++k)
+            if (t + k * bd < ns) atomicAdd(cnt + bp_cell(G, sph[k]), 1);
+    } else {
+        for (int g = t; g < ns; g += bd) {
+            const int cell = bp_cell(G, P.spheres[g]);
+            P.cell_of[g] = cell;
+            atomicAdd(cnt + cell, 1);
+        }
     }
     __syncthreads();
     // exclusive scans of the counts (into cell_start, and into cnt as the running
@@ -280,11 +319,27 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         *P.n_chunks = ccarry;
     }
     __syncthreads();
-    for (int g = t; g < ns; g += bd) {
-        const int pos = atomicAdd(cnt + P.cell_of[g], 1);
-        P.cell_pills[pos] = g;
-        P.cell_sph[pos] = P.spheres[g];
-        P.cell_grp[pos] = P.seg_group[g];
+    if (reg) {
+        int grp[kGridRegPills];  // loaded together, before the (generic-address) atomics
+#pragma unroll
+        for (int k = 0; k < kGridRegPills; ++k) grp[k] = t + k * bd < ns ? P.seg_group[t + k * bd] : 0;
+#pragma unroll
+        for (int k = 0; k < kGridRegPills; ++k) {
+            const int g = t + k * bd;
+            if (g < ns) {
+                const int pos = atomicAdd(cnt + bp_cell(G, sph[k]), 1);
+                P.cell_pills[pos] = g;
+                P.cell_sph[pos] = sph[k];
+                P.cell_grp[pos] = grp[k];
+            }
+        }
+    } else {
+        for (int g = t; g < ns; g += bd) {
+            const int pos = atomicAdd(cnt + P.cell_of[g], 1);
+            P.cell_pills[pos] = g;
+            P.cell_sph[pos] = P.spheres[g];
+            P.cell_grp[pos] = P.seg_group[g];
+        }
     }
     if (!in_smem) {  // return cell_count to zero for the next substep
         __syncthreads();
@@ -434,7 +489,11 @@ void launch(void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-constexpr int kEmitPillsPerWarp = 4;
+// Pills per pair-search warp: a scene has about 0.44 ns + 14 (occupied cells)
+// work units.  Groups of few pills get one warp per couple of units, so that
+// the units' dependent loads run side by side on more warps; large groups fill
+// the GPU with a few units per warp.
+constexpr int kEmitPillsPerWarp = 4, kEmitPillsPerWarpSmall = 1, kEmitSmallGroup = 16384;
 constexpr int kMeshPerThread = 16;  // kLbsBatch vertices per round, 4 rounds
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -500,7 +559,8 @@ struct Shape {
 // Device view of one scene for a frame of sub-step h (b.P.bq1 / bt1: the
 // scene's own target pose; the caller may point them elsewhere), and its
 // blocks per kernel kind.
-void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_batch_item &it, double h, bool cp)
+void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_batch_item &it, double h, bool cp,
+                int emit_ppw)
 {
     memset(&b, 0, sizeof(b));
     b.P = s->P;
@@ -526,7 +586,7 @@ void fill_scene(BatchScene &b, int cnt[K_KINDS], viper_scene *s, const viper_bat
     const int nv = s->nv, ns = s->ns;
     cnt[K_ELEM] = cdiv(nv + ns, kElemThreads);
     cnt[K_PILL] = b.pills ? cdiv(ns, kElemThreads) : 0;
-    cnt[K_EMIT] = b.pills ? cdiv(ns, kEmitWarpsB * kEmitPillsPerWarp) : 0;  // a few work units per warp
+    cnt[K_EMIT] = b.pills ? cdiv(ns, kEmitWarpsB * emit_ppw) : 0;  // about 0.4 emit_ppw work units per warp
     cnt[K_SCAN] = b.pills ? 1 : 0;
     cnt[K_ROD] = s->n_items;
     cnt[K_CONTACT] = cp ? std::min(64, std::max(1, cdiv(ns + (s->n_planes > 0 ? nv : 0), kElemThreads))) : 0;
@@ -641,13 +701,17 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     const double h = (double)dt / substeps;
     size_t bcur = 0;
     Shape sh;
+    long long group_pills = 0;
+    for (int i : idx)
+        if (items[i].scene->flags & VIPER_FLAG_CONTACTS) group_pills += items[i].scene->ns;
+    const int emit_ppw = group_pills <= kEmitSmallGroup ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
     for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1)] = 0;
     for (int k = 0; k < n; ++k) {
         const viper_batch_item &it = items[idx[k]];
         viper_scene *s = it.scene;
         BatchScene &b = hs[k];
         int cnt[K_KINDS];
-        fill_scene(b, cnt, s, it, h, cp);
+        fill_scene(b, cnt, s, it, h, cp, emit_ppw);
         if (it.bone_quat && s->n_bones > 0) {  // this frame's target pose, from the call's table
             memcpy(hbq + bcur, it.bone_quat, sizeof(float4) * s->n_bones);
             memcpy(hbt + 3 * bcur, it.bone_trans, sizeof(float) * 3 * s->n_bones);
@@ -696,7 +760,8 @@ int self_batch_capture(viper_scene *s, float dt, int substeps, int iterations, c
     it.scene = s;
     const bool cp = scene_contact_path(s);
     int cnt[K_KINDS];
-    fill_scene(*b, cnt, s, it, (double)dt / substeps, cp);  // bones: the scene's own target pose
+    const int emit_ppw = s->ns <= kEmitSmallGroup ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
+    fill_scene(*b, cnt, s, it, (double)dt / substeps, cp, emit_ppw);  // bones: the scene's own target pose
     Shape sh;
     shape_add(sh, s, cp);
     for (int c = 0; c < K_KINDS; ++c) {
