@@ -204,49 +204,126 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
 }
 
 // One scene's broadphase grid by one CTA: bounding spheres and their bounds,
-// the grid, cell counts (in shared memory when the grid spans at most
-// kGridSmemCells cells, else in cell_count), the exclusive cell scan into
-// cell_start, and the scatter into cell order with the sphere / group copies.
-// Up to kGridThreads x kGridRegPills pills, each thread keeps its pills'
-// spheres in registers from the first phase to the scatter: the
-// loads of a batch of 8 pills are issued together, so the phase waits for two
-// memory latencies per batch instead of two per pill, and the later phases
-// read nothing from memory.
-constexpr int kGridThreads = 512, kGridSmemCells = 12288, kGridMaxPills = 1 << 16, kGridRegPills = 16;
+// the grid, cell counts, the exclusive cell scan into cell_start (and the
+// list of 32-pill chunks per cell, chunk_of), and the scatter into cell order
+// with the sphere / group copies.
+//
+// Small scenes (at most kGridSmemVerts vertices and kGridSmemCells cells) run
+// from shared memory: the spheres are built per vertex slot (vertex v starts a
+// pill when vtx_seg[v + 1] = vtx_seg[v] + 1, so all loads of a slot are
+// independent), cell counts and offsets live in shared memory, the scan runs
+// warp-strided over consecutive cells (conflict-free, coalesced stores), and
+// the scatter goes through a shared permutation so that the cell-order arrays
+// are written with coalesced stores.  Larger scenes take the general path:
+// spheres and cells in global memory, counts in shared memory when the grid
+// spans at most kGridSmemCells cells, else in cell_count.
+constexpr int kGridThreads = 512, kGridSmemCells = 8192, kGridMaxPills = 1 << 16, kGridSmemVerts = 8192;
+constexpr int kGridSmemBytes = 4 * kGridSmemCells + (16 + 4 + 4) * kGridSmemVerts;  // 224 KB
+
+// Warp-strided exclusive scan of cnt[0, cells) into cnt (as each cell's fill
+// position) and cell_start, with the 32-pill chunks of every cell listed in
+// chunk_of.  Warp w owns cells [w m 32, (w + 1) m 32), m = ceil(cells / (32 W)).
+__device__ __forceinline__ void grid_scan_small(const Params &P, int *cnt, int cells, int *ws)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m = (cells + 32 * nw - 1) / (32 * nw);
+    const int c0 = w * m * 32;
+    int s = 0, cs = 0;
+    for (int j = 0; j < m; ++j) {
+        const int c = c0 + 32 * j + lane;
+        const int v = c < cells ? cnt[c] : 0;
+        s += v;
+        cs += (v + 31) >> 5;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    }
+    if (lane == 0) {
+        ws[w] = s;
+        ws[16 + w] = cs;
+    }
+    __syncthreads();
+    if (w == 0) {  // exclusive prefix of the warp totals (at most 16 warps)
+        const int a = lane < nw ? ws[lane] : 0, b = lane < nw ? ws[16 + lane] : 0;
+        const int ia = warp_incl_scan(a), ib = warp_incl_scan(b);
+        __syncwarp();
+        if (lane < nw) {
+            ws[lane] = ia - a;
+            ws[16 + lane] = ib - b;
+        }
+        if (lane == nw - 1) {
+            P.cell_start[cells] = ia;
+            *P.n_chunks = ib;
+        }
+    }
+    __syncthreads();
+    int off = ws[w], coff = ws[16 + w];
+    int2 *chunk_of = P.chunk_of;
+    int *cell_start = P.cell_start;
+    for (int j = 0; j < m; ++j) {
+        const int c = c0 + 32 * j + lane;
+        const int v = c < cells ? cnt[c] : 0, nch = (v + 31) >> 5;
+        const int iv = warp_incl_scan(v), ic = warp_incl_scan(nch);
+        if (c < cells) {
+            const int o = off + iv - v, oc = coff + ic - nch;
+            cell_start[c] = o;
+            cnt[c] = o;
+            for (int h = 0; h < nch; ++h) chunk_of[oc + h] = make_int2(c, h);
+        }
+        off += __shfl_sync(0xffffffffu, iv, 31);
+        coff += __shfl_sync(0xffffffffu, ic, 31);
+    }
+}
 
 __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
 {
     __shared__ BatchScene sb;
     __shared__ unsigned int s_bounds[8];
     __shared__ int ws[33];
-    extern __shared__ int s_cells[];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    int *s_cells = reinterpret_cast<int *>(s_dyn);
     int local, nblk;
     batch_enter(A, K_SCAN, sb, local, nblk);
     const Params &P = sb.P;
-    const int t = threadIdx.x, bd = blockDim.x, ns = P.ns;
+    const int t = threadIdx.x, bd = blockDim.x, ns = P.ns, nv = P.nv;
     if (t < 8) s_bounds[t] = 0u;
     __syncthreads();
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
-    const bool reg = ns <= bd * kGridRegPills;  // uniform over the CTA
-    float4 sph[kGridRegPills];
-    if (reg) {
-#pragma unroll
-        for (int b = 0; b < kGridRegPills; b += 8) {
-            int av[8];
+    const bool small = nv <= kGridSmemVerts;  // uniform over the CTA
+    float4 *s_sph = reinterpret_cast<float4 *>(s_dyn + 4 * kGridSmemCells);
+    int *s_pill = reinterpret_cast<int *>(s_dyn + 4 * kGridSmemCells + 16 * kGridSmemVerts);
+    int *s_perm = reinterpret_cast<int *>(s_dyn + 4 * kGridSmemCells + 20 * kGridSmemVerts);
+    if (small) {
+        const int *vtx_seg = P.vtx_seg;
+        const float4 *xp = P.Xpred;
+        const float *rbar = P.bp_rbar;
+        const size_t rs = (size_t)P.bp_rbar_stride;
+        for (int base = 0; base < nv; base += 8 * bd) {
+            int ga[8], gb[8];
+            float4 xa[8], xb[8];
+            float ra[8], rb[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int g = t + (b + k) * bd;
-                av[k] = g < ns ? P.seg_v0[g] : -1;
+                const int v = base + k * bd + t;
+                const bool ok = v + 1 < nv;
+                ga[k] = ok ? vtx_seg[v] : 0;
+                gb[k] = ok ? vtx_seg[v + 1] : 0;
+                xa[k] = ok ? xp[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+                xb[k] = ok ? xp[v + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ra[k] = ok ? rbar[(size_t)v * rs] : 0.f;
+                rb[k] = ok ? rbar[(size_t)(v + 1) * rs] : 0.f;
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int a = av[k];
-                sph[b + k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (a >= 0) {
-                    const float ra = P.bp_rbar[(size_t)a * P.bp_rbar_stride];
-                    const float rb = P.bp_rbar[(size_t)(a + 1) * P.bp_rbar_stride];
-                    const float4 sp = pill_sphere(P.Xpred[a], ra, P.Xpred[a + 1], rb);
-                    sph[b + k] = sp;
+                const int v = base + k * bd + t;
+                if (v >= nv) continue;
+                const bool pill = v + 1 < nv && gb[k] == ga[k] + 1;  // v and v + 1 on one rod
+                s_pill[v] = pill ? ga[k] : -1;
+                if (pill) {
+                    const float4 sp = pill_sphere(xa[k], ra[k], xb[k], rb[k]);
+                    s_sph[v] = sp;
                     mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
                     mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
                     mr = fmaxf(mr, sp.w);
@@ -262,7 +339,7 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
     const Grid G = make_grid_from(s_bounds, P.table, ok);
     const int cells = (int)min((long long)G.dim[0] * G.dim[1] * G.dim[2], (long long)P.table);
     const bool in_smem = cells <= kGridSmemCells;
-    int *cnt = in_smem ? s_cells : P.cell_count;  // cell_count is zero between substeps
+    // counts in s_cells, or in cell_count (zero between substeps) for larger grids
     if (in_smem)
         for (int c = t; c < cells; c += bd) s_cells[c] = 0;
     if (t == 0) {
@@ -271,21 +348,58 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         if (!ok) atomicOr(P.err, ERR_NONFINITE);
     }
     __syncthreads();
-    if (reg) {
+    if (small && in_smem) {
+        for (int v = t; v < nv; v += bd)
+            if (s_pill[v] >= 0) atomicAdd(s_cells + bp_cell(G, s_sph[v]), 1);
+        __syncthreads();
+        grid_scan_small(P, s_cells, cells, ws);
+        __syncthreads();
+        // cell-order slot of every pill into the shared permutation, then the
+        // cell-order arrays with coalesced stores
+        for (int v = t; v < nv; v += bd)
+            if (s_pill[v] >= 0) s_perm[atomicAdd(s_cells + bp_cell(G, s_sph[v]), 1)] = v;
+        __syncthreads();
+        const int *seg_group = P.seg_group;
+        int *cell_pills = P.cell_pills, *cell_grp = P.cell_grp;
+        float4 *cell_sph = P.cell_sph;
+        for (int q0 = 0; q0 < ns; q0 += 8 * bd) {
+            int vq[8], gq[8];
 #pragma unroll
-        for (int k = 0; k < kGridRegPills; ++k)
-            if (t + k * bd < ns) atomicAdd(cnt + bp_cell(G, sph[k]), 1);
-    } else {
-        for (int g = t; g < ns; g += bd) {
-            const int cell = bp_cell(G, P.spheres[g]);
-            P.cell_of[g] = cell;
-            atomicAdd(cnt + cell, 1);
+            for (int k = 0; k < 8; ++k) {
+                const int q = q0 + k * bd + t;
+                vq[k] = q < ns ? s_perm[q] : 0;
+                gq[k] = q < ns ? seg_group[s_pill[vq[k]]] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int q = q0 + k * bd + t;
+                if (q < ns) {
+                    cell_pills[q] = s_pill[vq[k]];
+                    cell_sph[q] = s_sph[vq[k]];
+                    cell_grp[q] = gq[k];
+                }
+            }
         }
+        return;
+    }
+    // general path
+    if (small) {  // spheres were built in shared memory: hand them to the global arrays
+        for (int v = t; v < nv; v += bd)
+            if (s_pill[v] >= 0) P.spheres[s_pill[v]] = s_sph[v];
+        __syncthreads();
+    }
+    for (int g = t; g < ns; g += bd) {
+        const int cell = bp_cell(G, P.spheres[g]);
+        P.cell_of[g] = cell;
+        if (in_smem)
+            atomicAdd(s_cells + cell, 1);
+        else
+            atomicAdd(P.cell_count + cell, 1);
     }
     __syncthreads();
-    // exclusive scans of the counts (into cell_start, and into cnt as the running
-    // fill position of each cell) and of the 32-pill chunks per cell (into the
-    // pair search's work list chunk_of)
+    // exclusive scans of the counts (into cell_start, and into the counts as the
+    // running fill position of each cell) and of the 32-pill chunks per cell
+    // (into the pair search's work list chunk_of)
     int carry = 0, ccarry = 0;
     for (int base = 0; base < cells; base += bd * kScanPerB) {
         const int b0 = base + t * kScanPerB;
@@ -304,7 +418,10 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         for (int k = 0; k < kScanPerB; ++k) {
             if (b0 + k < cells) {
                 P.cell_start[b0 + k] = off;
-                cnt[b0 + k] = off;
+                if (in_smem)
+                    s_cells[b0 + k] = off;
+                else
+                    P.cell_count[b0 + k] = off;
                 const int nch = (v[k] + 31) >> 5;
                 for (int h = 0; h < nch; ++h) P.chunk_of[coff + h] = make_int2(b0 + k, h);
                 coff += nch;
@@ -319,27 +436,11 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         *P.n_chunks = ccarry;
     }
     __syncthreads();
-    if (reg) {
-        int grp[kGridRegPills];  // loaded together, before the (generic-address) atomics
-#pragma unroll
-        for (int k = 0; k < kGridRegPills; ++k) grp[k] = t + k * bd < ns ? P.seg_group[t + k * bd] : 0;
-#pragma unroll
-        for (int k = 0; k < kGridRegPills; ++k) {
-            const int g = t + k * bd;
-            if (g < ns) {
-                const int pos = atomicAdd(cnt + bp_cell(G, sph[k]), 1);
-                P.cell_pills[pos] = g;
-                P.cell_sph[pos] = sph[k];
-                P.cell_grp[pos] = grp[k];
-            }
-        }
-    } else {
-        for (int g = t; g < ns; g += bd) {
-            const int pos = atomicAdd(cnt + P.cell_of[g], 1);
-            P.cell_pills[pos] = g;
-            P.cell_sph[pos] = P.spheres[g];
-            P.cell_grp[pos] = P.seg_group[g];
-        }
+    for (int g = t; g < ns; g += bd) {
+        const int pos = in_smem ? atomicAdd(s_cells + P.cell_of[g], 1) : atomicAdd(P.cell_count + P.cell_of[g], 1);
+        P.cell_pills[pos] = g;
+        P.cell_sph[pos] = P.spheres[g];
+        P.cell_grp[pos] = P.seg_group[g];
     }
     if (!in_smem) {  // return cell_count to zero for the next substep
         __syncthreads();
@@ -616,7 +717,7 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
                             : reinterpret_cast<const void *>(batch_rod_kernel<true>);
     if (raise_smem_limit(rod_fn, smem) != 0) return -1;
     if (cp && raise_smem_limit(reinterpret_cast<const void *>(batch_rod_first_kernel), smem) != 0) return -1;
-    const int grid_smem = sizeof(int) * kGridSmemCells;
+    const int grid_smem = kGridSmemBytes;
     if (fused_grid && raise_smem_limit(reinterpret_cast<const void *>(batch_grid_kernel), grid_smem) != 0) return -1;
     long long L = 0;
     auto go = [&](int cls, auto &&fn) {

@@ -388,7 +388,7 @@ int rebuild(viper_scene *s, bool keep_state)
     // internal-order tables
     std::vector<float4> LQ(ns), LC(ns);
     std::vector<int> seg_v0(ns), vtx_seg(nv), seg_group(ns), rod_of_v(nv);
-    std::vector<float4> rod_origin(nr);
+    std::vector<float4> rod_origin(nr), seg_org(ns);
     for (int k = 0; k < nr; ++k) {
         int r = S.rod_order[k];
         int n = s->h_rod_n[r];
@@ -404,6 +404,7 @@ int rebuild(viper_scene *s, bool keep_state)
             LC[gi] = s->u_LC[gu];
             seg_v0[gi] = s->h_int_off[k] + j;
             seg_group[gi] = s->u_group[r];
+            seg_org[gi] = s->u_origin[r];
         }
     }
     Params &P = s->P;
@@ -416,6 +417,7 @@ int rebuild(viper_scene *s, bool keep_state)
     if ((rc = upload(s, const_cast<int *>(P.seg_group), seg_group))) return rc;
     if ((rc = upload(s, const_cast<int *>(P.rod_of_v), rod_of_v))) return rc;
     if ((rc = upload(s, const_cast<float4 *>(P.rod_origin), rod_origin))) return rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.seg_org), seg_org))) return rc;
     if ((rc = upload(s, s->d_vperm, s->h_vperm))) return rc;
     if ((rc = upload(s, s->d_sperm, s->h_sperm))) return rc;
     if ((rc = upload(s, s->d_sinv, s->h_sinv))) return rc;
@@ -718,7 +720,7 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
     b += 16 * (7 * nv + 4 * ns);          // X V Xp Xpred RV0 RV1 ... state and rest
     b += 16 * (4 * ns) + 8 * ns;          // Q W Qp RS0, RS1
     b += 16 * 2 * ns + 48 * ns;           // LQ LC frames
-    b += 4 * (3 * ns + 3 * nv + 3 * ns) + 16 * nr;  // index tables, perms, rod origins
+    b += 4 * (3 * ns + 3 * nv + 3 * ns) + 16 * nr + 16 * ns;  // index tables, perms, rod origins (per rod, per segment)
     b += 16 * (ns + nv) + 8 * ns + 4 * nv;  // plain multipliers
     b += (16 + 8 + 88) * 3 * nv;          // schedule + slot multipliers (upper bound)
     b += 16 * (nv > ns ? nv : ns) + 4 * nv;  // staging
@@ -868,7 +870,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     AC(P.RS0, float4, ns); AC(P.RS1, float2, ns);
     if (!s->u_warm.empty()) AC(P.warm, float4, nv);
     AC(P.seg_v0, int, ns); AC(P.vtx_seg, int, nv); AC(P.seg_group, int, ns);
-    AC(P.rod_of_v, int, nv); AC(P.rod_origin, float4, nr);
+    AC(P.rod_of_v, int, nv); AC(P.rod_origin, float4, nr); AC(P.seg_org, float4, ns);
     A(s->LQ, ns); A(s->LC, ns); A(s->frames, 3 * (size_t)ns);
     A(s->d_vperm, nv); A(s->d_sperm, ns); A(s->d_sinv, ns);
     A(P.lamS, ns); A(P.lamS2, ns); A(P.lamB, nv); A(P.lamB2, nv); A(P.lamL, nv);

@@ -1037,7 +1037,13 @@ __device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
 {
     const int2 pr = P.pairs[i];
     const int va = P.seg_v0[pr.x], vb = P.seg_v0[pr.y];
-    const float4 xa1 = world_of(P, va), xa2 = world_of(P, va + 1), xb1 = world_of(P, vb), xb2 = world_of(P, vb + 1);
+    // the segments' rod origins, loaded beside their first vertices (not through rod_of_v)
+    const float4 oa = P.seg_org[pr.x], ob = P.seg_org[pr.y];
+    auto wpos = [&](int v, const float4 &o) {
+        const float4 x = P.X[v];
+        return make_float4(__fadd_rn(x.x, o.x), __fadd_rn(x.y, o.y), __fadd_rn(x.z, o.z), x.w);
+    };
+    const float4 xa1 = wpos(va, oa), xa2 = wpos(va + 1, oa), xb1 = wpos(vb, ob), xb2 = wpos(vb + 1, ob);
     const float ra1 = P.RV0[va].w, ra2 = P.RV0[va + 1].w, rb1 = P.RV0[vb].w, rb2 = P.RV0[vb + 1].w;
     PillPair Q;
     Q.a1 = xyz(xa1); Q.a2 = xyz(xa2); Q.b1 = xyz(xb1); Q.b2 = xyz(xb2);

@@ -57,6 +57,7 @@ struct Params {
     // from the world origin; world = local + rod_origin[rod_of_v[v]].
     const float4 *rod_origin;
     const int *rod_of_v;
+    const float4 *seg_org;  // rod_origin of each segment's rod (the contact pass's pills)
     const float4 *pins, *bq0, *bq1, *planes;
     const float *bt0, *bt1;  // bone origins, 3 floats per bone
     // plain-path multipliers
