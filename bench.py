@@ -434,7 +434,7 @@ def time_scene(V, torch, flush, dist, sc, frames, per_frame=None, solver=None):
 
 
 def bench_muscles(V, torch, flush, dist, frames, rank=0):
-    """Muscle features on the headline rig and on bundled muscles (Sec. 7.3, 7.5):
+    """Muscle features on the headline rig and on bundled muscles (Sec. 7.3, 8.2):
     per-frame time with a time-varying activation (rest tables recomputed on the
     host and uploaded every frame, inside the timed region) and the bone-driven
     warm start, against the same rig without them; bundled fibre muscles with

@@ -57,7 +57,7 @@ extern "C" {
  * four-colour Gauss-Seidel sweep.  Needs every rod in shared memory (at most
  * resident_max vertices) and a non-plain solver: VIPER_EINVAL otherwise. */
 #define VIPER_FLAG_JACOBI 8
-/* Warm start from the bones (Sec. 7.5 muscles): before a frame's first substep,
+/* Warm start from the bones (Sec. 8.2 muscles): before a frame's first substep,
  * every rod pinned at both ends to bones b0, b1 moves by linear blend skinning
  * with the two bones' transforms from their previous to their target pose,
  * T_b(p) = R1 R0^T (p - t0) + t1, weighted (1 - t, t) by the vertex's rest
@@ -180,7 +180,7 @@ int viper_prepare(viper_scene *scene, float dt, int substeps, int iterations);
 int viper_set_bones(viper_scene *scene, int n_bones, const float *quat, const float *trans);
 
 /*
- * Muscle activation (Sec. 7.5, fibre shortening).  activation[r] in [0, 0.9]
+ * Muscle activation (Sec. 8.2, fibre shortening).  activation[r] in [0, 0.9]
  * per rod in the caller's order (host memory, n_rods floats), or NULL for the
  * original rest state.  Rod r's rest lengths become (1 - a_r) times the
  * original ones and its rest radii 1/sqrt(1 - a_r) times theirs (rest volume

@@ -323,8 +323,8 @@ int vo_vertex_constraint(int kind, const double *qa, const double *qb, double s,
 /* ------------------------------------------------------------------------ */
 
 /*
- * K = (disc integral of the potential's coefficient) x element length (Sec. 6:
- * "stiffness parameters multiplied by the length of the piecewise elements");
+ * K = (disc integral of the potential's coefficient) x element length (Sec. 6
+ * scales the stiffness of each piecewise element by its length);
  * the objective carries 1/2 ||W||_K^2, so the printed energy coefficients are K
  * per unit length.  Compliance alpha = K^-1.  reading: one modulus per family,
  * k = 1/c, isotropic (k^x = k^y = k^z).
@@ -832,7 +832,7 @@ int vo_shape_match(vo_scene *S)
 
 /*
  * Bounding sphere of a pill in IEEE single precision, fixed operation order
- * (reading: the paper only says "bounding sphere"; an exact FP32 predicate
+ * (reading: the paper fixes only a conservative bounding sphere; an exact FP32 predicate
  * makes the candidate set reproducible bit for bit):
  *   c = (x1 + x2) * 0.5,  R = 0.5 * sqrt((dx*dx + dy*dy) + dz*dz) + max(r1, r2),
  *   r_k = s_k * rbar_k.   Pair test: ((ex*ex + ey*ey) + ez*ez) <= (Ra + Rb)^2.
@@ -1077,14 +1077,14 @@ int vo_narrowphase(const double *a1, double ra1, const double *a2, double ra2, c
 }
 
 /*
- * Contact pass (Sec. 7 "Jacobi solver ... displacements averaged", Sec. 7.2):
+ * Contact pass (Sec. 7: Jacobi iterations with averaged displacements, Sec. 7.2):
  * every candidate pair and every vertex-plane pair is evaluated on the state at
  * the start of the pass; each active constraint (C < 0) takes one XPBD update
  * with its own multiplier; each vertex then moves by the sum of its
  * corrections divided by the number of active constraints touching it.
  * Contact constraint: C = |c_a(alpha*) - c_b(beta*)| - r_a(alpha*) - r_b(beta*)
  * with alpha*, beta* held fixed; r = s rbar, so the constraint also acts on
- * the scales (it "correlates radii and positions").
+ * the scales (the paper couples contact radii with positions).
  * Half-plane (Sec. 7): per vertex sphere C = n.x - d - s rbar (the capsule's
  * distance to a plane is linear along the pill, so its end spheres suffice).
  */
@@ -1458,7 +1458,7 @@ static int state_finite(const vo_scene *S)
 }
 
 /*
- * Warm start from the bones (Sec. 7.5 muscle simulation): each vertex of a rod
+ * Warm start from the bones (Sec. 8.2 muscle simulation): each vertex of a rod
  * whose two ends are pinned to bones b0, b1 moves, before the frame's first
  * substep, by linear blend skinning with those two bones' transforms relative
  * to their previous poses, T_b = [R1 R0^T, t1 - R1 R0^T t0].  Reading: the

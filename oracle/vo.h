@@ -51,7 +51,7 @@ typedef struct vo_desc {
     int volume_vector;           /* volume constraint in the printed vector form  */
                                  /* (Sec. 5) instead of the determinant's scalar  */
     int warm_start;              /* bone-driven LBS initialisation per frame      */
-                                 /* (Sec. 7.5 muscle simulation)                  */
+                                 /* (Sec. 8.2 muscle simulation)                  */
     int n_bundles;               /* rod bundles for shape matching (Sec. 7.3)     */
     const int *bundle_offsets;   /* [n_bundles+1] CSR into bundle_rods            */
     const int *bundle_rods;      /* rods of each bundle, all of one vertex count  */
@@ -93,7 +93,7 @@ double vo_laplacian_compliance(const vo_scene *s, int i);
 /* Rotation R (row-major 3x3) maximising trace(R^T A): the rotational part
  * of the polar decomposition of A, by Horn's quaternion eigenvector. */
 int vo_polar_rotation(const double *A, double *R);
-/* Muscle activation (Sec. 7.5, fibre shortening): rod r's rest lengths become
+/* Muscle activation (Sec. 8.2, fibre shortening): rod r's rest lengths become
  * (1 - a_r) times the original ones and its rest radii 1/sqrt(1 - a_r) times
  * theirs (rest volume and mass kept); everything derived from them follows.
  * a_r in [0, 0.9]; NULL restores the original rest state. */

@@ -223,7 +223,8 @@ constexpr int kGridSmemBytes = 4 * kGridSmemCells + (16 + 4 + 4) * kGridSmemVert
 // Warp-strided exclusive scan of cnt[0, cells) into cnt (as each cell's fill
 // position) and cell_start, with the 32-pill chunks of every cell listed in
 // chunk_of.  Warp w owns cells [w m 32, (w + 1) m 32), m = ceil(cells / (32 W)).
-__device__ __forceinline__ void grid_scan_small(const Params &P, int *cnt, int cells, int *ws)
+// cnt is shared memory, or cell_count (`global`: written by atomics, read from L2).
+__device__ __forceinline__ void grid_scan(const Params &P, int *cnt, int cells, int *ws, bool global)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m = (cells + 32 * nw - 1) / (32 * nw);
@@ -231,7 +232,7 @@ __device__ __forceinline__ void grid_scan_small(const Params &P, int *cnt, int c
     int s = 0, cs = 0;
     for (int j = 0; j < m; ++j) {
         const int c = c0 + 32 * j + lane;
-        const int v = c < cells ? cnt[c] : 0;
+        const int v = c < cells ? (global ? __ldcg(cnt + c) : cnt[c]) : 0;
         s += v;
         cs += (v + 31) >> 5;
     }
@@ -264,7 +265,7 @@ __device__ __forceinline__ void grid_scan_small(const Params &P, int *cnt, int c
     int *cell_start = P.cell_start;
     for (int j = 0; j < m; ++j) {
         const int c = c0 + 32 * j + lane;
-        const int v = c < cells ? cnt[c] : 0, nch = (v + 31) >> 5;
+        const int v = c < cells ? (global ? __ldcg(cnt + c) : cnt[c]) : 0, nch = (v + 31) >> 5;
         const int iv = warp_incl_scan(v), ic = warp_incl_scan(nch);
         if (c < cells) {
             const int o = off + iv - v, oc = coff + ic - nch;
@@ -331,7 +332,29 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
             }
         }
     } else {
-        for (int g = t; g < ns; g += bd) bound_pill(P, g, mn, mx, mr);
+        for (int g0 = 0; g0 < ns; g0 += 8 * bd) {  // 8 pills per thread and batch, loads issued together
+            int av[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int g = g0 + k * bd + t;
+                av[k] = g < ns ? P.seg_v0[g] : -1;
+            }
+            float4 sp[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int a = av[k] < 0 ? 0 : av[k];
+                sp[k] = pill_sphere(P.Xpred[a], P.bp_rbar[(size_t)a * P.bp_rbar_stride], P.Xpred[a + 1],
+                                    P.bp_rbar[(size_t)(a + 1) * P.bp_rbar_stride]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (av[k] < 0) continue;
+                P.spheres[g0 + k * bd + t] = sp[k];
+                mn[0] = fminf(mn[0], sp[k].x); mn[1] = fminf(mn[1], sp[k].y); mn[2] = fminf(mn[2], sp[k].z);
+                mx[0] = fmaxf(mx[0], sp[k].x); mx[1] = fmaxf(mx[1], sp[k].y); mx[2] = fmaxf(mx[2], sp[k].z);
+                mr = fmaxf(mr, sp[k].w);
+            }
+        }
     }
     merge_bounds_to(s_bounds, mn, mx, mr);
     __syncthreads();
@@ -352,7 +375,7 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
         for (int v = t; v < nv; v += bd)
             if (s_pill[v] >= 0) atomicAdd(s_cells + bp_cell(G, s_sph[v]), 1);
         __syncthreads();
-        grid_scan_small(P, s_cells, cells, ws);
+        grid_scan(P, s_cells, cells, ws, false);
         __syncthreads();
         // cell-order slot of every pill into the shared permutation, then the
         // cell-order arrays with coalesced stores
@@ -388,59 +411,48 @@ __global__ void __launch_bounds__(kGridThreads) batch_grid_kernel(BatchArgs A)
             if (s_pill[v] >= 0) P.spheres[s_pill[v]] = s_sph[v];
         __syncthreads();
     }
-    for (int g = t; g < ns; g += bd) {
-        const int cell = bp_cell(G, P.spheres[g]);
-        P.cell_of[g] = cell;
-        if (in_smem)
-            atomicAdd(s_cells + cell, 1);
-        else
-            atomicAdd(P.cell_count + cell, 1);
+    for (int g0 = 0; g0 < ns; g0 += 8 * bd) {
+        float4 sp[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int g = g0 + k * bd + t;
+            sp[k] = g < ns ? P.spheres[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int g = g0 + k * bd + t;
+            if (g >= ns) continue;
+            const int cell = bp_cell(G, sp[k]);
+            P.cell_of[g] = cell;
+            if (in_smem)
+                atomicAdd(s_cells + cell, 1);
+            else
+                atomicAdd(P.cell_count + cell, 1);
+        }
     }
     __syncthreads();
-    // exclusive scans of the counts (into cell_start, and into the counts as the
-    // running fill position of each cell) and of the 32-pill chunks per cell
-    // (into the pair search's work list chunk_of)
-    int carry = 0, ccarry = 0;
-    for (int base = 0; base < cells; base += bd * kScanPerB) {
-        const int b0 = base + t * kScanPerB;
-        int v[kScanPerB], sum = 0, csum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanPerB; ++k) {
-            // counts in shared memory, or in global memory written by atomics (read from L2)
-            v[k] = (b0 + k < cells) ? (in_smem ? s_cells[b0 + k] : __ldcg(P.cell_count + b0 + k)) : 0;
-            sum += v[k];
-            csum += (v[k] + 31) >> 5;
-        }
-        int tot, ctot;
-        int off = block_excl_scan(sum, ws, &tot) + carry;
-        int coff = block_excl_scan(csum, ws, &ctot) + ccarry;
-#pragma unroll
-        for (int k = 0; k < kScanPerB; ++k) {
-            if (b0 + k < cells) {
-                P.cell_start[b0 + k] = off;
-                if (in_smem)
-                    s_cells[b0 + k] = off;
-                else
-                    P.cell_count[b0 + k] = off;
-                const int nch = (v[k] + 31) >> 5;
-                for (int h = 0; h < nch; ++h) P.chunk_of[coff + h] = make_int2(b0 + k, h);
-                coff += nch;
-            }
-            off += v[k];
-        }
-        carry += tot;
-        ccarry += ctot;
-    }
-    if (t == 0) {
-        P.cell_start[cells] = carry;
-        *P.n_chunks = ccarry;
-    }
+    grid_scan(P, in_smem ? s_cells : P.cell_count, cells, ws, !in_smem);
     __syncthreads();
-    for (int g = t; g < ns; g += bd) {
-        const int pos = in_smem ? atomicAdd(s_cells + P.cell_of[g], 1) : atomicAdd(P.cell_count + P.cell_of[g], 1);
-        P.cell_pills[pos] = g;
-        P.cell_sph[pos] = P.spheres[g];
-        P.cell_grp[pos] = P.seg_group[g];
+    for (int g0 = 0; g0 < ns; g0 += 8 * bd) {
+        int cq[8], gq[8];
+        float4 sp[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int g = g0 + k * bd + t;
+            const bool ok = g < ns;
+            cq[k] = ok ? P.cell_of[g] : 0;
+            gq[k] = ok ? P.seg_group[g] : 0;
+            sp[k] = ok ? P.spheres[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int g = g0 + k * bd + t;
+            if (g >= ns) continue;
+            const int pos = in_smem ? atomicAdd(s_cells + cq[k], 1) : atomicAdd(P.cell_count + cq[k], 1);
+            P.cell_pills[pos] = g;
+            P.cell_sph[pos] = sp[k];
+            P.cell_grp[pos] = gq[k];
+        }
     }
     if (!in_smem) {  // return cell_count to zero for the next substep
         __syncthreads();

@@ -825,7 +825,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
         }
     }
     rest_tables(s);
-    // warm start (Sec. 7.5): rods pinned at both ends to bones, with the rest
+    // warm start (Sec. 8.2): rods pinned at both ends to bones, with the rest
     // arclength fraction of each vertex
     if (d->flags & VIPER_FLAG_WARM_START) {
         s->u_warm.assign(nv, make_float4(-1.f, -1.f, 0.f, 0.f));

@@ -75,7 +75,7 @@ __device__ __forceinline__ V3 pin_target(const Params &P, int pin, float tau)
     return (qrot(q, xyz(pd)) + tr) - o;
 }
 
-// Warm start from the bones (Sec. 7.5): before a frame's first substep, vertex
+// Warm start from the bones (Sec. 8.2): before a frame's first substep, vertex
 // v of a rod pinned at both ends to bones b0, b1 moves by linear blend skinning
 // with those bones' transforms relative to their previous poses,
 // T_b(p) = R1 R0^T (p - t0) + t1, with weights (1 - t, t), t the vertex's rest

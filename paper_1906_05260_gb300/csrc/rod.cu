@@ -45,7 +45,7 @@ __global__ void warm_kernel(Params P)
         P.X[v] = warm_vertex(P, v, P.X[v]);
 }
 
-// Muscle activation (Sec. 7.5, fibre shortening): the rest tables of internal
+// Muscle activation (Sec. 8.2, fibre shortening): the rest tables of internal
 // vertex v (and of the segment that starts at v) from the FP64 rest data with
 // rod k's rest lengths scaled by (1 - a_k) and rest radii by 1/sqrt(1 - a_k).
 // The formulas are those of the scene's creation (Sec. 4 discretisation,

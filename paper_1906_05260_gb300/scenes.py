@@ -104,7 +104,7 @@ class Scene:
     surface_bending: bool = False     # scale-Laplacian constraints (Sec. 5, E_bending)
     jacobi: bool = False              # rod constraints by Jacobi with averaging (Sec. 7 engine)
     volume_vector: bool = False       # volume constraint in the printed vector form (Sec. 5)
-    warm_start: bool = False          # bone-driven LBS initialisation per frame (Sec. 7.5)
+    warm_start: bool = False          # bone-driven LBS initialisation per frame (Sec. 8.2)
     bundle_offsets: Optional[np.ndarray] = None  # int32 [n_bundles+1] CSR into bundle_rods (Sec. 7.3)
     bundle_rods: Optional[np.ndarray] = None     # int32 rods of each bundle (equal vertex counts)
 
@@ -360,7 +360,7 @@ def muscle_rig(seed: int = 1, n_rods: int = 200, mesh_verts: int = 200_000, n_bo
 
 def bundled_muscles(seed: int = 6, n_muscles: int = 24, fibers: int = 7, n_verts: int = 16, n_bones: int = 8,
                     frames: int = 300) -> Scene:
-    """Muscles made of bundled fibre rods (Sec. 7.3, Sec. 7.5 muscles).
+    """Muscles made of bundled fibre rods (Sec. 7.3, Sec. 8.2 muscles).
 
     Bones as in muscle_rig.  Each muscle spans a random bone gap and holds
     `fibers` rods of `n_verts` vertices in a hexagonal pattern (one central

@@ -134,9 +134,12 @@ def test_muscle_rig_one_frame_with_contacts_and_skinning(V, solver):
     assert np.abs(out - ref_own).max() < POS_TOL_1 * 0.3 * 3  # rods are ~0.22 m; frames move by pos error
 
 
-@pytest.mark.parametrize("solver", [1, 2], ids=["batched", "frame"])
-def test_muscle_rig_pairs_bit_exact(V, solver):
-    sc = S.muscle_rig(mesh_verts=0)
+@pytest.mark.parametrize("solver,n_rods", [(1, 200), (2, 200), (1, 500)], ids=["batched", "frame", "batched-500"])
+def test_muscle_rig_pairs_bit_exact(V, solver, n_rods):
+    """Candidate pairs of the first five frames against the oracle's FP32 predicate
+    on the GPU's predicted state (500 rods, about 18k vertices, take the one-CTA grid
+    build's general path; 200 rods its shared-memory path)."""
+    sc = S.muscle_rig(n_rods=n_rods, mesh_verts=0)
     g = V.Scene(sc, solver=solver)
     total = 0
     for f in range(5):
@@ -448,7 +451,7 @@ def test_bundles_refuse_the_frame_solver(V):
     assert g.sync() == 0
 
 
-# ---------------------------------------------------------------- muscle activation, warm start (Sec. 7.5)
+# ---------------------------------------------------------------- muscle activation, warm start (Sec. 8.2)
 
 def _activation(sc, seed=3):
     """Per-rod activations in [0, 0.6], multiples of 1/64 (exact in FP32)."""

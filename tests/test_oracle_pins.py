@@ -949,7 +949,7 @@ def test_bundle_cross_sections_are_similarities_after_each_step():
 
 
 # --------------------------------------------------------------------------
-# Muscle activation and the bone-driven warm start (Sec. 7.5)
+# Muscle activation and the bone-driven warm start (Sec. 8.2)
 # --------------------------------------------------------------------------
 
 def test_zero_activation_is_the_rest_state():
@@ -1026,7 +1026,7 @@ def test_warm_start_blends_the_two_bone_motions_by_arclength():
 
 
 def test_warm_start_lowers_the_residual_of_fast_bone_motion():
-    """Sec. 7.5: initialising from the bones speeds up convergence in fast
+    """Sec. 8.2: initialising from the bones speeds up convergence in fast
     motion -- after a frame in which the bones jump, the constraint residual is
     smaller with the warm start."""
     res = {}
