@@ -99,12 +99,16 @@ class ClockSampler:
 
 
 def dist_setup():
+    """Process group of a torchrun launch (RANK / WORLD_SIZE / LOCAL_RANK / MASTER_*
+    from the environment): NCCL with GPUs, gloo without.  Ranks are independent
+    replicas; the group carries only the barrier and the timing reductions."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend=backend)
         return dist, rank, ws, local
     return None, 0, 1, 0
@@ -115,22 +119,28 @@ def barrier(dist):
         dist.barrier()
 
 
-def reduce_max(dist, x):
+def _reduce(dist, x, op):
     if dist is None:
         return x
     import torch
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = torch.tensor([float(x)], device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def reduce_max(dist, x):
+    return _reduce(dist, x, dist.ReduceOp.MAX) if dist is not None else x
 
 
 def reduce_sum(dist, x):
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(dist, x, dist.ReduceOp.SUM) if dist is not None else x
+
+
+def whole_job(dist, units, ms):
+    """Whole-job throughput of a weak-scaling step: the units of all ranks over the
+    slowest rank's time per step.  Returns (units per second, max ms per step)."""
+    ms_max = reduce_max(dist, ms)
+    return reduce_sum(dist, units) / (ms_max * 1e-3), ms_max
 
 
 # ---------------------------------------------------------------------------- oracle arm
@@ -160,8 +170,8 @@ def cpu_baseline(scene, budget_s: float = 20.0):
 
 def run_reference(args):
     from paper_1906_05260_gb300 import scenes as S
-    dist, rank, ws, _ = dist_setup()
-    if rank != 0:
+    # the oracle runs on rank 0's host cores alone; the other ranks exit without work
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
     import oracle
     oracle.build()
@@ -579,9 +589,8 @@ def main():
     if rc != 0:
         raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
     mean_ms = sum(ts) / len(ts)
-    mean_ms_max = reduce_max(dist, mean_ms)
+    value, mean_ms_max = whole_job(dist, sc.nv * sc.substeps, mean_ms)
     units = reduce_sum(dist, sc.nv * sc.substeps)
-    value = units / (mean_ms_max * 1e-3)
     p50 = float(np.percentile(ts, 50))
     p99 = float(np.percentile(ts, 99))
 
