@@ -719,7 +719,7 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
     size_t b = 0;
     b += 16 * (7 * nv + 4 * ns);          // X V Xp Xpred RV0 RV1 ... state and rest
     b += 16 * (4 * ns) + 8 * ns;          // Q W Qp RS0, RS1
-    b += 16 * 2 * ns + 48 * ns;           // LQ LC frames
+    b += 16 * 2 * ns + 32 * ns;           // LQ LC frames
     b += 4 * (3 * ns + 3 * nv + 3 * ns) + 16 * nr + 16 * ns;  // index tables, perms, rod origins (per rod, per segment)
     b += 16 * (ns + nv) + 8 * ns + 4 * nv;  // plain multipliers
     b += (16 + 8 + 88) * 3 * nv;          // schedule + slot multipliers (upper bound)
@@ -871,7 +871,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     if (!s->u_warm.empty()) AC(P.warm, float4, nv);
     AC(P.seg_v0, int, ns); AC(P.vtx_seg, int, nv); AC(P.seg_group, int, ns);
     AC(P.rod_of_v, int, nv); AC(P.rod_origin, float4, nr); AC(P.seg_org, float4, ns);
-    A(s->LQ, ns); A(s->LC, ns); A(s->frames, 3 * (size_t)ns);
+    A(s->LQ, ns); A(s->LC, ns); A(s->frames, 2 * (size_t)ns);
     A(s->d_vperm, nv); A(s->d_sperm, ns); A(s->d_sinv, ns);
     A(P.lamS, ns); A(P.lamS2, ns); A(P.lamB, nv); A(P.lamB2, nv); A(P.lamL, nv);
     if (P.vvec) A(P.lamV2, ns);

@@ -1,11 +1,12 @@
 // io.cu -- skinning and state I/O kernels of the VIPER library (sm_103a).
 //
-// Linear blend skinning (Sec. 7.4): one kernel builds, per segment, the 3x4
+// Linear blend skinning (Sec. 7.4): one kernel builds, per segment, the
 // similarity frame T_j Tbar_j^-1 = [s_m R_j Rbar_j^T | c_m - s_m R_j Rbar_j^T cbar_m]
-// (Eq. shapematch frames, rest scale 1) into a small L2-resident table indexed
-// by the caller's segment id; a second kernel gathers four frames per mesh
-// vertex with 128-bit loads of the rest position, frame ids and weights and a
-// 128-bit store of the result.
+// (Eq. shapematch frames, rest scale 1) as 32 bytes (the relative rotation as a
+// quaternion; translation and scale) into a small L2-resident table indexed by
+// the caller's segment id; a second kernel gathers four frames per mesh vertex
+// with 128-bit loads of the rest position, frame ids and weights and a 128-bit
+// store of the result.
 #include "phases.cuh"
 
 namespace viper {

@@ -1187,6 +1187,7 @@ __device__ __forceinline__ void match_cross_section(const Params &P, int c)
 // LBS frame of segment g (Sec. 7.4): the 3x4 similarity T_j Tbar_j^-1 =
 // [s_m R_j Rbar_j^T | c_m - s_m R_j Rbar_j^T cbar_m] in world coordinates,
 // stored as three float4 rows at the caller's segment id sperm[g].
+constexpr int kLbsFrame = 2;  // float4 per skinning frame
 __device__ __forceinline__ void lbs_frame_at(const Params &P, const float4 *__restrict__ LQ,
                                              const float4 *__restrict__ LC, const int *__restrict__ sperm,
                                              float4 *__restrict__ frames, int g)
@@ -1195,22 +1196,19 @@ __device__ __forceinline__ void lbs_frame_at(const Params &P, const float4 *__re
     const float4 xa = P.X[a], xb = P.X[a + 1];
     const float sm = 0.5f * (xa.w + xb.w);
     const float4 q = P.Q[g], qb = LQ[g];
-    const float4 r = qmul(q, qconj(qb));  // R_j Rbar_j^T
-    V3 c0 = qrot(r, v3(1.f, 0.f, 0.f)), c1 = qrot(r, v3(0.f, 1.f, 0.f)), c2 = qrot(r, v3(0.f, 0.f, 1.f));
-    c0 = sm * c0;
-    c1 = sm * c1;
-    c2 = sm * c2;
+    const float4 r = qnormalize(qmul(q, qconj(qb)));  // R_j Rbar_j^T
     const float4 cb = LC[g];
     const V3 cm = 0.5f * (xyz(xa) + xyz(xb)) + xyz(P.rod_origin[P.rod_of_v[a]]);
-    const V3 t = cm - (cb.x * c0 + cb.y * c1 + cb.z * c2);
-    float4 *f = frames + 3 * (size_t)sperm[g];
-    f[0] = make_float4(c0.x, c1.x, c2.x, t.x);
-    f[1] = make_float4(c0.y, c1.y, c2.y, t.y);
-    f[2] = make_float4(c0.z, c1.z, c2.z, t.z);
+    const V3 t = cm - sm * qrot(r, xyz(cb));
+    float4 *f = frames + kLbsFrame * (size_t)sperm[g];
+    f[0] = r;
+    f[1] = make_float4(t.x, t.y, t.z, sm);
 }
 
 // Skinned position of mesh vertex i: sum_k w_k T_k Tbar_k^-1 rest_i over its
-// four frames, from the vertex's rest position, frame ids and weights.
+// four frames, from the vertex's rest position, frame ids and weights.  A
+// frame is 32 bytes: the relative rotation r = R_j Rbar_j^T as a unit
+// quaternion and (t, s_m) with t = c_m - s_m r cbar_m, so T Tbar^-1 p = s_m r p + t.
 // Frame ids outside [0, ns) contribute nothing and raise the error word.
 __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns, const float4 *__restrict__ frames,
                                            int *err)
@@ -1224,11 +1222,12 @@ __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns
             atomicOr(err, ERR_OVERFLOW);
             continue;
         }
-        const float4 *f = frames + 3 * (size_t)ids[k];
-        const float4 r0 = __ldg(f), r1 = __ldg(f + 1), r2 = __ldg(f + 2);
-        ox += wv[k] * (r0.x * p.x + r0.y * p.y + r0.z * p.z + r0.w);
-        oy += wv[k] * (r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w);
-        oz += wv[k] * (r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
+        const float4 *f = frames + kLbsFrame * (size_t)ids[k];
+        const float4 r = __ldg(f), ts = __ldg(f + 1);
+        const V3 y = qrot(r, v3(p.x, p.y, p.z));
+        ox += wv[k] * (ts.w * y.x + ts.x);
+        oy += wv[k] * (ts.w * y.y + ts.y);
+        oz += wv[k] * (ts.w * y.z + ts.z);
     }
     return make_float4(ox, oy, oz, 0.f);
 }

@@ -131,7 +131,7 @@ struct viper_scene {
     viper::Params P{};
     int *d_vperm = nullptr, *d_sperm = nullptr, *d_sinv = nullptr;
     float4 *LQ = nullptr, *LC = nullptr;  // LBS rest quaternion / rest midpoint per internal segment
-    float4 *frames = nullptr;             // LBS frames, 3 float4 per caller segment
+    float4 *frames = nullptr;             // LBS frames, 2 float4 per caller segment (rotation, translation + scale)
     float4 *stage4 = nullptr;             // staging for get/set state (max(nv, ns) float4)
     float *stage1 = nullptr;
     // plain path: segments (colours 0, 1), interior vertices (2, 3), surface bending (4, 5, 6)
