@@ -443,6 +443,41 @@ def time_scene(V, torch, flush, dist, sc, frames, per_frame=None, solver=None):
     return out
 
 
+def bench_lbs(V, torch, flush, dist, frames, peaks, peak_kind, rank=0):
+    """Skinning alone on a large mesh (the HBM-streaming stage): 8M mesh vertices
+    bound to the headline rig's 7,110-segment frames; algorithmic bytes 64 per
+    vertex (rest position, frame ids, weights in; skinned position out)."""
+    from paper_1906_05260_gb300 import scenes as S
+    sc = S.muscle_rig(seed=1 + rank, mesh_verts=8_000_000)
+    g = V.Scene(sc)
+    mesh = V.Mesh(sc.mesh)
+    st = g.stream
+    g.frame()
+    g.skin(mesh)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(frames):
+        with torch.cuda.stream(st):
+            flush.fill_(i & 0xFF)
+            e0.record(st)
+            g.skin(mesh)
+            e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = reduce_max(dist, float(np.median(ts)))
+    n = sc.mesh.n
+    gbs = n * 64.0 / (ms * 1e-3) / 1e9
+    g.close()
+    return {"workload": f"LBS of {n} mesh vertices (4 frames each, random order) on the muscle_rig's "
+                        f"{sc.ns} segment frames; frames rebuilt and gathered every call",
+            "ms_per_call": ms, "skinned_vertices_per_s": reduce_sum(dist, n) / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                         "bytes_per_vertex": 64}}
+
+
 def bench_muscles(V, torch, flush, dist, frames, rank=0):
     """Muscle features on the headline rig and on bundled muscles (Sec. 7.3, 8.2):
     per-frame time with a time-varying activation (rest tables recomputed on the
@@ -513,6 +548,7 @@ def main():
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-muscles", action="store_true")
+    ap.add_argument("--no-lbs", action="store_true")
     ap.add_argument("--serving", type=float, default=10.0,
                     help="seconds of the real-time serving load (0 disables)")
     args = ap.parse_args()
@@ -696,7 +732,11 @@ def main():
                     "pairs": pairs}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dominant
-    roof["traffic"] = None
+    # DRAM bytes per launch of the dominant class from one ncu capture of this workload
+    # (profiles/batch_kernels_muscle_rig.md: first sweep 1.03 MB, later sweeps 1.10 MB,
+    # one and three per substep); other classes or solvers: not captured
+    roof["traffic"] = (1.028e6 + 3 * 1.098e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
+    roof["traffic_unit"] = "bytes per launch (dram read + write, ncu)"
     roof["per_class"] = per_class
 
     # ---- the other solvers on the same scene: graph-replayed launches and plain per-colour launches
@@ -729,6 +769,11 @@ def main():
     if not args.no_batching:
         batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
         convergence = bench_convergence(V, np)
+
+    # ---- skinning alone on a large mesh: the HBM-streaming stage's roofline
+    lbs = None
+    if not args.no_lbs:
+        lbs = bench_lbs(V, torch, flush, dist, max(10, K // 2), peaks, peak_kind, rank=rank)
 
     # ---- muscle features: activation + warm start, bundled muscles
     muscles = None
@@ -786,6 +831,7 @@ def main():
         "convergence": convergence,
         "multi_scene": multi,
         "muscles": muscles,
+        "lbs": lbs,
         "serving": serving,
     }
     if rank == 0:
