@@ -78,6 +78,11 @@ __device__ __forceinline__ void rotate_by(float4 &q, V3 d)
 // Vertex inverse mass: RV1.x when >= 0, else the vertex is pinned (mass infinite).
 __device__ __forceinline__ float inv_mass(float4 rv1) { return fmaxf(rv1.x, 0.f); }
 
+// Division in the constraint projections: x * approx(1/y) (at most 2 ulp; the
+// denominators here are positive sums of inverse masses, inertias and
+// compliance terms or scaled determinants, far inside the normal range).
+__device__ __forceinline__ float fdiv(float x, float y) { return __fdividef(x, y); }
+
 // ---------------------------------------------------------------- segment constraints
 // Segment j between vertices a, b, frame q; per-constraint multipliers in lam
 // (S.xyz, V) and lam2 (X, G).  project_segment: order S, V, X, G, each evaluated
@@ -108,13 +113,13 @@ __device__ __forceinline__ void seg_stretch(const float4 &xa, const float4 &xb, 
     V3 d3 = qd3(q);
     V3 C = (xyz(xb) - xyz(xa)) * inv_l - d3;
     float sm = 0.5f * (xa.w + xb.w);
-    float a = 4.f * rs0.y / (sm * sm);
+    float a = fdiv(4.f * rs0.y, sm * sm);
     float wp = (wa + wb) * inv_l * inv_l;
     float at = rs0.z * inv_h2;
     V3 lm = {lam.x, lam.y, lam.z};
     V3 rhs = -C - at * lm;
     float dn = dot(rhs, d3);
-    V3 dl = (rhs - dn * d3) * (1.f / (wp + a + at)) + d3 * (dn / (wp + at));
+    V3 dl = (rhs - dn * d3) * fdiv(1.f, wp + a + at) + d3 * fdiv(dn, wp + at);
     lam.x += dl.x;
     lam.y += dl.y;
     lam.z += dl.z;
@@ -137,10 +142,10 @@ __device__ __forceinline__ void seg_volume(const float4 &xa, const float4 &xb, c
     float jx = sm * sm * inv_l;  // J_xb = jx d3, J_xa = -jx d3
     float js = sm * e * inv_l;   // J_sa = J_sb
     V3 jt = (sm * sm * inv_l) * cross(d3, dx);  // J_theta (orthogonal to d3)
-    float a = 4.f * rs0.y / (sm * sm);
+    float a = fdiv(4.f * rs0.y, sm * sm);
     float at = rs0.w * inv_h2;
     float den = (wa + wb) * jx * jx + (wsa + wsb) * js * js + a * dot(jt, jt) + at;
-    float dl = (-C - at * lam.w) / den;
+    float dl = fdiv(-C - at * lam.w, den);
     lam.w += dl;
     d.dxa = (-wa * jx * dl) * d3;
     d.dxb = (wb * jx * dl) * d3;
@@ -165,16 +170,16 @@ __device__ __forceinline__ void seg_volume_vec(const float4 &xa, const float4 &x
     float jx = sm * sm * inv_l;
     V3 C = jx * dx - d3;
     V3 u = (sm * inv_l) * dx;
-    float a = 4.f * rs0.y / (sm * sm);
+    float a = fdiv(4.f * rs0.y, sm * sm);
     float at = rs0.w * inv_h2;
     float ws = wsa + wsb;
     float wp = (wa + wb) * jx * jx;
     V3 rhs = -C - at * v3(lw, lv.x, lv.y);
-    const float i_perp = 1.f / (wp + at + a), i_par = 1.f / (wp + at);
+    const float i_perp = fdiv(1.f, wp + at + a), i_par = fdiv(1.f, wp + at);
     float rn = dot(rhs, d3), un = dot(u, d3);
     V3 Dr = (rhs - rn * d3) * i_perp + d3 * (rn * i_par);
     V3 Du = (u - un * d3) * i_perp + d3 * (un * i_par);
-    V3 dl = Dr - Du * (ws * dot(u, Dr) / (1.f + ws * dot(u, Du)));
+    V3 dl = Dr - Du * fdiv(ws * dot(u, Dr), 1.f + ws * dot(u, Du));
     lw += dl.x;
     lv.x += dl.y;
     lv.y += dl.z;
@@ -192,7 +197,7 @@ __device__ __forceinline__ void seg_xsection(float sa, float sb, float wsa, floa
 {
     float C = 0.5f * (sa + sb) - 1.f;
     float at = rs1.x * inv_h2;
-    float dl = (-C - at * lam2.x) / (0.25f * (wsa + wsb) + at);
+    float dl = fdiv(-C - at * lam2.x, 0.25f * (wsa + wsb) + at);
     lam2.x += dl;
     dsa = 0.5f * wsa * dl;
     dsb = 0.5f * wsb * dl;
@@ -204,7 +209,7 @@ __device__ __forceinline__ void seg_gradient(float sa, float sb, float wsa, floa
 {
     float C = (sb - sa) * inv_l;
     float at = rs1.y * inv_h2;
-    float dl = (-C - at * lam2.y) / ((wsa + wsb) * inv_l * inv_l + at);
+    float dl = fdiv(-C - at * lam2.y, (wsa + wsb) * inv_l * inv_l + at);
     lam2.y += dl;
     dsa = -wsa * inv_l * dl;
     dsb = wsb * inv_l * dl;
@@ -217,7 +222,7 @@ __device__ __forceinline__ void project_segment(float4 &xa, float4 &xb, float4 &
                                                 float4 &lam, float2 &lam2, float inv_h2, bool volume,
                                                 float2 *lamv = nullptr)
 {
-    const float inv_l = 1.f / rs0.x;
+    const float inv_l = fdiv(1.f, rs0.x);
     SegDelta d;
     seg_stretch(xa, xb, q, wa, wb, rs0, inv_l, lam, inv_h2, d);
     add_to(xa, d.dxa);
@@ -248,7 +253,7 @@ __device__ __forceinline__ void jacobi_segment(const float4 &xa, const float4 &x
                                                float wb, float wsa, float wsb, float4 rs0, float2 rs1, float4 &lam,
                                                float2 &lam2, float inv_h2, bool volume, SegDelta &sum)
 {
-    const float inv_l = 1.f / rs0.x;
+    const float inv_l = fdiv(1.f, rs0.x);
     seg_stretch(xa, xb, q, wa, wb, rs0, inv_l, lam, inv_h2, sum);
     if (volume) {
         SegDelta d;
@@ -293,8 +298,8 @@ __device__ __forceinline__ void rel_frame(RelFrame &f, float4 qa, float4 qb, flo
     f.p = p;
     f.om = kappa * v3(p.x, p.y, p.z);
     f.h2 = 0.5f * kappa;
-    f.da = 4.f * imr2a / (sma * sma);
-    f.db = 4.f * imr2b / (smb * smb);
+    f.da = fdiv(4.f * imr2a, sma * sma);
+    f.db = fdiv(4.f * imr2b, smb * smb);
     f.e = qd3(p);
     V3 pv = {p.x, p.y, p.z};
     // M ez and M e, with M v = p_w v - p_v x v
@@ -337,7 +342,7 @@ __device__ __forceinline__ void apply_rel(const RelFrame &f, float4 &qa, float4 
 // (~A^3) would overflow.
 __device__ __forceinline__ V3 solve_sym3(const float *A_, V3 b)
 {
-    const float sc = 1.f / fmaxf(fmaxf(fabsf(A_[0]), fabsf(A_[1])), fmaxf(fabsf(A_[2]), 1e-30f));
+    const float sc = fdiv(1.f, fmaxf(fmaxf(fabsf(A_[0]), fabsf(A_[1])), fmaxf(fabsf(A_[2]), 1e-30f)));
     float A[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) A[k] = A_[k] * sc;
@@ -349,7 +354,7 @@ __device__ __forceinline__ V3 solve_sym3(const float *A_, V3 b)
     float c12 = A[3] * A[4] - A[0] * A[5];
     float c22 = A[0] * A[1] - A[3] * A[3];
     float det = A[0] * c00 + A[3] * c01 + A[4] * c02;
-    float id = 1.f / det;
+    float id = fdiv(1.f, det);
     return {(c00 * b.x + c01 * b.y + c02 * b.z) * id, (c01 * b.x + c11 * b.y + c12 * b.z) * id,
             (c02 * b.x + c12 * b.y + c22 * b.z) * id};
 }
@@ -402,9 +407,9 @@ __device__ __forceinline__ void vtx_volbend(const float4 &qa, const float4 &qb, 
     float a11 = k * f.N[1] + ws * js_v * js_v + at;
     float a01 = k * f.N[3] + ws * js_u * js_v;
     float r0 = -cu - at * lam.w, r1 = -cv - at * lam_v;
-    const float sc = 1.f / fmaxf(fmaxf(fabsf(a00), fabsf(a11)), 1e-30f);  // keep the determinant in range
+    const float sc = fdiv(1.f, fmaxf(fmaxf(fabsf(a00), fabsf(a11)), 1e-30f));  // keep the determinant in range
     a00 *= sc; a11 *= sc; a01 *= sc; r0 *= sc; r1 *= sc;
-    float id = 1.f / (a00 * a11 - a01 * a01);
+    float id = fdiv(1.f, a00 * a11 - a01 * a01);
     float d0 = (a11 * r0 - a01 * r1) * id, d1 = (a00 * r1 - a01 * r0) * id;
     lam.w += d0;
     lam_v += d1;
@@ -417,7 +422,7 @@ __device__ __forceinline__ void project_vertex(float4 &qa, float4 &qb, float &s,
                                                float4 rv0, float aB, float aVb, float4 &lam, float &lam_v,
                                                float inv_h2, bool volume)
 {
-    const float kappa = 4.f / (la + lb);
+    const float kappa = fdiv(4.f, la + lb);
     VtxDelta d;
     vtx_bend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aB, lam, inv_h2, d);
     rotate_by(qa, d.dtha);
@@ -436,7 +441,7 @@ __device__ __forceinline__ void jacobi_vertex(const float4 &qa, const float4 &qb
                                               float aB, float aVb, float4 &lam, float &lam_v, float inv_h2,
                                               bool volume, VtxDelta &sum)
 {
-    const float kappa = 4.f / (la + lb);
+    const float kappa = fdiv(4.f, la + lb);
     vtx_bend(qa, qb, s, s_prev, s_next, kappa, imr2a, imr2b, ws, rv0, aB, lam, inv_h2, sum);
     if (volume) {
         VtxDelta d;
@@ -460,7 +465,7 @@ __device__ __forceinline__ void laplacian_increments(float sp, float s, float sn
     const float jp = rv2.x, jn = rv2.y, jc = -(jp + jn);
     const float C = jn * (sn - s) - jp * (s - sp);
     const float at = rv2.z * inv_h2;
-    const float dl = (-C - at * lam) / (wp * jp * jp + w * jc * jc + wn * jn * jn + at);
+    const float dl = fdiv(-C - at * lam, wp * jp * jp + w * jc * jc + wn * jn * jn + at);
     lam += dl;
     dsp = wp * jp * dl;
     ds = w * jc * dl;
