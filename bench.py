@@ -733,9 +733,9 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dominant
     # DRAM bytes per launch of the dominant class from one ncu capture of this workload
-    # (profiles/batch_kernels_muscle_rig.md: first sweep 1.03 MB, later sweeps 1.10 MB,
+    # (profiles/batch_kernels_muscle_rig.md: first sweep 1.02 MB, later sweeps 1.09 MB,
     # one and three per substep); other classes or solvers: not captured
-    roof["traffic"] = (1.028e6 + 3 * 1.098e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
+    roof["traffic"] = (1.016e6 + 3 * 1.089e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
     roof["traffic_unit"] = "bytes per launch (dram read + write, ncu)"
     roof["per_class"] = per_class
 
