@@ -198,7 +198,8 @@ int viper_set_activation(viper_scene *scene, const float *activation);
  * Tbar_k^-1 rest with segment similarity frames T = [s_m R, c_m] (Eq.
  * shapematch).  rest4 [4n] (x, y, z, unused), idx4 [4n] caller segment ids,
  * w4 [4n], out4 [4n] (x, y, z, 0); all host or device.  Host output makes the
- * call synchronous.
+ * call synchronous.  Device arrays must be 16-byte aligned (they are read and
+ * written as float4 / int4): VIPER_EINVAL otherwise.
  */
 int viper_skin(viper_scene *scene, int n, const float *rest4, const int *idx4, const float *w4,
                float *out4);
@@ -345,6 +346,7 @@ typedef struct viper_batch_item {
     const int *idx4;          /* device [4 n_mesh]                                                */
     const float *w4;          /* device [4 n_mesh]                                                */
     float *out4;              /* device [4 n_mesh]                                                */
+    /* the four mesh arrays 16-byte aligned (VIPER_EINVAL otherwise)                                */
 } viper_batch_item;
 
 /*

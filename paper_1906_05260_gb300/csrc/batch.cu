@@ -957,6 +957,9 @@ int viper_batch_step(viper_batch *B, const viper_batch_item *items, int n, float
         const viper_batch_item &it = items[i];
         if (!it.scene || (!it.bone_quat) != (!it.bone_trans) || it.n_mesh < 0) return VIPER_EINVAL;
         if (it.n_mesh > 0 && (!it.rest4 || !it.idx4 || !it.w4 || !it.out4)) return VIPER_EINVAL;
+        if (it.n_mesh > 0 && ((reinterpret_cast<uintptr_t>(it.rest4) | reinterpret_cast<uintptr_t>(it.idx4) |
+                               reinterpret_cast<uintptr_t>(it.w4) | reinterpret_cast<uintptr_t>(it.out4)) & 15u))
+            return VIPER_EINVAL;  // float4 / int4 arrays
         seen[i] = it.scene;
     }
     std::sort(seen.begin(), seen.end());

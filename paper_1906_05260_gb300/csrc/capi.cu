@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <numeric>
 #include <vector>
 
@@ -1174,6 +1175,10 @@ int viper_skin(viper_scene *s, int n, const float *rest4, const int *idx4, const
     if (n == 0) return VIPER_OK;
     s->prof_used_skin = 0;
     const bool dr = is_device_ptr(rest4), di = is_device_ptr(idx4), dw = is_device_ptr(w4), dout = is_device_ptr(out4);
+    // device operands are read and written as float4 / int4: 16-byte alignment
+    auto misaligned = [](bool dev, const void *p) { return dev && (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+    if (misaligned(dr, rest4) || misaligned(di, idx4) || misaligned(dw, w4) || misaligned(dout, out4))
+        return VIPER_EINVAL;
     if (dr && di && dw && dout) {
         s->prof_in_skin = true;
         launch_lbs(s, n, (const float4 *)rest4, (const int4 *)idx4, (const float4 *)w4, (float4 *)out4);

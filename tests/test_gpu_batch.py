@@ -201,3 +201,30 @@ def test_batch_large_scene_and_zero_iterations(V):
             scale = np.abs(sa["x4"][:, :3]).max() + 1e-3
             assert np.abs(sa["x4"] - sb["x4"]).max() < 4e-6 * scale
             assert np.abs(sa["q4"] - sb["q4"]).max() < 1e-4
+
+
+def test_misaligned_mesh_arrays_are_rejected(V):
+    """The skinning arrays are read and written as float4 / int4: device pointers
+    that are not 16-byte aligned are refused (no misaligned access on the GPU)."""
+    import ctypes as C
+    import torch
+    sc = S.muscle_rig(seed=1, n_rods=20, mesh_verts=100)
+    g = V.Scene(sc)
+    mesh = V.Mesh(sc.mesh)
+    L = V.lib()
+    bad = torch.empty(4 * mesh.n + 1, dtype=torch.float32, device="cuda")
+    bad_ptr = C.c_void_p(bad.data_ptr() + 4)  # 4-byte offset
+    assert L.viper_skin(g.handle, mesh.n, bad_ptr, C.c_void_p(mesh.idx.data_ptr()), C.c_void_p(mesh.w.data_ptr()),
+                        C.c_void_p(mesh.out.data_ptr())) == V.EINVAL
+    items = (V.BatchItem * 1)()
+    items[0].scene = g.handle.value
+    items[0].n_mesh = mesh.n
+    items[0].rest4 = bad_ptr.value
+    items[0].idx4 = mesh.idx.data_ptr()
+    items[0].w4 = mesh.w.data_ptr()
+    items[0].out4 = mesh.out.data_ptr()
+    B = V.Batch()
+    assert L.viper_batch_step(B._h, items, 1, DT, SUB, IT, None) == V.EINVAL
+    # aligned arrays still skin
+    g.skin(mesh)
+    assert g.sync() == 0
