@@ -179,10 +179,12 @@ __global__ void __launch_bounds__(kElemThreads) batch_scatter_kernel(BatchArgs A
     }
 }
 
-// Candidate pairs, one warp per work unit: a 32-pill chunk against one
-// neighbour list when the grid came from batch_grid_kernel (see emit_chunk),
-// else a cell against one neighbour cell (see emit_cell).
-__global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs A, int chunked)
+// Candidate pairs, one warp per work unit.  With a grid from batch_grid_kernel:
+// mode 1, a 32-pill chunk against one neighbour list (see emit_chunk), for groups
+// of few pills; mode 2, a chunk against all its neighbour lists (see
+// emit_chunk_all), for many.  Mode 0 (grid from the multi-kernel build): a cell
+// against one neighbour cell (see emit_cell).
+__global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs A, int mode)
 {
     __shared__ BatchScene sb;
     int local, nblk;
@@ -194,9 +196,16 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     const int cells = grid_cells(P.grid, P.table);
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
-    if (chunked) {
+    __shared__ float4 s_cand[kEmitWarpsB][32];  // per warp: the neighbour block being tested
+    __shared__ int s_cgrp[kEmitWarpsB][32];
+    if (mode == 2) {  // a chunk with all its neighbour lists per warp
+        const int n = *P.n_chunks;
+        for (int q = local * kEmitWarpsB + wib; q < n; q += nblk * kEmitWarpsB)
+            emit_chunk_all<4>(P, G, q, start, s_cand[wib], s_cgrp[wib]);
+    } else if (mode == 1) {  // a chunk with one neighbour list per warp
         const int n = kEmitUnits * *P.n_chunks;
-        for (int u = local * kEmitWarpsB + wib; u < n; u += nblk * kEmitWarpsB) emit_chunk<4>(P, G, u, start);
+        for (int u = local * kEmitWarpsB + wib; u < n; u += nblk * kEmitWarpsB)
+            emit_chunk<4>(P, G, u, start, s_cand[wib], s_cgrp[wib]);
     } else {
         for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
             emit_cell<4>(P, G, u, start);
@@ -602,11 +611,12 @@ void launch(void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Pills per pair-search warp: a scene has about 0.44 ns + 14 (occupied cells)
-// work units.  Groups of few pills get one warp per couple of units, so that
-// the units' dependent loads run side by side on more warps; large groups fill
-// the GPU with a few units per warp.
-constexpr int kEmitPillsPerWarp = 4, kEmitPillsPerWarpSmall = 1, kEmitSmallGroup = 16384;
+// Pair search shape: a scene has about ns / 32 + (occupied cells) chunks of 14
+// units.  Groups of few pills run one unit per warp (mode 1, a warp per pill,
+// so the units' dependent loads run side by side); large groups run one chunk
+// per warp (mode 2, a warp per 8 pills), which cuts the number of dependent
+// load chains by about 14.
+constexpr int kEmitPillsPerWarp = 8, kEmitPillsPerWarpSmall = 1, kEmitSmallGroup = 16384;
 constexpr int kMeshPerThread = 16;  // kLbsBatch vertices per round, 4 rounds
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -665,6 +675,7 @@ int stage_reserve(viper_batch::Stage &S, size_t bytes)
 // Launch shape of one sequence: blocks per kernel kind over all its scenes.
 struct Shape {
     int tot[K_KINDS] = {};
+    int emit_mode = 1;  // pair search with the one-CTA grid: 1 unit / 2 chunk per warp
     int threads = 0, smem = 16;
     bool cp = false, fused_grid = true;
 };
@@ -748,7 +759,7 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
             go(PROF_BROADPHASE, [&] { launch(batch_scatter_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
         }
         go(PROF_PAIRS, [&] {
-            launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A, fused_grid ? 1 : 0);
+            launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A, fused_grid ? sh.emit_mode : 0);
         });
     };
     auto contact = [&]() {
@@ -817,7 +828,9 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     long long group_pills = 0;
     for (int i : idx)
         if (items[i].scene->flags & VIPER_FLAG_CONTACTS) group_pills += items[i].scene->ns;
-    const int emit_ppw = group_pills <= kEmitSmallGroup ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
+    const bool small_group = group_pills <= kEmitSmallGroup;
+    const int emit_ppw = small_group ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
+    sh.emit_mode = small_group ? 1 : 2;
     for (int c = 0; c < K_KINDS; ++c) off[c * (n + 1)] = 0;
     for (int k = 0; k < n; ++k) {
         const viper_batch_item &it = items[idx[k]];
@@ -873,10 +886,12 @@ int self_batch_capture(viper_scene *s, float dt, int substeps, int iterations, c
     it.scene = s;
     const bool cp = scene_contact_path(s);
     int cnt[K_KINDS];
-    const int emit_ppw = s->ns <= kEmitSmallGroup ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
+    const bool small_group = s->ns <= kEmitSmallGroup;
+    const int emit_ppw = small_group ? kEmitPillsPerWarpSmall : kEmitPillsPerWarp;
     fill_scene(*b, cnt, s, it, (double)dt / substeps, cp, emit_ppw);  // bones: the scene's own target pose
     Shape sh;
     shape_add(sh, s, cp);
+    sh.emit_mode = small_group ? 1 : 2;
     for (int c = 0; c < K_KINDS; ++c) {
         off[2 * c] = 0;
         off[2 * c + 1] = cnt[c];

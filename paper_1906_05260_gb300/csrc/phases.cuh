@@ -927,69 +927,36 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
     }
 }
 
-// Candidate pairs of one chunk of up to 32 pills of a cell (chunk_of[q] =
-// (cell, chunk)) with one neighbour list, by one warp: work unit u = 14 q + k
-// pairs the chunk with the cell's forward neighbour k < 13, or with the rest of
-// its own cell from the chunk on (k = 13).  Every pair of pills of neighbouring
-// cells is visited once (as in emit_cell), and no unit is larger than one
-// chunk against one neighbour cell, so the units are balanced across warps.
-// The chunk's pills sit one per lane; the neighbour's are loaded 32 at a time
-// and broadcast, STEP candidates per step.
-template <int STEP, class StartFn>
-__device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u, StartFn start)
+// The chunk's pills (lane: entry pa of the cell order, sphere sa, group ga,
+// `own` when the lane holds a pill) against the neighbour list [d0, d1) by one
+// warp: the neighbour's pills are loaded 32 at a time from the cell-order
+// sphere / group copies (coalesced) into the warp's shared buffers (32 float4
+// + 32 int) and read back as broadcasts, STEP candidates per step; only pairs
+// with the neighbour entry above pa count (so the own cell's list, starting at
+// the chunk, yields each pair once).  Hits are compacted with a ballot and
+// their output slots reserved with one atomic per step.
+template <int STEP>
+__device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, float4 sa, int ga, int d0, int d1,
+                                           float4 *cbuf, int *gbuf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const int k = u % kEmitUnits;
-    const int2 ch = P.chunk_of[u / kEmitUnits];
-    const int c = ch.x;
-    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
-    const int o1 = min(o0 + 32, cend);
-    int d0, d1;
-    if (k == 13) {  // the own cell from this chunk on: pairs with pb > pa
-        d0 = o0;
-        d1 = cend;
-    } else {
-        int dx, dy, dz;
-        if (k < 9) {
-            dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
-        } else if (k < 12) {
-            dx = k - 10; dy = 1; dz = 0;
-        } else {
-            dx = 1; dy = 0; dz = 0;
-        }
-        const int ix = c % G.dim[0], iy = (c / G.dim[0]) % G.dim[1], iz = c / (G.dim[0] * G.dim[1]);
-        const int x = ix + dx, y = iy + dy, z = iz + dz;
-        if (x < 0 || x >= G.dim[0] || y < 0 || y >= G.dim[1] || z >= G.dim[2]) return;
-        const int d = x + G.dim[0] * (y + G.dim[1] * z);
-        d0 = start(d);
-        d1 = start(d + 1);
-    }
-    if (d0 >= d1) return;  // uniform over the warp
-    const int pa = o0 + lane;
-    const bool own = pa < o1;
-    const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int ga = own ? P.cell_grp[pa] : 0;
     for (int cb = d0; cb < d1; cb += 32) {
         const int q = cb + lane;
-        float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cg = 0;
+        __syncwarp();  // the previous block's reads are done
         if (q < d1) {
-            cs = P.cell_sph[q];
-            cg = P.cell_grp[q];
+            cbuf[lane] = P.cell_sph[q];
+            gbuf[lane] = P.cell_grp[q];
         }
+        __syncwarp();
         const int m = min(32, d1 - cb);
         for (int j0 = 0; j0 < m; j0 += STEP) {
             bool hit[STEP];
 #pragma unroll
             for (int t = 0; t < STEP; ++t) {
-                const int j = j0 + t;  // past m: no candidate (j & 31 is still a valid source lane)
-                float4 sj;
-                sj.x = __shfl_sync(full, cs.x, j & 31);
-                sj.y = __shfl_sync(full, cs.y, j & 31);
-                sj.z = __shfl_sync(full, cs.z, j & 31);
-                sj.w = __shfl_sync(full, cs.w, j & 31);
-                const int gj = __shfl_sync(full, cg, j & 31);
+                const int j = j0 + t;  // past m: no candidate (j & 31 is still a valid entry)
+                const float4 sj = cbuf[j & 31];
+                const int gj = gbuf[j & 31];
                 hit[t] = j < m && own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
             }
 #pragma unroll
@@ -1010,6 +977,95 @@ __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u
                 }
             }
         }
+    }
+}
+
+// Forward neighbour k < 13 of cell c (dz = 1: 9 cells; dz = 0, dy = 1: 3; dz = dy = 0, dx = 1),
+// or -1 outside the grid.
+__device__ __forceinline__ int forward_neighbour(const Grid &G, int c, int k)
+{
+    int dx, dy, dz;
+    if (k < 9) {
+        dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
+    } else if (k < 12) {
+        dx = k - 10; dy = 1; dz = 0;
+    } else {
+        dx = 1; dy = 0; dz = 0;
+    }
+    const int ix = c % G.dim[0], iy = (c / G.dim[0]) % G.dim[1], iz = c / (G.dim[0] * G.dim[1]);
+    const int x = ix + dx, y = iy + dy, z = iz + dz;
+    if (x < 0 || x >= G.dim[0] || y < 0 || y >= G.dim[1] || z >= G.dim[2]) return -1;
+    return x + G.dim[0] * (y + G.dim[1] * z);
+}
+
+// Candidate pairs of one chunk of up to 32 pills of a cell (chunk_of[q] =
+// (cell, chunk)) with one neighbour list, by one warp: work unit u = 14 q + k
+// pairs the chunk with the cell's forward neighbour k < 13, or with the rest of
+// its own cell from the chunk on (k = 13).  Every pair of pills of neighbouring
+// cells is visited once (as in emit_cell), and no unit is larger than one
+// chunk against one neighbour cell, so the units are balanced across warps.
+template <int STEP, class StartFn>
+__device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u, StartFn start, float4 *cbuf,
+                                           int *gbuf)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = u % kEmitUnits;
+    const int2 ch = P.chunk_of[u / kEmitUnits];
+    const int c = ch.x;
+    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
+    const int o1 = min(o0 + 32, cend);
+    int d0, d1;
+    if (k == 13) {  // the own cell from this chunk on: pairs with pb > pa
+        d0 = o0;
+        d1 = cend;
+    } else {
+        const int d = forward_neighbour(G, c, k);
+        if (d < 0) return;
+        d0 = start(d);
+        d1 = start(d + 1);
+    }
+    if (d0 >= d1) return;  // uniform over the warp
+    const int pa = o0 + lane;
+    const bool own = pa < o1;
+    const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ga = own ? P.cell_grp[pa] : 0;
+    emit_block<STEP>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
+}
+
+// All 14 neighbour lists of chunk q by one warp (the same pairs as the 14 units
+// of emit_chunk): lanes 0..13 look up the lists' ranges at once, then the warp
+// walks the non-empty ones.  Fewer, longer units: for many scenes at once, where
+// each unit's chain of dependent loads, not its tests, sets the time.
+template <int STEP, class StartFn>
+__device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, int q, StartFn start, float4 *cbuf,
+                                               int *gbuf)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int2 ch = P.chunk_of[q];
+    const int c = ch.x;
+    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
+    const int o1 = min(o0 + 32, cend);
+    int d0 = 0, d1 = 0;
+    if (lane == 13) {  // the own cell from this chunk on
+        d0 = o0;
+        d1 = cend;
+    } else if (lane < 13) {
+        const int d = forward_neighbour(G, c, lane);
+        if (d >= 0) {
+            d0 = start(d);
+            d1 = start(d + 1);
+        }
+    }
+    const int pa = o0 + lane;
+    const bool own = pa < o1;
+    const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ga = own ? P.cell_grp[pa] : 0;
+    unsigned lists = __ballot_sync(full, lane < 14 && d1 > d0);
+    while (lists) {
+        const int k = __ffs(lists) - 1;
+        lists &= lists - 1;
+        emit_block<STEP>(P, pa, own, sa, ga, __shfl_sync(full, d0, k), __shfl_sync(full, d1, k), cbuf, gbuf);
     }
 }
 

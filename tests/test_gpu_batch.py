@@ -228,3 +228,21 @@ def test_misaligned_mesh_arrays_are_rejected(V):
     # aligned arrays still skin
     g.skin(mesh)
     assert g.sync() == 0
+
+
+def test_batch_pairs_bit_exact_in_a_large_group(V):
+    """Four 200-rod muscle rigs in one multi-scene step (about 28k pills: the pair
+    search runs a chunk with all its neighbour lists per warp): every scene's
+    candidate pairs equal the oracle's FP32 predicate on its predicted state."""
+    scenes = [S.muscle_rig(seed=11 + k, n_rods=200, mesh_verts=0) for k in range(4)]
+    assert sum(sc.ns for sc in scenes) > 16384
+    objs = [V.Scene(sc) for sc in scenes]
+    B = V.Batch()
+    for f in range(2):
+        B.step(objs, [sc.bone_pose((f + 1) * DT) for sc in scenes], None, DT, SUB, IT)
+        B.synchronize()
+        for o, sc in zip(objs, scenes):
+            x4, rb = o.predicted()
+            ref = oracle.broadphase_f32(sc.rod_offsets, sc.group, x4, rb)
+            np.testing.assert_array_equal(o.pairs(), ref)
+    assert all(o.sync() == 0 for o in objs)
