@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256) batch_rod_first_kernel(BatchArgs A, int f
 // One colour sweep of every work item (contact path): FULL = false, or the
 // whole substep with all iterations (no contacts): FULL = true.
 template <bool FULL>
-__global__ void __launch_bounds__(256) batch_rod_kernel(BatchArgs A, int n_iter, int first, int apply, float tau)
+__global__ void __launch_bounds__(256, 2) batch_rod_kernel(BatchArgs A, int n_iter, int first, int apply, float tau)
 {
     __shared__ BatchScene sb;
     extern __shared__ float4 smem[];

@@ -127,8 +127,11 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
     __shared__ int s_toff[kMaxTiles + 1];
     const bool owner = blockIdx.x < P.n_items;
     const int4 item = owner ? P.items[blockIdx.x] : make_int4(0, 0, 0, 0);
-    float4 *sX = smem, *sV = sX + item.y, *sXp = sV + item.y;
-    float4 *sQ = sXp + item.y, *sW = sQ + item.w, *sQp = sW + item.w;
+    const SmemRod sX = smem_rod(smem, item.y), sV = smem_rod(smem + item.y, item.y);
+    const SmemRod sXp = smem_rod(smem + 2 * item.y, item.y);
+    const SmemRod sQ = smem_rod(smem + 3 * item.y, item.w), sW = smem_rod(smem + 3 * item.y + item.w, item.w);
+    const SmemRod sQp = smem_rod(smem + 3 * item.y + 2 * item.w, item.w);
+    float4 *const rec = smem + 3 * (item.y + item.w);  // Jacobi records behind the state
     const unsigned int nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
     const int wib = threadIdx.x >> 5, gwarp = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
         }
         if (iters > 0 && owner) {
             __syncthreads();
-            sweep_any(P, sX, sQ, R, L, sQp + item.w, item);
+            sweep_any(P, sX, sQ, R, L, rec, item);
             if (BARRIERS)
                 for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
         }
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
             if (it + 1 < iters) {
                 if (owner) {
                     __syncthreads();
-                    sweep_any(P, sX, sQ, R, L, sQp + item.w, item);
+                    sweep_any(P, sX, sQ, R, L, rec, item);
                     if (BARRIERS)
                         for (int i = threadIdx.x; i < item.y; i += blockDim.x) P.X[item.x + i] = sX[i];
                 }

@@ -211,6 +211,17 @@ __device__ __forceinline__ void finish_segment_at(const Params &P, int g)
     P.W[g] = omega_of(P, q, P.Qp[g]);
 }
 
+// A rod work item's per-element state in shared memory, de-interleaved: the
+// elements with even item-local index first, then the odd ones.  A colour's
+// threads touch every second element of their rods, so each colour reads and
+// writes consecutive float4s (no shared-memory bank conflicts).
+struct SmemRod {
+    float4 *p;
+    int half;  // elements with even index: (n + 1) / 2
+    __device__ __forceinline__ float4 &operator[](int i) const { return p[(i & 1) ? half + (i >> 1) : (i >> 1)]; }
+};
+__device__ __forceinline__ SmemRod smem_rod(float4 *p, int n) { return SmemRod{p, (n + 1) >> 1}; }
+
 // Multipliers of one slot kept across launches (contact path): 24 floats.
 struct SlotLam {
     float4 s0, s1, b1, b2;
@@ -330,7 +341,7 @@ __device__ __forceinline__ void zero_lam(SlotLam &L)
 // with surface bending (RV2 non-null), three colours of interior vertices
 // i mod 3 (each couples scales i-1, i, i+1).  Every thread of the CTA must call
 // it (it synchronises the CTA between colours).
-__device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L, float inv_h2,
+__device__ __forceinline__ void sweep(SmemRod sX, SmemRod sQ, const SlotRest &R, SlotLam &L, float inv_h2,
                                       bool vol, const float4 *__restrict__ RV2 = nullptr)
 {
     const int lv = R.lv, ls = R.ls;
@@ -360,7 +371,7 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
                        R.aV2, L.b2, L.v2, inv_h2, vol);
         sQ[ls + 1] = qa;
         sQ[ls + 2] = qb;
-        reinterpret_cast<float *>(sX + lv + 2)[3] = s;
+        sX[lv + 2].w = s;
     }
     __syncthreads();
     // colour 3: odd interior vertices (2p+1), segments 2p and 2p+1
@@ -371,7 +382,7 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
                        R.aB1, R.aV1, L.b1, L.v1, inv_h2, vol);
         sQ[ls] = qa;
         sQ[ls + 1] = qb;
-        reinterpret_cast<float *>(sX + lv + 1)[3] = s;
+        sX[lv + 1].w = s;
     }
     __syncthreads();
     if (RV2) {
@@ -380,15 +391,15 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
             if (R.has1 && (R.p2 + 1) % 3 == c) {  // vertex 2p+1: scales 2p, 2p+1, 2p+2
                 float sp = sX[lv].w, s = sX[lv + 1].w, sn = sX[lv + 2].w;
                 project_laplacian(sp, s, sn, R.ws0, R.ws1, R.ws2, __ldg(RV2 + R.gv + 1), L.l1, inv_h2);
-                reinterpret_cast<float *>(sX + lv)[3] = sp;
-                reinterpret_cast<float *>(sX + lv + 1)[3] = s;
-                reinterpret_cast<float *>(sX + lv + 2)[3] = sn;
+                sX[lv].w = sp;
+                sX[lv + 1].w = s;
+                sX[lv + 2].w = sn;
             } else if (R.hasv2 && (R.p2 + 2) % 3 == c) {  // vertex 2p+2: scales 2p+1, 2p+2, 2p+3
                 float sp = sX[lv + 1].w, s = sX[lv + 2].w, sn = sX[lv + 3].w;
                 project_laplacian(sp, s, sn, R.ws1, R.ws2, R.ws3, __ldg(RV2 + R.gv + 2), L.l2, inv_h2);
-                reinterpret_cast<float *>(sX + lv + 1)[3] = sp;
-                reinterpret_cast<float *>(sX + lv + 2)[3] = s;
-                reinterpret_cast<float *>(sX + lv + 3)[3] = sn;
+                sX[lv + 1].w = sp;
+                sX[lv + 2].w = s;
+                sX[lv + 3].w = sn;
             }
             __syncthreads();
         }
@@ -403,7 +414,7 @@ __device__ __forceinline__ void sweep(float4 *sX, float4 *sQ, const SlotRest &R,
 // it owns (vertices 2p, 2p+1 and the rod's last one, segments 2p, 2p+1) by the
 // sum of the records acting on them divided by their number.  Every thread
 // of the CTA must call it.
-__device__ __forceinline__ void sweep_jacobi(float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L, float inv_h2,
+__device__ __forceinline__ void sweep_jacobi(SmemRod sX, SmemRod sQ, const SlotRest &R, SlotLam &L, float inv_h2,
                                              bool vol, const float4 *__restrict__ RV2, float4 *jS, float4 *jV,
                                              float4 *jL)
 {
@@ -514,7 +525,7 @@ __device__ __forceinline__ void sweep_jacobi(float4 *sX, float4 *sQ, const SlotR
 
 // The iteration of either ordering.  rec: the shared-memory records of
 // sweep_jacobi (3 float4 per segment, 3 per vertex), unused by the colours.
-__device__ __forceinline__ void sweep_any(const Params &P, float4 *sX, float4 *sQ, const SlotRest &R, SlotLam &L,
+__device__ __forceinline__ void sweep_any(const Params &P, SmemRod sX, SmemRod sQ, const SlotRest &R, SlotLam &L,
                                           float4 *rec, int4 item)
 {
     const bool vol = P.volume != 0;
@@ -539,10 +550,10 @@ __device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, boo
                                          float4 *smem)
 {
     const int4 item = P.items[b];
-    float4 *sX = smem;
-    float4 *sQ = smem + item.y;
-    float4 *sXp = sQ + item.w;
-    float4 *sQp = sXp + item.y;
+    const SmemRod sX = smem_rod(smem, item.y);
+    const SmemRod sQ = smem_rod(smem + item.y, item.w);
+    const SmemRod sXp = smem_rod(smem + item.y + item.w, item.y);
+    const SmemRod sQp = smem_rod(smem + 2 * item.y + item.w, item.w);
 
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
         const int v = item.x + i;
@@ -611,8 +622,8 @@ __device__ __forceinline__ void rod_item_first(const Params &P, int b, bool fini
                                                float4 *smem)
 {
     const int4 item = P.items[b];
-    float4 *sX = smem;
-    float4 *sQ = smem + item.y;
+    const SmemRod sX = smem_rod(smem, item.y);
+    const SmemRod sQ = smem_rod(smem + item.y, item.w);
     for (int i = threadIdx.x; i < item.y; i += blockDim.x) {
         const int v = item.x + i;
         float4 x = P.X[v], vel;
