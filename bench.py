@@ -701,7 +701,9 @@ def main():
     fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     nv, ns = sc.nv, sc.ns
     d = per_class[dominant]
-    # algorithmic work per launch of each class (derivation in the design doc)
+    # algorithmic work per launch of each class: 1030 FP32 flop per vertex per colour
+    # sweep, 1500 per candidate pair per contact pass, 64 B per skinned vertex, and for
+    # the broadphase about 60 B per pill plus 8 B per emitted pair
     pairs_last = g.pairs().shape[0]
     if dominant == "rod" and g.solver == V.SOLVER_FRAME:
         # the whole frame: colour sweeps (1030 flop per vertex per sweep) + contact passes
