@@ -942,11 +942,12 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
 // `own` when the lane holds a pill) against the neighbour list [d0, d1) by one
 // warp: the neighbour's pills are loaded 32 at a time from the cell-order
 // sphere / group copies (coalesced) into the warp's shared buffers (32 float4
-// + 32 int) and read back as broadcasts, STEP candidates per step; only pairs
-// with the neighbour entry above pa count (so the own cell's list, starting at
-// the chunk, yields each pair once).  Hits are compacted with a ballot and
-// their output slots reserved with one atomic per step.
-template <int STEP>
+// + 32 int) and read back as broadcasts, STEP candidates per step.  SELF: the
+// list is the chunk's own cell from the chunk on, where only entries above pa
+// pair (each pair once); a forward neighbour's entries all lie above the
+// chunk's.  Steps without a hit in the warp cost one vote; hits are compacted
+// with a ballot and their output slots reserved with one atomic.
+template <int STEP, bool SELF>
 __device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, float4 sa, int ga, int d0, int d1,
                                            float4 *cbuf, int *gbuf)
 {
@@ -963,13 +964,18 @@ __device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, fl
         const int m = min(32, d1 - cb);
         for (int j0 = 0; j0 < m; j0 += STEP) {
             bool hit[STEP];
+            bool any = false;
 #pragma unroll
             for (int t = 0; t < STEP; ++t) {
                 const int j = j0 + t;  // past m: no candidate (j & 31 is still a valid entry)
                 const float4 sj = cbuf[j & 31];
                 const int gj = gbuf[j & 31];
-                hit[t] = j < m && own && cb + j > pa && gj != ga && spheres_overlap(sa, sj);
+                bool h = own && spheres_overlap(sa, sj) && gj != ga && j < m;
+                if (SELF) h = h && cb + j > pa;
+                hit[t] = h;
+                any = any || h;
             }
+            if (!__any_sync(full, any)) continue;
 #pragma unroll
             for (int t = 0; t < STEP; ++t) {
                 const unsigned hm = __ballot_sync(full, hit[t]);
@@ -1040,7 +1046,10 @@ __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u
     const bool own = pa < o1;
     const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int ga = own ? P.cell_grp[pa] : 0;
-    emit_block<STEP>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
+    if (k == 13)
+        emit_block<STEP, true>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
+    else
+        emit_block<STEP, false>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
 }
 
 // All 14 neighbour lists of chunk q by one warp (the same pairs as the 14 units
@@ -1076,7 +1085,11 @@ __device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, i
     while (lists) {
         const int k = __ffs(lists) - 1;
         lists &= lists - 1;
-        emit_block<STEP>(P, pa, own, sa, ga, __shfl_sync(full, d0, k), __shfl_sync(full, d1, k), cbuf, gbuf);
+        const int b0 = __shfl_sync(full, d0, k), b1 = __shfl_sync(full, d1, k);
+        if (k == 13)
+            emit_block<STEP, true>(P, pa, own, sa, ga, b0, b1, cbuf, gbuf);
+        else
+            emit_block<STEP, false>(P, pa, own, sa, ga, b0, b1, cbuf, gbuf);
     }
 }
 
