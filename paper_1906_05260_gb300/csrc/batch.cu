@@ -523,6 +523,23 @@ __global__ void __launch_bounds__(kElemThreads) batch_bundle_kernel(BatchArgs A)
     for (int c = local * warps + (threadIdx.x >> 5); c < sb.P.n_xs; c += nblk * warps) match_cross_section(sb.P, c);
 }
 
+// The start of a substep without its first sweep (the sweep runs beside the
+// broadphase): the previous substep's velocity update (`finish_prev`) and the
+// prediction of every vertex and segment.
+__global__ void __launch_bounds__(kElemThreads) batch_advance_kernel(BatchArgs A, int finish_prev, float tau)
+{
+    __shared__ BatchScene sb;
+    int local, nblk;
+    batch_enter(A, K_ELEM, sb, local, nblk);
+    const Params &P = sb.P;
+    if (sb.pills && local == 0 && threadIdx.x < 8) P.bounds[threadIdx.x] = 0u;
+    const int i = local * blockDim.x + threadIdx.x;
+    if (i < P.nv)
+        advance_vertex_at(P, i, finish_prev != 0, tau, sb.pills != 0);
+    else if (i < P.nv + P.ns)
+        advance_segment_at(P, i - P.nv, finish_prev != 0);
+}
+
 // Warm start from the bones before the frame's first substep (scenes with a warm-start table).
 __global__ void __launch_bounds__(kElemThreads) batch_warm_kernel(BatchArgs A)
 {
@@ -640,6 +657,8 @@ struct viper_batch {
     int cur = 0;
     std::vector<cudaEvent_t> ev;  // ordering after the scenes' streams
     cudaEvent_t ev_after = nullptr;
+    cudaStream_t side = nullptr;  // the broadphase branch of a sequence
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long launches = 0;
 };
 
@@ -671,6 +690,12 @@ int stage_reserve(viper_batch::Stage &S, size_t bytes)
     S.cap = cap;
     return VIPER_OK;
 }
+
+// A second stream and two events for the broadphase branch of a sequence.
+struct Fork {
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+};
 
 // Launch shape of one sequence: blocks per kernel kind over all its scenes.
 struct Shape {
@@ -731,7 +756,7 @@ void shape_add(Shape &sh, const viper_scene *s, bool cp)
 // Enqueue the frame's launch sequence on st; returns the number of kernels or
 // -1.  With `prof`, each launch is bracketed by that scene's profiling events.
 long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, int iterations, cudaStream_t st,
-                           viper_scene *prof)
+                           viper_scene *prof, const Fork *fork)
 {
     const int *tot = sh.tot;
     const int threads = sh.threads, smem = sh.smem;
@@ -748,20 +773,23 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
         fn();
         ++L;
     };
-    auto broadphase = [&]() {
+    auto broadphase = [&](cudaStream_t bs) {
         if (tot[K_PILL] <= 0) return;
         if (fused_grid) {
-            go(PROF_BROADPHASE, [&] { launch(batch_grid_kernel, tot[K_SCAN], kGridThreads, grid_smem, st, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_grid_kernel, tot[K_SCAN], kGridThreads, grid_smem, bs, A); });
         } else {
-            go(PROF_BROADPHASE, [&] { launch(batch_bounds_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
-            go(PROF_BROADPHASE, [&] { launch(batch_count_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
-            go(PROF_BROADPHASE, [&] { launch(batch_scan_kernel, tot[K_SCAN], kScanThreadsB, 0, st, A); });
-            go(PROF_BROADPHASE, [&] { launch(batch_scatter_kernel, tot[K_PILL], kElemThreads, 0, st, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_bounds_kernel, tot[K_PILL], kElemThreads, 0, bs, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_count_kernel, tot[K_PILL], kElemThreads, 0, bs, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_scan_kernel, tot[K_SCAN], kScanThreadsB, 0, bs, A); });
+            go(PROF_BROADPHASE, [&] { launch(batch_scatter_kernel, tot[K_PILL], kElemThreads, 0, bs, A); });
         }
         go(PROF_PAIRS, [&] {
-            launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, st, A, fused_grid ? sh.emit_mode : 0);
+            launch(batch_emit_kernel, tot[K_EMIT], 32 * kEmitWarpsB, 0, bs, A, fused_grid ? sh.emit_mode : 0);
         });
     };
+    // the broadphase on a second branch beside the first sweep (not while profiling:
+    // the per-class events bracket one stream)
+    const bool forked = fork && fork->side && tot[K_PILL] > 0 && (!prof || prof->prof_class == PROF_NONE);
     auto contact = [&]() {
         go(PROF_CONTACT, [&] { launch(batch_contact_kernel, tot[K_CONTACT], kElemThreads, 0, st, A); });
     };
@@ -770,8 +798,20 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
         // per substep: [finish + predict + sweep 0] | grid | emit | contact | {sweep | contact} x (I - 1)
         for (int k = 0; k < substeps; ++k) {
             const float tau = (float)((double)(k + 1) / substeps);  // as the one-scene path
-            go(PROF_ROD, [&] { launch(batch_rod_first_kernel, tot[K_ROD], threads, smem, st, A, k > 0 ? 1 : 0, tau); });
-            broadphase();
+            if (forked) {
+                // advance | [grid, pair search] beside [first sweep] | contact ...
+                go(PROF_ELEM, [&] { launch(batch_advance_kernel, tot[K_ELEM], kElemThreads, 0, st, A, k > 0 ? 1 : 0, tau); });
+                if (cudaEventRecord(fork->ev_fork, st) != cudaSuccess ||
+                    cudaStreamWaitEvent(fork->side, fork->ev_fork, 0) != cudaSuccess)
+                    return -1;
+                broadphase(fork->side);
+                if (cudaEventRecord(fork->ev_join, fork->side) != cudaSuccess) return -1;
+                go(PROF_ROD, [&] { launch(batch_rod_kernel<false>, tot[K_ROD], threads, smem, st, A, 1, 1, 0, tau); });
+                if (cudaStreamWaitEvent(st, fork->ev_join, 0) != cudaSuccess) return -1;
+            } else {
+                go(PROF_ROD, [&] { launch(batch_rod_first_kernel, tot[K_ROD], threads, smem, st, A, k > 0 ? 1 : 0, tau); });
+                broadphase(st);
+            }
             contact();
             for (int i = 1; i < iterations; ++i) {
                 go(PROF_ROD, [&] { launch(batch_rod_kernel<false>, tot[K_ROD], threads, smem, st, A, 1, 0, 1, tau); });
@@ -790,7 +830,7 @@ long long enqueue_sequence(const BatchArgs &A, const Shape &sh, int substeps, in
             }
             // contact path without iterations: prediction, broadphase, velocity update
             go(PROF_ELEM, [&] { launch(batch_predict_kernel, tot[K_ELEM], kElemThreads, 0, st, A, tau); });
-            broadphase();
+            broadphase(st);
             go(PROF_ELEM, [&] { launch(batch_finish_kernel, tot[K_ELEM], kElemThreads, 0, st, A, 0); });
         }
     }
@@ -853,7 +893,8 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
     cudaStream_t st = B->stream;
     if (cudaMemcpyAsync(S.d, S.h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return VIPER_ECUDA;
     BatchArgs A{reinterpret_cast<const BatchScene *>(S.d), reinterpret_cast<const int *>(S.d + o_off), n};
-    const long long L = enqueue_sequence(A, sh, substeps, iterations, st, nullptr);
+    const Fork fk{B->side, B->ev_fork, B->ev_join};
+    const long long L = enqueue_sequence(A, sh, substeps, iterations, st, nullptr, &fk);
     if (L < 0) return VIPER_ECUDA;
     B->launches += L;
     if (cudaEventRecord(S.done, st) != cudaSuccess) return VIPER_ECUDA;
@@ -905,7 +946,8 @@ int self_batch_capture(viper_scene *s, float dt, int substeps, int iterations, c
     BatchArgs A{reinterpret_cast<const BatchScene *>(t), reinterpret_cast<const int *>(t + o_off), 1};
     s->prof_used = 0;
     if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VIPER_ECUDA;
-    const long long L = enqueue_sequence(A, sh, substeps, iterations, s->stream, s);
+    const Fork fk{s->side, s->ev_fork, s->ev_join};
+    const long long L = enqueue_sequence(A, sh, substeps, iterations, s->stream, s, &fk);
     cudaError_t ce = cudaStreamEndCapture(s->stream, graph);
     if (L < 0 || ce != cudaSuccess) {
         if (ce == cudaSuccess && *graph) cudaGraphDestroy(*graph);
@@ -936,6 +978,9 @@ int viper_batch_create(void *stream, viper_batch **out)
     for (int i = 0; i < 2 && ok; ++i)
         ok = cudaEventCreateWithFlags(&B->stage[i].done, cudaEventDisableTiming) == cudaSuccess;
     if (ok) ok = cudaEventCreateWithFlags(&B->ev_after, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         viper_batch_destroy(B);
         return VIPER_ECUDA;
@@ -955,6 +1000,12 @@ void viper_batch_destroy(viper_batch *B)
     }
     for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
     if (B->ev_after) cudaEventDestroy(B->ev_after);
+    if (B->side) {
+        cudaStreamSynchronize(B->side);
+        cudaStreamDestroy(B->side);
+    }
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_join) cudaEventDestroy(B->ev_join);
     if (B->own_stream) cudaStreamDestroy(B->stream);
     delete B;
 }

@@ -191,6 +191,47 @@ __device__ __forceinline__ void predict_segment_at(const Params &P, int g, bool 
     }
 }
 
+// The start of a substep for vertex v without its first sweep: with
+// `finish_prev`, the previous substep's pending contact corrections and
+// velocity update; then the prediction (Sec. 6) at bone fraction tau, the
+// substep's start state in Xp, the predicted world position for the
+// broadphase when `world`, and cleared half-plane multipliers (as the first
+// sweep kernel does before its sweep).
+__device__ __forceinline__ void advance_vertex_at(const Params &P, int v, bool finish_prev, float tau, bool world)
+{
+    float4 x = P.X[v], vel;
+    if (finish_prev) {
+        x = apply_pending(P, v, x);
+        const float4 xp = P.Xp[v];
+        vel = make_float4((x.x - xp.x) * P.inv_h, (x.y - xp.y) * P.inv_h, (x.z - xp.z) * P.inv_h,
+                          (x.w - xp.w) * P.inv_h);
+        check_finite(P, x);
+        P.V[v] = vel;
+    } else {
+        vel = P.V[v];
+    }
+    P.Xp[v] = x;
+    x = predict_vertex(P, x, vel, P.RV1[v], tau);
+    if (world) P.Xpred[v] = to_world(P, v, x);
+    for (int k = 0; k < P.n_planes; ++k) P.lam_plane[(size_t)v * P.n_planes + k] = 0.f;
+    P.X[v] = x;
+}
+
+__device__ __forceinline__ void advance_segment_at(const Params &P, int g, bool finish_prev)
+{
+    const float4 q = P.Q[g];
+    float4 w;
+    if (finish_prev) {
+        check_finite(P, q);
+        w = omega_of(P, q, P.Qp[g]);
+        P.W[g] = w;
+    } else {
+        w = P.W[g];
+    }
+    P.Qp[g] = q;
+    P.Q[g] = predict_quat(P, q, w);
+}
+
 // Velocity update of vertex v (after the pending contact corrections when `apply`).
 __device__ __forceinline__ void finish_vertex_at(const Params &P, int v, bool apply)
 {

@@ -559,8 +559,8 @@ def test_warm_start_and_activation_in_a_multi_scene_step(V):
         B.step(a, [sc.bone_pose((f + 1) * sc.dt) for sc in scenes], None, warm.dt, 10, 4)
         counts.append(B.launch_count() - c0)
     B.synchronize()
-    # per substep 2 I + 2, velocity update and frame end, one warm-start launch (no mesh: no skinning)
-    assert counts == [10 * (2 * 4 + 2) + 2 + 1] * 2, counts
+    # per substep 2 I + 3, velocity update and frame end, one warm-start launch (no mesh: no skinning)
+    assert counts == [10 * (2 * 4 + 3) + 2 + 1] * 2, counts
     for f in range(2):
         for o, sc in zip(b, scenes):
             o.set_bones(*sc.bone_pose((f + 1) * sc.dt))
