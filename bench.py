@@ -47,7 +47,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """nvidia-smi clock / throttle sampling while the timed region runs: the
+    sampler is started (and has printed its first line) before the region, and
+    only the lines that arrive between begin() and end() are kept."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -57,6 +59,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -65,12 +68,21 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.monotonic() + 5.0
+            while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -80,9 +92,12 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        t0 = self.t0 if self.t0 is not None else 0.0
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        lines = [ln for t, ln in self.lines if t0 <= t <= t1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -95,7 +110,8 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window_s": (t1 - t0) if self.t1 is not None and self.t0 is not None else None}
 
 
 def dist_setup():
@@ -540,7 +556,7 @@ def bench_muscles(V, torch, flush, dist, frames, rank=0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -571,6 +587,7 @@ def main():
     stream = g.stream
     nb = sc.bones.n
     K, W = args.steps, args.warmup
+    sec_frames = max(10, min(K, 60) // 2)  # frames per timed section beside the main line
 
     # per-frame bone poses: the inputs, generated before timing
     total_frames = 10 * (W + K) + 400
@@ -616,8 +633,10 @@ def main():
     barrier(dist)
     torch.cuda.synchronize()
     l0 = g.launch_count()
+    clocks.begin()
     ts = timed(K, device_frame)
     torch.cuda.synchronize()
+    clocks.end()
     barrier(dist)
     launches = g.launch_count() - l0
     clk = clocks.stop()
@@ -735,9 +754,10 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dominant
     # DRAM bytes per launch of the dominant class from one ncu capture of this workload
-    # (profiles/batch_kernels_muscle_rig.md: first sweep 1.02 MB, later sweeps 1.09 MB,
-    # one and three per substep); other classes or solvers: not captured
-    roof["traffic"] = (1.016e6 + 3 * 1.089e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
+    # (first sweep 0.716 MB, later sweeps 1.092 MB, one and three per substep; the
+    # velocity update and prediction run in the advance kernel before them); other
+    # classes or solvers: not captured
+    roof["traffic"] = (0.716e6 + 3 * 1.092e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
     roof["traffic_unit"] = "bytes per launch (dram read + write, ncu)"
     roof["per_class"] = per_class
 
@@ -754,7 +774,7 @@ def main():
             g.set_solver(mode)
             for _ in range(3):
                 device_frame()
-            tp = timed(max(10, K // 2), device_frame)
+            tp = timed(sec_frames, device_frame)
             pm = reduce_max(dist, sum(tp) / len(tp))
             res = {"value": units / (pm * 1e-3), "ms_per_step": pm, "p50_ms": float(np.percentile(tp, 50)),
                    "p99_ms": float(np.percentile(tp, 99)), "solver": label}
@@ -769,24 +789,24 @@ def main():
     batching = None
     convergence = None
     if not args.no_batching:
-        batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, max(10, K // 2))
+        batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, sec_frames)
         convergence = bench_convergence(V, np)
 
     # ---- skinning alone on a large mesh: the HBM-streaming stage's roofline
     lbs = None
     if not args.no_lbs:
-        lbs = bench_lbs(V, torch, flush, dist, max(10, K // 2), peaks, peak_kind, rank=rank)
+        lbs = bench_lbs(V, torch, flush, dist, sec_frames, peaks, peak_kind, rank=rank)
 
     # ---- muscle features: activation + warm start, bundled muscles
     muscles = None
     if not args.no_muscles:
-        muscles = bench_muscles(V, torch, flush, dist, max(10, K // 2), rank=rank)
+        muscles = bench_muscles(V, torch, flush, dist, sec_frames, rank=rank)
 
     # ---- many scenes at once: the multi-scene step against per-scene graphs
     multi = None
     if not args.no_multi:
         g.close()
-        multi = bench_multi_scene(V, torch, flush, dist, max(10, K // 2), rank=rank)
+        multi = bench_multi_scene(V, torch, flush, dist, sec_frames, rank=rank)
 
     # ---- serving: Poisson stream of muscle-rig scenes, 60 Hz frame requests each
     serving = None

@@ -279,7 +279,10 @@ int viper_get_predicted(viper_scene *scene, float *x4, float *rbar);
 /*
  * Device allocator hook for all later scene allocations (e.g. a framework's
  * caching allocator).  alloc(bytes, ctx) returns device memory or NULL;
- * release(ptr, ctx).  Passing NULL restores cudaMalloc/cudaFree.
+ * release(ptr, ctx).  Passing NULL restores cudaMalloc/cudaFree.  Blocks must
+ * be 256-byte aligned, as cudaMalloc's are (the kernels issue aligned 256-bit
+ * loads): scene creation releases a misaligned block and fails with
+ * VIPER_EINVAL.
  */
 int viper_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*release)(void *ptr, void *ctx),
                         void *ctx);

@@ -32,6 +32,10 @@ int dalloc(viper_scene *s, T **p, size_t count)
     if (s->alloc.alloc) {
         ptr = s->alloc.alloc(bytes, s->alloc.ctx);
         if (!ptr) return VIPER_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(ptr) & 255) {  // kernels rely on cudaMalloc's alignment
+            s->alloc.release(ptr, s->alloc.ctx);
+            return VIPER_EINVAL;
+        }
     } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
         return VIPER_ENOMEM;

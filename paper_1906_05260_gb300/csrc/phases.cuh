@@ -1326,6 +1326,17 @@ __device__ __forceinline__ void lbs_frame_at(const Params &P, const float4 *__re
     f[1] = make_float4(t.x, t.y, t.z, sm);
 }
 
+// One 32-byte frame in a single 256-bit read-only load (sm_100 and later): the
+// frame array starts 256-byte aligned and a frame is 32 bytes, so each frame is
+// one aligned sector and a warp's random gather costs one L1 request per lane
+// instead of two.
+__device__ __forceinline__ void ld_frame(const float4 *f, float4 &r, float4 &ts)
+{
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w), "=f"(ts.x), "=f"(ts.y), "=f"(ts.z), "=f"(ts.w)
+                 : "l"(f));
+}
+
 // Skinned position of mesh vertex i: sum_k w_k T_k Tbar_k^-1 rest_i over its
 // four frames, from the vertex's rest position, frame ids and weights.  A
 // frame is 32 bytes: the relative rotation r = R_j Rbar_j^T as a unit
@@ -1344,7 +1355,8 @@ __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns
             continue;
         }
         const float4 *f = frames + kLbsFrame * (size_t)ids[k];
-        const float4 r = __ldg(f), ts = __ldg(f + 1);
+        float4 r, ts;
+        ld_frame(f, r, ts);
         const V3 y = qrot(r, v3(p.x, p.y, p.z));
         ox += wv[k] * (ts.w * y.x + ts.x);
         oy += wv[k] * (ts.w * y.y + ts.y);

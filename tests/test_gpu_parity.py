@@ -623,3 +623,68 @@ def test_vector_volume_stays_on_the_plain_solver(V):
     assert a.sync() == 0 and b.sync() == 0
     for key in ("x4", "v4", "q4", "w4"):
         np.testing.assert_array_equal(a.get_state()[key], b.get_state()[key], err_msg=key)
+
+
+# ---------------------------------------------------------------- degenerate inputs
+
+def _two_vertex_rods(n_rods=5, contacts=True):
+    """Rods of a single segment (no interior vertex: no bend constraints) in a
+    zig-zag chain: consecutive rods head +-60 deg off the x axis with seeded
+    jitter, and each rod's end sphere overlaps the next rod's start sphere by
+    0.1 mm, so every contact is end to end.  There the separation grows with
+    slope ~l/2 away from both closest points, and the ten dichotomous decisions
+    stay far above FP32 rounding; where two pills cross away from their ends the
+    last decisions compare values that differ by less than FP32 resolves, the
+    contact point is known to ~2^-7 of the segment, and free rods carry the
+    resulting velocity differences (1e-4 of their length after two frames)."""
+    rng = np.random.default_rng(4)
+    r, l, depth = 0.01, 0.05, 1e-4
+    off = (np.arange(n_rods + 1) * 2).astype(np.int32)
+    pos = np.zeros((2 * n_rods, 3))
+    quats = []
+    start = np.zeros(3)
+    prev = None
+    for k in range(n_rods):
+        th = np.radians((60.0 if k % 2 == 0 else -60.0) + rng.uniform(-10, 10))
+        d = np.array([np.cos(th), np.sin(th), 0.0])
+        if prev is not None:
+            g = prev + d
+            start = pos[2 * k - 1] + (2 * r - depth) * g / np.linalg.norm(g)
+        pos[2 * k], pos[2 * k + 1] = start, start + l * d
+        quats.append(S.quat_from_z(d))
+        prev = d
+    return S.Scene(name="two-vertex", rod_offsets=off, rest_pos=pos, rest_quat=np.array(quats),
+                   radius=np.full(2 * n_rods, r), density=np.full(n_rods, 1000.0),
+                   c_stretch=np.full(n_rods, 1e-6), c_bend=np.full(n_rods, 1e-6), c_volume=np.full(n_rods, 1e-6),
+                   group=np.arange(n_rods, dtype=np.int32), gravity=np.array([0.0, -9.81, 0.0]),
+                   pin_vertex=np.zeros(0, np.int32), pin_bone=np.zeros(0, np.int32), pin_offset=np.zeros((0, 3)),
+                   bones=None, planes=np.zeros((0, 4)), contact_compliance=1e-9, contacts=contacts, volume=True,
+                   dt=1 / 60, substeps=10, iterations=4, frames=2)
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
+def test_single_segment_rods_with_contacts(V, solver):
+    """The smallest rods (two vertices, one segment, no interior vertex) in
+    shallow crossing contact: the slot layout, colouring and contacts still
+    match.  (Deep, near-parallel initial overlaps are left out: there the
+    dichotomous probe's comparisons flip with rounding and FP32 and FP64
+    legitimately part ways.)"""
+    sc = _two_vertex_rods()
+    g, o = _pair(V, sc, solver)
+    g.frame(); o.frame()
+    assert len(g.pairs()) > 0  # the rods do touch
+    g.frame(); o.frame()
+    assert g.sync() == 0
+    e = assert_parity(sc, g.get_state(), o.get_state(), POS_TOL_1, what="two-vertex rods, 2 frames")
+    print("two-vertex rods with contacts, 2 frames errors vs FP64:", e)
+
+
+def test_empty_skin_and_empty_batch_calls(V):
+    sc = S.muscle_rig(seed=1, n_rods=10, mesh_verts=100)
+    g = V.Scene(sc)
+    L = V.lib()
+    assert L.viper_skin(g.handle, 0, None, None, None, None) == 0
+    B = V.Batch()
+    assert B.step([], None, None, 1 / 60, 10, 4) == []
+    g.frame()
+    assert g.sync() == 0
