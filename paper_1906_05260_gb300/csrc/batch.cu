@@ -502,9 +502,21 @@ __global__ void __launch_bounds__(kElemThreads) batch_contact_kernel(BatchArgs A
     const int np_all = sb.pills ? *P.npairs : 0;
     const int np = min(np_all, P.max_pairs);
     if (local == 0 && threadIdx.x == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
-    const int total = np + (P.n_planes > 0 ? P.nv : 0);
+    const int nvp = P.n_planes > 0 ? P.nv : 0;
     const float at = P.contact_alpha * P.inv_h2;
-    for (int i = local * blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
+    const int threads = nblk * blockDim.x;
+    if (!P.contact_threads && (long long)np * 16 <= threads) {
+        // few pairs (a scene's usual case, a few per cent of its pills): a warp
+        // per pair, at most two pairs per warp, the search's steps four at a
+        // time (three rounds against ten steps); then the vertices' half-plane
+        // constraints
+        const int lane = threadIdx.x & 31;
+        for (int i = (local * blockDim.x + threadIdx.x) >> 5; i < np; i += threads >> 5)
+            contact_pair_warp(P, i, at, lane);
+        for (int i = local * blockDim.x + threadIdx.x; i < nvp; i += threads) contact_planes(P, i, at);
+        return;
+    }
+    for (int i = local * blockDim.x + threadIdx.x; i < np + nvp; i += threads) {
         if (i < np)
             contact_pair(P, i, at);
         else
@@ -889,6 +901,11 @@ int run_group(viper_batch *B, const viper_batch_item *items, const std::vector<i
         shape_add(sh, s, cp);
     }
     for (int c = 0; c < K_KINDS; ++c) sh.tot[c] = off[c * (n + 1) + n];
+    // a warp per contact pair shortens one scene's chain but multiplies the
+    // lanes' work; once the scenes' contact passes fill the GPU, throughput
+    // decides: one thread per pair
+    if (sh.tot[K_CONTACT] > device_sm_count())
+        for (int k = 0; k < n; ++k) hs[k].P.contact_threads = 1;
 
     cudaStream_t st = B->stream;
     if (cudaMemcpyAsync(S.d, S.h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return VIPER_ECUDA;

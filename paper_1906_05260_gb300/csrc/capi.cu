@@ -861,6 +861,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.jacobi = (d->flags & VIPER_FLAG_JACOBI) ? 1 : 0;
     P.vvec = (d->flags & VIPER_FLAG_VOLUME_VECTOR) && (d->flags & VIPER_FLAG_VOLUME) ? 1 : 0;
     if (P.vvec) s->mode = VIPER_SOLVER_PLAIN;  // the vector volume form runs on the plain path only
+    P.contact_threads = (d->flags & VIPER_FLAG_CONTACT_THREADS) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
     P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;

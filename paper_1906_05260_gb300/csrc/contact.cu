@@ -180,21 +180,10 @@ static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n
     if (s) s->launches += 3;
 }
 
-static int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
 
 void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s)
 {
-    const int grid = (P.ns + 255) / 256 < 4 * sm_count() ? (P.ns + 255) / 256 + 1 : 4 * sm_count();
+    const int grid = (P.ns + 255) / 256 < 4 * device_sm_count() ? (P.ns + 255) / 256 + 1 : 4 * device_sm_count();
     cudaMemsetAsync(P.bounds, 0, 8 * sizeof(unsigned int), st);
     {
         ProfScope ps(s, PROF_BROADPHASE);
@@ -211,7 +200,7 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
     }
     {
         int eg = (P.ns + 8 * kEmitWarps - 1) / (8 * kEmitWarps);  // a warp per 8 pills: a few units each
-        if (eg > 8 * sm_count()) eg = 8 * sm_count();
+        if (eg > 8 * device_sm_count()) eg = 8 * device_sm_count();
         if (eg < 1) eg = 1;
         ProfScope ps(s, PROF_PAIRS);
         bp_emit_kernel<<<eg, 32 * kEmitWarps, 0, st>>>(P);
@@ -241,7 +230,7 @@ void launch_contacts(viper_scene *s)
 {
     const int cap = s->P.max_pairs + (s->P.n_planes > 0 ? s->P.nv : 0);
     int grid = (cap + 255) / 256;
-    if (grid > 2 * sm_count()) grid = 2 * sm_count();
+    if (grid > 2 * device_sm_count()) grid = 2 * device_sm_count();
     if (grid < 1) grid = 1;
     ProfScope ps(s, PROF_CONTACT);
     contact_kernel<<<grid, 256, 0, s->ls>>>(s->P);

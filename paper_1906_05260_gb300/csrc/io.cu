@@ -28,7 +28,7 @@ __global__ void lbs_gather_kernel(int n, int ns, const float4 *__restrict__ rest
         lbs_vertices(base + threadIdx.x, blockDim.x, n, ns, rest, idx, w, frames, out, err);
 }
 
-static int sms()
+int device_sm_count()
 {
     static int n = 0;
     if (!n) {
@@ -44,7 +44,7 @@ void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, cons
 {
     lbs_frames_kernel<<<(s->ns + 255) / 256, 256, 0, s->ls>>>(s->P, s->LQ, s->LC, s->d_sperm, s->frames);
     int grid = (n + 256 * kLbsBatch - 1) / (256 * kLbsBatch);
-    if (grid > 8 * sms()) grid = 8 * sms();
+    if (grid > 8 * device_sm_count()) grid = 8 * device_sm_count();
     if (grid < 1) grid = 1;
     ProfScope ps(s, PROF_LBS);
     lbs_gather_kernel<<<grid, 256, 0, s->ls>>>(n, s->ns, rest, idx, w, s->frames, out, s->P.err);

@@ -1152,9 +1152,15 @@ __device__ __forceinline__ float4 world_of(const Params &P, int v)
 }
 
 
-// One pill-pill contact (Sec. 7.2): narrowphase on the current state, then one
+// Pill-pill contacts (Sec. 7.2): narrowphase on the current state, then one
 // XPBD update of pair i's multiplier if the pills interpenetrate.
-__device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
+struct ContactPair {
+    PillPair Q;
+    int vs[4];      // the pills' vertices a1, a2, b1, b2
+    float rbar[4];  // their rest radii
+};
+
+__device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair &c)
 {
     const int2 pr = P.pairs[i];
     const int va = P.seg_v0[pr.x], vb = P.seg_v0[pr.y];
@@ -1165,31 +1171,57 @@ __device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
         return make_float4(__fadd_rn(x.x, o.x), __fadd_rn(x.y, o.y), __fadd_rn(x.z, o.z), x.w);
     };
     const float4 xa1 = wpos(va, oa), xa2 = wpos(va + 1, oa), xb1 = wpos(vb, ob), xb2 = wpos(vb + 1, ob);
-    const float ra1 = P.RV0[va].w, ra2 = P.RV0[va + 1].w, rb1 = P.RV0[vb].w, rb2 = P.RV0[vb + 1].w;
-    PillPair Q;
-    Q.a1 = xyz(xa1); Q.a2 = xyz(xa2); Q.b1 = xyz(xb1); Q.b2 = xyz(xb2);
-    Q.ra1 = xa1.w * ra1; Q.ra2 = xa2.w * ra2; Q.rb1 = xb1.w * rb1; Q.rb2 = xb2.w * rb2;
-    const float al = dichotomous(Q);
+    c.vs[0] = va; c.vs[1] = va + 1; c.vs[2] = vb; c.vs[3] = vb + 1;
+    c.rbar[0] = P.RV0[va].w; c.rbar[1] = P.RV0[va + 1].w; c.rbar[2] = P.RV0[vb].w; c.rbar[3] = P.RV0[vb + 1].w;
+    c.Q.a1 = xyz(xa1); c.Q.a2 = xyz(xa2); c.Q.b1 = xyz(xb1); c.Q.b2 = xyz(xb2);
+    c.Q.ra1 = xa1.w * c.rbar[0]; c.Q.ra2 = xa2.w * c.rbar[1]; c.Q.rb1 = xb1.w * c.rbar[2]; c.Q.rb2 = xb2.w * c.rbar[3];
+}
+
+// The update of pair i at contact parameter al; vertices t0, t0 + tstep, ...
+// of the four are accumulated by this thread, and the multiplier is stored if
+// write_lam.
+__device__ __forceinline__ void contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
+                                              int tstep, bool write_lam)
+{
     float be;
-    const float C = coll_f(Q, al, be);
-    V3 d = lerp3(Q.a1, Q.a2, al) - lerp3(Q.b1, Q.b2, be);
+    const float C = coll_f(c.Q, al, be);
+    V3 d = lerp3(c.Q.a1, c.Q.a2, al) - lerp3(c.Q.b1, c.Q.b2, be);
     float dist = sqrtf(dot(d, d));
     if (!(C < 0.f) || dist < 1e-12f) return;
     V3 n = (1.f / dist) * d;
-    const float4 m1 = P.RV1[va], m2 = P.RV1[va + 1], m3 = P.RV1[vb], m4 = P.RV1[vb + 1];
+    const float4 m1 = P.RV1[c.vs[0]], m2 = P.RV1[c.vs[1]], m3 = P.RV1[c.vs[2]], m4 = P.RV1[c.vs[3]];
     const float wt[4] = {1.f - al, al, -(1.f - be), -be};
     const float wx[4] = {inv_mass(m1), inv_mass(m2), inv_mass(m3), inv_mass(m4)};
     const float wsv[4] = {m1.y, m2.y, m3.y, m4.y};
-    const float rb[4] = {ra1, ra2, rb1, rb2};
     float den = at;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * rb[t] * rb[t];
+    for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * c.rbar[t] * c.rbar[t];
     const float lam = P.lam_pair[i];
     const float dl = (-C - at * lam) / den;
-    P.lam_pair[i] = lam + dl;
-    const int vs[4] = {va, va + 1, vb, vb + 1};
+    if (write_lam) P.lam_pair[i] = lam + dl;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc_add(P, vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * rb[t] * dl);
+    for (int t = 0; t < 4; ++t)
+        if (t >= t0 && (t - t0) % tstep == 0)
+            acc_add(P, c.vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * c.rbar[t] * dl);
+}
+
+// Pair i by one thread.
+__device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
+{
+    ContactPair c;
+    contact_load(P, i, c);
+    contact_apply(P, i, at, c, dichotomous(c.Q), 0, 1, true);
+}
+
+// Pair i by one warp (all lanes call): the search four steps per round
+// (dichotomous_warp), lane t < 4 accumulates vertex t, lane 0 stores the
+// multiplier.  Same result as contact_pair, bit for bit.
+__device__ __forceinline__ void contact_pair_warp(const Params &P, int i, float at, int lane)
+{
+    ContactPair c;
+    contact_load(P, i, c);
+    const float al = dichotomous_warp(c.Q, lane);
+    contact_apply(P, i, at, c, al, lane, 4, lane == 0);
 }
 
 // Half-plane constraints of vertex v's sphere (Sec. 7).

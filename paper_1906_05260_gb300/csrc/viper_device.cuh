@@ -524,18 +524,75 @@ __device__ __forceinline__ float coll_f(const PillPair &P, float al, float &be)
 
 // Dichotomous search, 10 iterations (Sec. 7.2): probes mid -+ eps/2 with
 // eps = 1e-3 of the current bracket; keep the side of the smaller probe.
+constexpr int kDichoSteps = 10;
+__device__ __forceinline__ void dicho_probes(float lo, float hi, float &x1, float &x2)
+{
+    const float mid = 0.5f * (lo + hi);
+    const float eps = 1e-3f * (hi - lo);
+    x1 = mid - 0.5f * eps;
+    x2 = mid + 0.5f * eps;
+}
+__device__ __forceinline__ void dicho_keep(float &lo, float &hi, float x1, float x2, bool left)
+{
+    if (left)
+        hi = x2;
+    else
+        lo = x1;
+}
+
 __device__ __forceinline__ float dichotomous(const PillPair &P)
 {
     float lo = 0.f, hi = 1.f, be;
 #pragma unroll 1
-    for (int it = 0; it < 10; ++it) {
-        float mid = 0.5f * (lo + hi);
-        float eps = 1e-3f * (hi - lo);
-        float x1 = mid - 0.5f * eps, x2 = mid + 0.5f * eps;
-        if (coll_f(P, x1, be) < coll_f(P, x2, be))
-            hi = x2;
-        else
-            lo = x1;
+    for (int it = 0; it < kDichoSteps; ++it) {
+        float x1, x2;
+        dicho_probes(lo, hi, x1, x2);
+        dicho_keep(lo, hi, x1, x2, coll_f(P, x1, be) < coll_f(P, x2, be));
+    }
+    return 0.5f * (lo + hi);
+}
+
+// The same search by one warp, four steps per round: the 2 + 4 + 8 + 16 probes
+// of the next four steps' possible brackets are evaluated at once (lane ->
+// depth j, node b = the earlier decisions of the round, side), then the four
+// decisions are read off in order.  Every lane derives its bracket by the same
+// operations the sequential search performs, so the probes, the decisions and
+// the result are bitwise those of dichotomous().  All 32 lanes must call it.
+__device__ __forceinline__ float dichotomous_warp(const PillPair &P, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const int j = 31 - __clz((lane >> 1) + 1);  // depth of this lane's node (4 for lanes 30, 31)
+    const int b = (lane - 2 * ((1 << j) - 1)) >> 1;
+    const int side = lane & 1;
+    float lo = 0.f, hi = 1.f;
+#pragma unroll
+    for (int k0 = 0; k0 < kDichoSteps; k0 += 4) {
+        const int m = kDichoSteps - k0 < 4 ? kDichoSteps - k0 : 4;
+        float f = 0.f;
+        if (j < m) {
+            float l = lo, h = hi, x1, x2;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t < j) {
+                    dicho_probes(l, h, x1, x2);
+                    dicho_keep(l, h, x1, x2, (b >> t) & 1);
+                }
+            dicho_probes(l, h, x1, x2);
+            float be;
+            f = coll_f(P, side ? x2 : x1, be);
+        }
+        int node = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (t < m) {
+                const int base = 2 * ((1 << t) - 1) + 2 * node;
+                const float f1 = __shfl_sync(full, f, base), f2 = __shfl_sync(full, f, base + 1);
+                const bool left = f1 < f2;
+                float x1, x2;
+                dicho_probes(lo, hi, x1, x2);
+                dicho_keep(lo, hi, x1, x2, left);
+                node |= (left ? 1 : 0) << t;
+            }
     }
     return 0.5f * (lo + hi);
 }

@@ -41,6 +41,7 @@ struct Params {
     int surface;
     int jacobi;  // rod constraints by Jacobi with averaging instead of four-colour Gauss-Seidel
     int vvec;    // volume constraint in the printed vector form (plain path; multipliers in lamV2)
+    int contact_threads;  // batched contact pass: one thread per pair even when the pairs fit its warps
     // bundle cross-sections (shape matching): members xs_off[c] .. xs_off[c+1] with
     // vertex, frame segment (-1: none), rest offset from the rest mean, rest frame;
     // xs_mub[c] = (rest mean, sum of the rest members' squared norms)
@@ -225,6 +226,7 @@ void launch_broadphase(viper_scene *s);
 void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s);
 void launch_contacts(viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
+int device_sm_count();  // SMs of the current device (cached)
 void launch_bundles(viper_scene *s);
 void launch_warm(viper_scene *s);
 void launch_activation(viper_scene *s);

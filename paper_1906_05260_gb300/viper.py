@@ -21,6 +21,7 @@ OK = 0
 EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET = -1, -2, -3, -4, -5, -6, -7
 FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI, FLAG_WARM_START = 1, 2, 4, 8, 16
 FLAG_VOLUME_VECTOR = 32
+FLAG_CONTACT_THREADS = 64  # contact pass with one thread per pair always (timing only)
 SOLVER_PLAIN, SOLVER_BATCHED, SOLVER_FRAME = 0, 1, 2
 SOLVER_AUTO = -1
 PROF_NONE, PROF_ROD, PROF_CONTACT, PROF_BROADPHASE, PROF_LBS, PROF_ELEMENTWISE, PROF_PAIRS = 0, 1, 2, 3, 4, 5, 6
@@ -182,7 +183,7 @@ def _i(a):
     return a, a.ctypes.data_as(_ip)
 
 
-def make_desc(scene, stream_handle=None, max_pairs=0):
+def make_desc(scene, stream_handle=None, max_pairs=0, extra_flags=0):
     """Marshal a scenes.Scene into a viper_scene_desc; returns (desc, keepalive)."""
     keep = []
 
@@ -227,7 +228,7 @@ def make_desc(scene, stream_handle=None, max_pairs=0):
                   | (FLAG_SURFACE_BENDING if getattr(scene, "surface_bending", False) else 0)
                   | (FLAG_JACOBI if getattr(scene, "jacobi", False) else 0)
                   | (FLAG_WARM_START if getattr(scene, "warm_start", False) else 0)
-                  | (FLAG_VOLUME_VECTOR if getattr(scene, "volume_vector", False) else 0))
+                  | (FLAG_VOLUME_VECTOR if getattr(scene, "volume_vector", False) else 0) | int(extra_flags))
     desc.max_pairs = int(max_pairs)
     desc.stream = stream_handle
     if getattr(scene, "bundle_offsets", None) is not None and len(scene.bundle_offsets) > 1:
@@ -261,7 +262,7 @@ class Scene:
     """A device-resident VIPER scene (one viper_scene handle)."""
 
     def __init__(self, scene, stream=None, solver=SOLVER_AUTO, block_warps=4, resident_max=256,
-                 max_pairs=0, torch_allocator=True):
+                 max_pairs=0, torch_allocator=True, extra_flags=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA GPU is required")
@@ -269,7 +270,7 @@ class Scene:
         if torch_allocator:
             use_torch_allocator()
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        desc, keep = make_desc(scene, C.c_void_p(self.stream.cuda_stream), max_pairs)
+        desc, keep = make_desc(scene, C.c_void_p(self.stream.cuda_stream), max_pairs, extra_flags)
         h = C.c_void_p()
         with torch.cuda.stream(self.stream):
             _check(L.viper_scene_create(C.byref(desc), C.byref(h)), "viper_scene_create")

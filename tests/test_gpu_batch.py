@@ -248,3 +248,21 @@ def test_batch_pairs_bit_exact_in_a_large_group(V):
             ref = oracle.broadphase_f32(sc.rod_offsets, sc.group, x4, rb)
             np.testing.assert_array_equal(o.pairs(), ref)
     assert all(o.sync() == 0 for o in objs)
+
+
+def test_contact_warp_search_matches_thread_search_bitwise(V):
+    """The batched contact pass gives each pair a warp while the pairs fit its
+    warps (the dichotomous search four steps per round); with
+    FLAG_CONTACT_THREADS it searches with one thread per pair.  Both make the
+    same decisions on the same values, so the states agree bit for bit."""
+    sc = S.muscle_rig(mesh_verts=0)
+    a = V.Scene(sc, solver=V.SOLVER_BATCHED, extra_flags=V.FLAG_CONTACT_THREADS)
+    b = V.Scene(sc, solver=V.SOLVER_BATCHED)
+    warps = min(64, -(-sc.ns // 256)) * 8  # the batched contact pass's warps for this scene
+    for _ in range(3):
+        a.frame(); b.frame()
+        assert 0 < len(b.pairs()) <= 2 * warps  # the warp-per-pair branch ran
+    assert a.sync() == 0 and b.sync() == 0
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("x4", "v4", "q4", "w4"):
+        np.testing.assert_array_equal(sa[k], sb[k])
