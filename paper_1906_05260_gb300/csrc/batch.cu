@@ -197,15 +197,15 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
     __shared__ float4 s_cand[kEmitWarpsB][32];  // per warp: the neighbour block being tested
-    __shared__ int s_cgrp[kEmitWarpsB][32];
+    __shared__ int s_cgrp[kEmitWarpsB][32], s_cid[kEmitWarpsB][32];
     if (mode == 2) {  // a chunk with all its neighbour lists per warp
         const int n = *P.n_chunks;
         for (int q = local * kEmitWarpsB + wib; q < n; q += nblk * kEmitWarpsB)
-            emit_chunk_all<4>(P, G, q, start, s_cand[wib], s_cgrp[wib]);
+            emit_chunk_all<4>(P, G, q, start, s_cand[wib], s_cgrp[wib], s_cid[wib]);
     } else if (mode == 1) {  // a chunk with one neighbour list per warp
         const int n = kEmitUnits * *P.n_chunks;
         for (int u = local * kEmitWarpsB + wib; u < n; u += nblk * kEmitWarpsB)
-            emit_chunk<4>(P, G, u, start, s_cand[wib], s_cgrp[wib]);
+            emit_chunk<4>(P, G, u, start, s_cand[wib], s_cgrp[wib], s_cid[wib]);
     } else {
         for (int u = local * kEmitWarpsB + wib; u < kEmitUnits * cells; u += nblk * kEmitWarpsB)
             emit_cell<4>(P, G, u, start);
@@ -646,7 +646,7 @@ void launch(void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_
 // per warp (mode 2, a warp per 8 pills), which cuts the number of dependent
 // load chains by about 14.
 constexpr int kEmitPillsPerWarp = 8, kEmitPillsPerWarpSmall = 1, kEmitSmallGroup = 16384;
-constexpr int kMeshPerThread = 16;  // kLbsBatch vertices per round, 4 rounds
+constexpr int kMeshPerThread = 16;  // kLbsBatch vertices per round, 16 / kLbsBatch rounds
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -988,18 +988,19 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
 // pair (each pair once); a forward neighbour's entries all lie above the
 // chunk's.  Steps without a hit in the warp cost one vote; hits are compacted
 // with a ballot and their output slots reserved with one atomic.
-template <int STEP, bool SELF>
-__device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, float4 sa, int ga, int d0, int d1,
-                                           float4 *cbuf, int *gbuf)
+template <int STEP, bool SELF, bool IDS>
+__device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, float4 sa, int ga, int ia, int d0, int d1,
+                                           float4 *cbuf, int *gbuf, int *ibuf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     for (int cb = d0; cb < d1; cb += 32) {
         const int q = cb + lane;
         __syncwarp();  // the previous block's reads are done
-        if (q < d1) {
+        if (q < d1) {  // sphere and group of the block; with IDS the pill ids too (ready for the hits)
             cbuf[lane] = P.cell_sph[q];
             gbuf[lane] = P.cell_grp[q];
+            if (IDS) ibuf[lane] = P.cell_pills[q];
         }
         __syncwarp();
         const int m = min(32, d1 - cb);
@@ -1027,7 +1028,8 @@ __device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, fl
                     if (hit[t]) {
                         const int idx = out + __popc(hm & ((1u << lane) - 1u));
                         if (idx < P.max_pairs) {
-                            const int a = P.cell_pills[pa], b = P.cell_pills[cb + j0 + t];
+                            const int a = IDS ? ia : P.cell_pills[pa];
+                            const int b = IDS ? ibuf[j0 + t] : P.cell_pills[cb + j0 + t];
                             P.pairs[idx] = make_int2(min(a, b), max(a, b));
                             if (P.lam_pair) P.lam_pair[idx] = 0.f;
                         }
@@ -1064,7 +1066,7 @@ __device__ __forceinline__ int forward_neighbour(const Grid &G, int c, int k)
 // chunk against one neighbour cell, so the units are balanced across warps.
 template <int STEP, class StartFn>
 __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u, StartFn start, float4 *cbuf,
-                                           int *gbuf)
+                                           int *gbuf, int *ibuf)
 {
     const int lane = threadIdx.x & 31;
     const int k = u % kEmitUnits;
@@ -1087,10 +1089,11 @@ __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u
     const bool own = pa < o1;
     const float4 sa = own ? P.cell_sph[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int ga = own ? P.cell_grp[pa] : 0;
+    const int ia = own ? P.cell_pills[pa] : 0;  // latency bound: ids loaded beside the spheres
     if (k == 13)
-        emit_block<STEP, true>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
+        emit_block<STEP, true, true>(P, pa, own, sa, ga, ia, d0, d1, cbuf, gbuf, ibuf);
     else
-        emit_block<STEP, false>(P, pa, own, sa, ga, d0, d1, cbuf, gbuf);
+        emit_block<STEP, false, true>(P, pa, own, sa, ga, ia, d0, d1, cbuf, gbuf, ibuf);
 }
 
 // All 14 neighbour lists of chunk q by one warp (the same pairs as the 14 units
@@ -1099,7 +1102,7 @@ __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u
 // each unit's chain of dependent loads, not its tests, sets the time.
 template <int STEP, class StartFn>
 __device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, int q, StartFn start, float4 *cbuf,
-                                               int *gbuf)
+                                               int *gbuf, int *ibuf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
@@ -1127,10 +1130,11 @@ __device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, i
         const int k = __ffs(lists) - 1;
         lists &= lists - 1;
         const int b0 = __shfl_sync(full, d0, k), b1 = __shfl_sync(full, d1, k);
+        // throughput bound (many scenes): pill ids loaded only for the hits
         if (k == 13)
-            emit_block<STEP, true>(P, pa, own, sa, ga, b0, b1, cbuf, gbuf);
+            emit_block<STEP, true, false>(P, pa, own, sa, ga, 0, b0, b1, cbuf, gbuf, ibuf);
         else
-            emit_block<STEP, false>(P, pa, own, sa, ga, b0, b1, cbuf, gbuf);
+            emit_block<STEP, false, false>(P, pa, own, sa, ga, 0, b0, b1, cbuf, gbuf, ibuf);
     }
 }
 
@@ -1401,7 +1405,7 @@ __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns
 // the streaming 128-bit loads of all of them are issued first (the mesh is
 // read once per frame and bypasses L1), then each blends its frames (L2
 // resident) and is written with a streaming 128-bit store.
-constexpr int kLbsBatch = 4;
+constexpr int kLbsBatch = 2;
 __device__ __forceinline__ void lbs_vertices(int i0, int stride, int n, int ns, const float4 *__restrict__ rest,
                                              const int4 *__restrict__ idx, const float4 *__restrict__ w,
                                              const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
