@@ -71,3 +71,24 @@ def test_reference_arm_under_torchrun_with_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_clock_sampler_keeps_only_the_timed_window():
+    """bench.py's clock record: lines that arrive before begin() or after end()
+    are dropped; the median SM clock, the maximum and the active throttle
+    reasons come from the window alone."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
+    row = "0, {sm}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {pc}"
+    cs.lines = [(1.0, row.format(sm=1000, hw="Active", pc="Not Active")),    # before the window
+                (2.1, row.format(sm=2000, hw="Not Active", pc="Active")),
+                (2.2, row.format(sm=2070, hw="Not Active", pc="Not Active")),
+                (2.3, row.format(sm=2060, hw="Not Active", pc="Not Active")),
+                (3.5, row.format(sm=500, hw="Active", pc="Not Active"))]     # after it
+    cs.t0, cs.t1 = 2.0, 3.0
+    out = cs.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2060 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["window_s"] == pytest.approx(1.0)
