@@ -1022,6 +1022,12 @@ void viper_scene_destroy(viper_scene *s)
 {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->skin_cs) {
+        cudaStreamSynchronize(s->skin_cs);
+        cudaStreamDestroy(s->skin_cs);
+        cudaEventDestroy(s->ev_skin_up);
+        cudaEventDestroy(s->ev_skin_used);
+    }
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : s->prof_ev_skin) cudaEventDestroy(e);
@@ -1202,16 +1208,28 @@ int viper_skin(viper_scene *s, int n, const float *rest4, const int *idx4, const
     const size_t bytes = sizeof(float4) * (size_t)n;
     const float4 *pr = (const float4 *)rest4, *pw = (const float4 *)w4;
     const int4 *pi = (const int4 *)idx4;
-    if (!dr) { VCHECK(cudaMemcpyAsync(br, rest4, bytes, cudaMemcpyHostToDevice, s->stream)); pr = br; }
-    if (!di) { VCHECK(cudaMemcpyAsync(bi, idx4, bytes, cudaMemcpyHostToDevice, s->stream)); pi = (const int4 *)bi; }
-    if (!dw) { VCHECK(cudaMemcpyAsync(bw, w4, bytes, cudaMemcpyHostToDevice, s->stream)); pw = bw; }
+    if (!dr || !di || !dw) {
+        // upload on a copy stream, so that it overlaps the frame still running on
+        // the scene stream; the skinning waits for it
+        if (!s->skin_cs) {
+            VCHECK(cudaStreamCreateWithFlags(&s->skin_cs, cudaStreamNonBlocking));
+            VCHECK(cudaEventCreateWithFlags(&s->ev_skin_up, cudaEventDisableTiming));
+            VCHECK(cudaEventCreateWithFlags(&s->ev_skin_used, cudaEventDisableTiming));
+            VCHECK(cudaEventRecord(s->ev_skin_used, s->ls));
+        }
+        VCHECK(cudaStreamWaitEvent(s->skin_cs, s->ev_skin_used, 0));  // the staging buffer is free
+        if (!dr) { VCHECK(cudaMemcpyAsync(br, rest4, bytes, cudaMemcpyHostToDevice, s->skin_cs)); pr = br; }
+        if (!di) { VCHECK(cudaMemcpyAsync(bi, idx4, bytes, cudaMemcpyHostToDevice, s->skin_cs)); pi = (const int4 *)bi; }
+        if (!dw) { VCHECK(cudaMemcpyAsync(bw, w4, bytes, cudaMemcpyHostToDevice, s->skin_cs)); pw = bw; }
+        VCHECK(cudaEventRecord(s->ev_skin_up, s->skin_cs));
+        VCHECK(cudaStreamWaitEvent(s->ls, s->ev_skin_up, 0));
+    }
     s->prof_in_skin = true;
     launch_lbs(s, n, pr, pi, pw, dout ? (float4 *)out4 : bo);
     s->prof_in_skin = false;
-    if (!dout) {
-        VCHECK(cudaMemcpyAsync(out4, bo, bytes, cudaMemcpyDeviceToHost, s->stream));
-        VCHECK(cudaStreamSynchronize(s->stream));
-    }
+    if (!dout) VCHECK(cudaMemcpyAsync(out4, bo, bytes, cudaMemcpyDeviceToHost, s->ls));
+    if (s->skin_cs) VCHECK(cudaEventRecord(s->ev_skin_used, s->ls));
+    if (!dout) VCHECK(cudaStreamSynchronize(s->ls));
     return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;
 }
 

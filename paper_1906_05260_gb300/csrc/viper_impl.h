@@ -186,6 +186,11 @@ struct viper_scene {
     // scratch for host-pointer skinning
     float4 *skin_buf = nullptr;
     size_t skin_cap = 0;
+    // host operands of viper_skin are uploaded on skin_cs (beside the frame's
+    // kernels); ev_skin_up orders the skinning after the upload, ev_skin_used
+    // the next upload after the skinning that read the staging buffer
+    cudaStream_t skin_cs = nullptr;
+    cudaEvent_t ev_skin_up = nullptr, ev_skin_used = nullptr;
     size_t bytes = 0;
     // kernel timing (viper_profile)
     int prof_class = 0;

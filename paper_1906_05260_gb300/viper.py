@@ -359,8 +359,12 @@ class Scene:
         return self.step()
 
     def skin(self, mesh: Mesh):
+        """LBS of the current state into mesh.out (enqueued on the scene stream;
+        torch's current stream is made to wait for it before later torch work)."""
+        import torch
         _check(lib().viper_skin(self._h, mesh.n, C.c_void_p(mesh.rest.data_ptr()), C.c_void_p(mesh.idx.data_ptr()),
                                 C.c_void_p(mesh.w.data_ptr()), C.c_void_p(mesh.out.data_ptr())), "viper_skin")
+        torch.cuda.current_stream().wait_stream(self.stream)
         return mesh.out
 
     def skin_host(self, rest4, idx4, w4, out4):

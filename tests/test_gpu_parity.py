@@ -262,6 +262,37 @@ def test_state_roundtrip_and_host_skinning(V):
     np.testing.assert_array_equal(dev, host)
 
 
+def test_host_skinning_beside_frames_and_staging_reuse(V):
+    """Host operands are uploaded on a copy stream beside the frame's kernels:
+    each call's result (device or host output) equals the device-operand path
+    on the same operands, also when a call with device output (no sync) is
+    followed at once by a call that refills the staging buffer."""
+    import ctypes as C
+    import torch
+    sc = S.muscle_rig(n_rods=20, mesh_verts=3000)
+    g = V.Scene(sc)
+    n = sc.mesh.n
+    rest4 = np.zeros((n, 4), np.float32); rest4[:, :3] = sc.mesh.rest
+    idx4 = np.ascontiguousarray(sc.mesh.idx, np.int32)
+    rng = np.random.default_rng(5)
+    L = V.lib()
+    for f in range(4):
+        g.frame()  # still running while the next uploads start
+        w_a = np.ascontiguousarray(rng.dirichlet(np.ones(4), n), np.float32)
+        w_b = np.ascontiguousarray(rng.dirichlet(np.ones(4), n), np.float32)
+        dev_out = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+        assert L.viper_skin(g.handle, n, C.c_void_p(rest4.ctypes.data), C.c_void_p(idx4.ctypes.data),
+                            C.c_void_p(w_a.ctypes.data), C.c_void_p(dev_out.data_ptr())) == 0
+        host = np.zeros((n, 4), np.float32)
+        g.skin_host(rest4, idx4, w_b, host)
+        assert g.sync() == 0
+        ref_a = g.skin(V.Mesh(dataclasses.replace(sc.mesh, w=w_a.astype(np.float64))))
+        ref_b = g.skin(V.Mesh(dataclasses.replace(sc.mesh, w=w_b.astype(np.float64))))
+        torch.cuda.synchronize()  # the scene stream included
+        np.testing.assert_array_equal(dev_out.cpu().numpy(), ref_a.cpu().numpy())
+        np.testing.assert_array_equal(host, ref_b.cpu().numpy())
+
+
 def test_autotune_keeps_results(V):
     sc = S.batching(n_rods=256)
     g = V.Scene(sc)
