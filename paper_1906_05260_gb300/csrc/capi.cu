@@ -87,6 +87,19 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister),
+// or nullptr for pageable or device memory.
+void *pinned_device_alias(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 int next_pow2(long long x)
@@ -1224,10 +1237,23 @@ int viper_skin(viper_scene *s, int n, const float *rest4, const int *idx4, const
         VCHECK(cudaEventRecord(s->ev_skin_up, s->skin_cs));
         VCHECK(cudaStreamWaitEvent(s->ls, s->ev_skin_up, 0));
     }
+    // page-locked host output: the kernel stores into it directly (over the
+    // chip-to-host link, overlapped with the kernel) instead of a copy after it
+    float4 *po = dout ? (float4 *)out4 : nullptr;
+    bool copy_out = false;
+    if (!dout) {
+        void *alias = pinned_device_alias(out4);
+        if (alias && (reinterpret_cast<uintptr_t>(alias) & 15u) == 0) {
+            po = static_cast<float4 *>(alias);
+        } else {
+            po = bo;
+            copy_out = true;
+        }
+    }
     s->prof_in_skin = true;
-    launch_lbs(s, n, pr, pi, pw, dout ? (float4 *)out4 : bo);
+    launch_lbs(s, n, pr, pi, pw, po);
     s->prof_in_skin = false;
-    if (!dout) VCHECK(cudaMemcpyAsync(out4, bo, bytes, cudaMemcpyDeviceToHost, s->ls));
+    if (copy_out) VCHECK(cudaMemcpyAsync(out4, bo, bytes, cudaMemcpyDeviceToHost, s->ls));
     if (s->skin_cs) VCHECK(cudaEventRecord(s->ev_skin_used, s->ls));
     if (!dout) VCHECK(cudaStreamSynchronize(s->ls));
     return cudaGetLastError() == cudaSuccess ? VIPER_OK : VIPER_ECUDA;

@@ -264,9 +264,10 @@ def test_state_roundtrip_and_host_skinning(V):
 
 def test_host_skinning_beside_frames_and_staging_reuse(V):
     """Host operands are uploaded on a copy stream beside the frame's kernels:
-    each call's result (device or host output) equals the device-operand path
-    on the same operands, also when a call with device output (no sync) is
-    followed at once by a call that refills the staging buffer."""
+    each call's result (device, pageable host or page-locked host output)
+    equals the device-operand path on the same operands, also when a call with
+    device output (no sync) is followed at once by a call that refills the
+    staging buffer."""
     import ctypes as C
     import torch
     sc = S.muscle_rig(n_rods=20, mesh_verts=3000)
@@ -285,12 +286,17 @@ def test_host_skinning_beside_frames_and_staging_reuse(V):
                             C.c_void_p(w_a.ctypes.data), C.c_void_p(dev_out.data_ptr())) == 0
         host = np.zeros((n, 4), np.float32)
         g.skin_host(rest4, idx4, w_b, host)
+        # page-locked host output: written by the kernel directly
+        pinned = torch.zeros((n, 4), dtype=torch.float32).pin_memory()
+        assert L.viper_skin(g.handle, n, C.c_void_p(rest4.ctypes.data), C.c_void_p(idx4.ctypes.data),
+                            C.c_void_p(w_b.ctypes.data), C.c_void_p(pinned.data_ptr())) == 0
         assert g.sync() == 0
         ref_a = g.skin(V.Mesh(dataclasses.replace(sc.mesh, w=w_a.astype(np.float64))))
         ref_b = g.skin(V.Mesh(dataclasses.replace(sc.mesh, w=w_b.astype(np.float64))))
         torch.cuda.synchronize()  # the scene stream included
         np.testing.assert_array_equal(dev_out.cpu().numpy(), ref_a.cpu().numpy())
         np.testing.assert_array_equal(host, ref_b.cpu().numpy())
+        np.testing.assert_array_equal(pinned.numpy(), host)
 
 
 def test_autotune_keeps_results(V):
