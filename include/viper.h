@@ -191,9 +191,10 @@ int viper_set_bones(viper_scene *scene, int n_bones, const float *quat, const fl
  * original rest state.  Rod r's rest lengths become (1 - a_r) times the
  * original ones and its rest radii 1/sqrt(1 - a_r) times theirs (rest volume
  * and mass kept); masses, inertias, rest Darboux vectors and compliances are
- * recomputed in FP64 on the host from the original rest data and uploaded on
- * the scene stream, so the change applies to every step enqueued after the
- * call (also within a viper_batch_step).  The radius scale s in the state is
+ * recomputed in FP64 by a kernel on the scene stream from the original rest
+ * data (kept on the device after the first call; the activations travel
+ * through a page-locked staging array), so the change applies to every step
+ * enqueued after the call (also within a viper_batch_step).  The radius scale s in the state is
  * kept, so a rod's radius s * rbar changes with it.  VIPER_EINVAL for a value
  * outside [0, 0.9] (nothing changed).  The array may be reused on return.
  */
@@ -203,9 +204,13 @@ int viper_set_activation(viper_scene *scene, const float *activation);
  * Linear blend skinning (Sec. 7.4) of n mesh vertices: out = sum_k w_k T_k
  * Tbar_k^-1 rest with segment similarity frames T = [s_m R, c_m] (Eq.
  * shapematch).  rest4 [4n] (x, y, z, unused), idx4 [4n] caller segment ids,
- * w4 [4n], out4 [4n] (x, y, z, 0); all host or device.  Host output makes the
- * call synchronous.  Device arrays must be 16-byte aligned (they are read and
- * written as float4 / int4): VIPER_EINVAL otherwise.
+ * w4 [4n], out4 [4n] (x, y, z, 0); all host or device.  Host operands are
+ * copied to a scene-owned staging buffer on a copy stream, beside the work
+ * still queued on the scene stream; the skinning waits for the copy.  Host
+ * output makes the call synchronous; page-locked host output (cudaHostAlloc,
+ * cudaHostRegister) is written by the kernel directly, other host output is
+ * copied back after it.  Device arrays must be 16-byte aligned (they are read
+ * and written as float4 / int4): VIPER_EINVAL otherwise.
  */
 int viper_skin(viper_scene *scene, int n, const float *rest4, const int *idx4, const float *w4,
                float *out4);
