@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     batch_enter(A, K_EMIT, sb, local, nblk);
     const Params &P = sb.P;
     const Grid G = *P.grid;
+    const int n_chunks = mode > 0 ? *P.n_chunks : 0;  // loaded beside the grid, not after the test
     if (G.pad) return;  // no valid grid: no candidates (uniform over the CTA)
     const int wib = threadIdx.x >> 5;
     const int cells = grid_cells(P.grid, P.table);
@@ -199,11 +200,11 @@ __global__ void __launch_bounds__(32 * kEmitWarpsB) batch_emit_kernel(BatchArgs 
     __shared__ float4 s_cand[kEmitWarpsB][32];  // per warp: the neighbour block being tested
     __shared__ int s_cgrp[kEmitWarpsB][32], s_cid[kEmitWarpsB][32];
     if (mode == 2) {  // a chunk with all its neighbour lists per warp
-        const int n = *P.n_chunks;
+        const int n = n_chunks;
         for (int q = local * kEmitWarpsB + wib; q < n; q += nblk * kEmitWarpsB)
             emit_chunk_all<4>(P, G, q, start, s_cand[wib], s_cgrp[wib], s_cid[wib]);
     } else if (mode == 1) {  // a chunk with one neighbour list per warp
-        const int n = kEmitUnits * *P.n_chunks;
+        const int n = kEmitUnits * n_chunks;
         for (int u = local * kEmitWarpsB + wib; u < n; u += nblk * kEmitWarpsB)
             emit_chunk<4>(P, G, u, start, s_cand[wib], s_cgrp[wib], s_cid[wib]);
     } else {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void grid_scan(const Params &P, int *cnt, int cells, 
     }
     __syncthreads();
     int off = ws[w], coff = ws[16 + w];
-    int2 *chunk_of = P.chunk_of;
+    int4 *chunk_of = P.chunk_of;
     int *cell_start = P.cell_start;
     for (int j = 0; j < m; ++j) {
         const int c = c0 + 32 * j + lane;
@@ -280,7 +281,7 @@ __device__ __forceinline__ void grid_scan(const Params &P, int *cnt, int cells, 
             const int o = off + iv - v, oc = coff + ic - nch;
             cell_start[c] = o;
             cnt[c] = o;
-            for (int h = 0; h < nch; ++h) chunk_of[oc + h] = make_int2(c, h);
+            for (int h = 0; h < nch; ++h) chunk_of[oc + h] = make_int4(c, o + 32 * h, min(o + 32 * h + 32, o + v), o + v);
         }
         off += __shfl_sync(0xffffffffu, iv, 31);
         coff += __shfl_sync(0xffffffffu, ic, 31);

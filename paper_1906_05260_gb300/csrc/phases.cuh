@@ -1070,10 +1070,8 @@ __device__ __forceinline__ void emit_chunk(const Params &P, const Grid &G, int u
 {
     const int lane = threadIdx.x & 31;
     const int k = u % kEmitUnits;
-    const int2 ch = P.chunk_of[u / kEmitUnits];
-    const int c = ch.x;
-    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
-    const int o1 = min(o0 + 32, cend);
+    const int4 ch = P.chunk_of[u / kEmitUnits];
+    const int c = ch.x, o0 = ch.y, o1 = ch.z, cend = ch.w;
     int d0, d1;
     if (k == 13) {  // the own cell from this chunk on: pairs with pb > pa
         d0 = o0;
@@ -1106,10 +1104,8 @@ __device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, i
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const int2 ch = P.chunk_of[q];
-    const int c = ch.x;
-    const int o0 = start(c) + 32 * ch.y, cend = start(c + 1);
-    const int o1 = min(o0 + 32, cend);
+    const int4 ch = P.chunk_of[q];
+    const int c = ch.x, o0 = ch.y, o1 = ch.z, cend = ch.w;
     int d0 = 0, d1 = 0;
     if (lane == 13) {  // the own cell from this chunk on
         d0 = o0;

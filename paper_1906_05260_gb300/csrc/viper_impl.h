@@ -92,7 +92,7 @@ struct Params {
     int *cell_of, *cell_count, *cell_start, *cell_pills;
     float4 *cell_sph;  // bounding spheres in cell order
     int *cell_grp;     // collision groups in cell order
-    int2 *chunk_of;    // pair-search chunks: (cell, chunk of 32 pills), from the one-CTA grid build
+    int4 *chunk_of;    // pair-search chunks of 32 pills: (cell, first, end, cell end) in cell order, from the one-CTA grid build
     int *n_chunks;
     int table;
     Grid *grid;
