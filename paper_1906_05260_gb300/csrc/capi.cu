@@ -749,7 +749,8 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
         if (d->flags & VIPER_FLAG_CONTACTS) {
             size_t cap = (size_t)pair_capacity(d, (int)ns);
             size_t table = (size_t)next_pow2(std::max<long long>(2LL * (long long)ns, 4096));
-            b += 12 * cap + 16 * ns + 4 * (2 * ns) + 4 * (2 * table + 1) + 4 * 4096;
+            b += 20 * cap + 16 * ns + 4 * (2 * ns) + 4 * (2 * table + 1) + 4 * 4096;  // pairs, their vertices, lambda
+            b += 16 * (ns + ns / 32 + 1);  // pair-search chunk records
         }
     }
     return b;
@@ -906,6 +907,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.max_pairs = pills ? pair_capacity(d, ns) : 0;
     P.table = pills ? next_pow2(std::max<long long>(2LL * ns, 4096)) : 1;
     A(P.pairs, pills ? P.max_pairs : 1); A(P.lam_pair, pills ? P.max_pairs : 1); A(P.npairs, 1);
+    A(P.pair_v, pills ? P.max_pairs : 1);
     A(P.spheres, pills ? ns : 1); A(P.bounds, 8); A(P.grid, 1);
     A(P.cell_of, pills ? ns : 1); A(P.cell_pills, pills ? ns : 1);
     A(P.cell_sph, pills ? ns : 1); A(P.cell_grp, pills ? ns : 1);

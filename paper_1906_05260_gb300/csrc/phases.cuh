@@ -969,6 +969,7 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
                             if (idx < P.max_pairs) {
                                 const int a = P.cell_pills[pa], b = P.cell_pills[cb + j0 + t];
                                 P.pairs[idx] = make_int2(min(a, b), max(a, b));
+                                if (P.pair_v) P.pair_v[idx] = make_int2(P.seg_v0[min(a, b)], P.seg_v0[max(a, b)]);
                                 if (P.lam_pair) P.lam_pair[idx] = 0.f;
                             }
                         }
@@ -1031,6 +1032,7 @@ __device__ __forceinline__ void emit_block(const Params &P, int pa, bool own, fl
                             const int a = IDS ? ia : P.cell_pills[pa];
                             const int b = IDS ? ibuf[j0 + t] : P.cell_pills[cb + j0 + t];
                             P.pairs[idx] = make_int2(min(a, b), max(a, b));
+                            if (P.pair_v) P.pair_v[idx] = make_int2(P.seg_v0[min(a, b)], P.seg_v0[max(a, b)]);
                             if (P.lam_pair) P.lam_pair[idx] = 0.f;
                         }
                     }
@@ -1163,7 +1165,10 @@ struct ContactPair {
 __device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair &c)
 {
     const int2 pr = P.pairs[i];
-    const int va = P.seg_v0[pr.x], vb = P.seg_v0[pr.y];
+    // the segments' first vertices, stored beside the pair by the pair search
+    // (one dependent load less on the contact pass's chain)
+    const int2 pv = P.pair_v ? P.pair_v[i] : make_int2(P.seg_v0[pr.x], P.seg_v0[pr.y]);
+    const int va = pv.x, vb = pv.y;
     // the segments' rod origins, loaded beside their first vertices (not through rod_of_v)
     const float4 oa = P.seg_org[pr.x], ob = P.seg_org[pr.y];
     auto wpos = [&](int v, const float4 &o) {

@@ -80,6 +80,7 @@ struct Params {
     float contact_alpha;
     int max_pairs;
     int2 *pairs;
+    int2 *pair_v;  // per pair: the first vertices of its two segments, written with it (NULL: looked up)
     int *npairs;
     float *lam_pair, *lam_plane;
     unsigned long long *acc;
