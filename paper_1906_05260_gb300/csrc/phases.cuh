@@ -1184,9 +1184,10 @@ __device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair
 
 // The update of pair i at contact parameter al; vertices t0, t0 + tstep, ...
 // of the four are accumulated by this thread, and the multiplier is stored if
-// write_lam.
+// write_lam.  With `warp` all 32 lanes handle the same pair (the early return
+// is uniform) and the multiplier is written only after every lane has read it.
 __device__ __forceinline__ void contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
-                                              int tstep, bool write_lam)
+                                              int tstep, bool write_lam, bool warp)
 {
     float be;
     const float C = coll_f(c.Q, al, be);
@@ -1203,6 +1204,7 @@ __device__ __forceinline__ void contact_apply(const Params &P, int i, float at, 
     for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * c.rbar[t] * c.rbar[t];
     const float lam = P.lam_pair[i];
     const float dl = (-C - at * lam) / den;
+    if (warp) __syncwarp();
     if (write_lam) P.lam_pair[i] = lam + dl;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
@@ -1215,7 +1217,7 @@ __device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
 {
     ContactPair c;
     contact_load(P, i, c);
-    contact_apply(P, i, at, c, dichotomous(c.Q), 0, 1, true);
+    contact_apply(P, i, at, c, dichotomous(c.Q), 0, 1, true, false);
 }
 
 // Pair i by one warp (all lanes call): the search four steps per round
@@ -1226,7 +1228,7 @@ __device__ __forceinline__ void contact_pair_warp(const Params &P, int i, float 
     ContactPair c;
     contact_load(P, i, c);
     const float al = dichotomous_warp(c.Q, lane);
-    contact_apply(P, i, at, c, al, lane, 4, lane == 0);
+    contact_apply(P, i, at, c, al, lane, 4, lane == 0, true);
 }
 
 // Half-plane constraints of vertex v's sphere (Sec. 7).
