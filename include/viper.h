@@ -69,11 +69,12 @@ extern "C" {
  * plain solver only (a scene created with it starts there; viper_set_solver to
  * another solver returns VIPER_EINVAL; viper_batch_step steps it with viper_step). */
 #define VIPER_FLAG_VOLUME_VECTOR 32
-/* Contact pass of the batched and multi-scene paths with one thread per pair
- * always.  By default a warp searches each pair (the dichotomous steps four at
- * a time) while the pairs fit the pass's warps (two pairs per warp) and the
- * step's contact passes together occupy at most one CTA per SM; both make the
- * same decisions, so the flag changes timing only. */
+/* Contact pass of the plain, batched and multi-scene paths with one thread
+ * per pair always.  By default a warp searches each pair (the dichotomous
+ * steps four at a time) while the pairs fit the pass's warps (two pairs per
+ * warp) and, in a multi-scene step, the scenes' contact passes together
+ * occupy at most one CTA per SM; both make the same decisions, so the flag
+ * changes timing only. */
 #define VIPER_FLAG_CONTACT_THREADS 64
 
 #define VIPER_SOLVER_PLAIN 0   /* one launch per constraint colour, state in HBM  */

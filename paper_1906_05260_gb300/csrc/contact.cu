@@ -216,9 +216,18 @@ __global__ void contact_kernel(Params P)
     const int np_all = *P.npairs;
     const int np = min(np_all, P.max_pairs);
     if (blockIdx.x == 0 && threadIdx.x == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
-    const int total = np + (P.n_planes > 0 ? P.nv : 0);
+    const int nvp = P.n_planes > 0 ? P.nv : 0;
     const float at = P.contact_alpha * P.inv_h2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int threads = gridDim.x * blockDim.x;
+    if (!P.contact_threads && (long long)np * 16 <= threads) {
+        // few pairs: a warp per pair (at most two per warp), as in the batched pass
+        const int lane = threadIdx.x & 31;
+        for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < np; i += threads >> 5)
+            contact_pair_warp(P, i, at, lane);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nvp; i += threads) contact_planes(P, i, at);
+        return;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nvp; i += threads) {
         if (i < np)
             contact_pair(P, i, at);
         else

@@ -250,15 +250,16 @@ def test_batch_pairs_bit_exact_in_a_large_group(V):
     assert all(o.sync() == 0 for o in objs)
 
 
-def test_contact_warp_search_matches_thread_search_bitwise(V):
-    """The batched contact pass gives each pair a warp while the pairs fit its
-    warps (the dichotomous search four steps per round); with
-    FLAG_CONTACT_THREADS it searches with one thread per pair.  Both make the
-    same decisions on the same values, so the states agree bit for bit."""
+@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+def test_contact_warp_search_matches_thread_search_bitwise(V, solver):
+    """The contact pass gives each pair a warp while the pairs fit its warps
+    (the dichotomous search four steps per round); with FLAG_CONTACT_THREADS
+    it searches with one thread per pair.  Both make the same decisions on the
+    same values, so the states agree bit for bit."""
     sc = S.muscle_rig(mesh_verts=0)
-    a = V.Scene(sc, solver=V.SOLVER_BATCHED, extra_flags=V.FLAG_CONTACT_THREADS)
-    b = V.Scene(sc, solver=V.SOLVER_BATCHED)
-    warps = min(64, -(-sc.ns // 256)) * 8  # the batched contact pass's warps for this scene
+    a = V.Scene(sc, solver=solver, extra_flags=V.FLAG_CONTACT_THREADS)
+    b = V.Scene(sc, solver=solver)
+    warps = min(64, -(-sc.ns // 256)) * 8  # the batched contact pass's warps (the plain pass has more)
     for _ in range(3):
         a.frame(); b.frame()
         assert 0 < len(b.pairs()) <= 2 * warps  # the warp-per-pair branch ran
