@@ -236,12 +236,18 @@ __global__ void __launch_bounds__(32 * kFrameWarps) frame_kernel(Params P, int s
                 const int np_all = PILLS ? *P.npairs : 0;
                 const int np = min(np_all, P.max_pairs);
                 if (PILLS && gtid == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
-                const int total = np + (planes ? P.nv : 0);
-                for (int i = gtid; i < total; i += gthreads) {
-                    if (i < np)
-                        contact_pair(P, i, at);
-                    else
-                        contact_planes(P, i - np, at);
+                const int nvp = planes ? P.nv : 0;
+                if (!P.contact_threads && (long long)np * 16 <= gthreads) {
+                    // few pairs: a warp per pair (all lanes of a warp take the same iterations)
+                    for (int i = gtid >> 5; i < np; i += gthreads >> 5) contact_pair_warp(P, i, at, threadIdx.x & 31);
+                    for (int i = gtid; i < nvp; i += gthreads) contact_planes(P, i, at);
+                } else {
+                    for (int i = gtid; i < np + nvp; i += gthreads) {
+                        if (i < np)
+                            contact_pair(P, i, at);
+                        else
+                            contact_planes(P, i - np, at);
+                    }
                 }
                 if (!grid_barrier(P.bar, nb, P.err)) return;
                 if (owner)
