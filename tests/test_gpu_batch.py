@@ -250,7 +250,7 @@ def test_batch_pairs_bit_exact_in_a_large_group(V):
     assert all(o.sync() == 0 for o in objs)
 
 
-@pytest.mark.parametrize("solver", [0, 1], ids=["plain", "batched"])
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["plain", "batched", "frame"])
 def test_contact_warp_search_matches_thread_search_bitwise(V, solver):
     """The contact pass gives each pair a warp while the pairs fit its warps
     (the dichotomous search four steps per round); with FLAG_CONTACT_THREADS
@@ -259,7 +259,7 @@ def test_contact_warp_search_matches_thread_search_bitwise(V, solver):
     sc = S.muscle_rig(mesh_verts=0)
     a = V.Scene(sc, solver=solver, extra_flags=V.FLAG_CONTACT_THREADS)
     b = V.Scene(sc, solver=solver)
-    warps = min(64, -(-sc.ns // 256)) * 8  # the batched contact pass's warps (the plain pass has more)
+    warps = min(64, -(-sc.ns // 256)) * 8  # the batched contact pass's warps (the others have more)
     for _ in range(3):
         a.frame(); b.frame()
         assert 0 < len(b.pairs()) <= 2 * warps  # the warp-per-pair branch ran
