@@ -54,3 +54,20 @@ def test_oracle_and_library_share_no_code():
     for fn in ("viper.py", "scenes.py", "build.py", "__init__.py"):
         txt = open(os.path.join(ROOT, "paper_1906_05260_gb300", fn)).read()
         assert "import oracle" not in txt and "from oracle" not in txt
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's flag, solver and profiling constants carry the
+    values include/viper.h defines (the binding passes them through as ints)."""
+    text = open(os.path.join(ROOT, "include", "viper.h")).read()
+    defs = dict((k, int(v)) for k, v in re.findall(r"#define\s+VIPER_([A-Z0-9_]+)\s+(-?\d+)", text))
+    from paper_1906_05260_gb300 import viper as V
+    checked = 0
+    for name, value in defs.items():
+        if name.startswith(("FLAG_", "SOLVER_", "PROF_")) and hasattr(V, name):
+            assert getattr(V, name) == value, name
+            checked += 1
+    for name in ("FLAG_CONTACTS", "FLAG_VOLUME", "FLAG_SURFACE_BENDING", "FLAG_JACOBI", "FLAG_WARM_START",
+                 "FLAG_VOLUME_VECTOR", "FLAG_CONTACT_THREADS", "SOLVER_PLAIN", "SOLVER_BATCHED", "SOLVER_FRAME"):
+        assert name in defs and hasattr(V, name), name
+    assert checked >= 10
