@@ -417,6 +417,175 @@ def test_linear_momentum_conserved_without_external_forces():
     np.testing.assert_allclose(p1, p0, atol=1e-12 * max(1.0, np.abs(p0).max()))
 
 
+# --------------------------------------------------------------------------
+# how the solve uses compliance and inertia (Sec. 6 "Correction steps",
+# App. B, App. C): static and dynamic closed forms
+# --------------------------------------------------------------------------
+
+def _straight_rod(n, lbar, r, cs, cb, rho, direction, pins, gravity):
+    """One straight rod of n vertices along `direction`, volume term off (the
+    scales then stay at one), vertices `pins` held at their rest positions."""
+    d = np.asarray(direction, float)
+    d = d / np.linalg.norm(d)
+    pos = np.arange(n)[:, None] * lbar * d[None, :]
+    pins = np.asarray(pins, np.int32)
+    return S.Scene(
+        name="straight", rod_offsets=np.array([0, n], np.int32), rest_pos=pos,
+        rest_quat=np.tile(S.quat_from_z(d), (n - 1, 1)), radius=np.full(n, r), density=np.array([rho]),
+        c_stretch=np.array([cs]), c_bend=np.array([cb]), c_volume=np.array([cs]), group=np.zeros(1, np.int32),
+        gravity=np.asarray(gravity, float), pin_vertex=pins, pin_bone=np.full(len(pins), -1, np.int32),
+        pin_offset=pos[pins], bones=None, planes=np.zeros((0, 4)), contact_compliance=1e-9, contacts=False,
+        volume=False, dt=1 / 60, substeps=1, iterations=1, frames=1)
+
+
+def test_hanging_rod_strain_is_weight_over_stiffness():
+    """Hooke's law in the solve's static limit.  A vertical rod hangs from its
+    pinned top vertex.  Stepping with the velocities cleared after every step
+    (and a fully converged inner solve) drives the state to the minimum of
+    elastic plus gravitational energy.  Segment j then carries the weight of
+    the lumped vertex masses below it: strain_j = g W_j c_s / (pi r^2), the
+    stress over the modulus 1/c_s.  Only a compliance that enters the update as
+    alpha / h^2 reaches this equilibrium (alpha / h would stiffen the rod by a
+    factor 1/h)."""
+    n, lbar, r, cs, rho, g = 8, 0.02, 0.01, 1e-6, 1000.0, 9.81
+    sc = _straight_rod(n, lbar, r, cs, 1e-6, rho, [0, -1, 0], [0], [0, -g, 0])
+    o = oracle.OracleScene(sc)
+    for _ in range(300):
+        assert o.step(dt=1 / 60, substeps=1, iterations=1000) == 0
+        o.set_state(v=np.zeros((n, 3)), sdot=np.zeros(n), w=np.zeros((n - 1, 3)))
+    x = o.get_state()["x"]
+    strain = np.linalg.norm(np.diff(x, axis=0), axis=1) / lbar - 1
+    M = math.pi * r * r * rho * lbar  # segment mass; vertices carry half of each adjacent segment
+    m = np.full(n, M)
+    m[0] = m[-1] = 0.5 * M
+    W = np.array([m[j + 1:].sum() for j in range(n - 1)])
+    expect = g * W * cs / (math.pi * r * r)
+    np.testing.assert_allclose(strain, expect, rtol=1e-4)
+
+
+def _zero_crossings(sig, h):
+    t = []
+    for k in range(1, len(sig)):
+        if (sig[k - 1] < 0) != (sig[k] < 0):
+            t.append(h * (k - 1 + sig[k - 1] / (sig[k - 1] - sig[k])))
+    return np.array(t)
+
+
+def test_twist_oscillation_frequency():
+    """Torsional mode of two segments between three pinned vertices.  The
+    twist part of the bend/twist term stores (pi r^4 / (2 c_b l)) phi^2 / 2 for a
+    relative twist phi, and each segment spins about its axis with inertia
+    M r^2 / 2 (App. B: s^2 m I with I_zz = pi r^4 / 2), so counter-rotating
+    segments oscillate at w = sqrt(2 / (c_b rho)) / l.  The solve is an
+    implicit step, whose phase advances by atan(w h) per step: the measured
+    frequency must be atan(w h) / h.  A factor in the compliance scaling, the
+    twist stiffness or the axial inertia moves it far outside the bound."""
+    lbar, r, cb, rho = 0.05, 0.01, 1e-5, 1000.0
+    sc = _straight_rod(3, lbar, r, 1e-8, cb, rho, [1, 0, 0], [0, 1, 2], np.zeros(3))
+    o = oracle.OracleScene(sc)
+    o.set_state(w=np.array([[-2.0, 0, 0], [2.0, 0, 0]]))
+    h = 1 / 6000
+    sig = []
+    for _ in range(400):
+        assert o.step(dt=h, substeps=1, iterations=4) == 0
+        q = o.get_state()["q"]
+        p = S.quat_mul(q[0] * np.array([-1, -1, -1, 1]), q[1])  # conj(q0) q1: twist about the rod axis
+        sig.append(2 * math.atan2(p[2], p[3]))
+    tc = _zero_crossings(np.array(sig), h)
+    assert len(tc) >= 4
+    w = math.sqrt(2 / (cb * rho)) / lbar
+    np.testing.assert_allclose(math.pi / np.diff(tc).mean(), math.atan(w * h) / h, rtol=5e-5)
+
+
+def test_shear_rocking_frequency():
+    """A single segment between two pinned vertices, turned about an axis
+    across it: the stretch/shear term C = dx / l - d3 stores
+    (pi r^2 l / c_s) psi^2 / 2 for a tilt psi, against the transverse inertia
+    M r^2 / 4, so it rocks at w = sqrt(4 / (c_s rho r^2)); the implicit step
+    advances atan(w h) per step."""
+    lbar, r, cs, rho = 0.05, 0.05, 1e-4, 1000.0
+    sc = _straight_rod(2, lbar, r, cs, 1e-5, rho, [1, 0, 0], [0, 1], np.zeros(3))
+    o = oracle.OracleScene(sc)
+    o.set_state(w=np.array([[0, 0.5, 0]]))
+    w = math.sqrt(4 / (cs * rho * r * r))
+    h = 2 * math.pi / w / 200
+    sig = []
+    for _ in range(800):
+        assert o.step(dt=h, substeps=1, iterations=4) == 0
+        d3 = S.quat_rotate(o.get_state()["q"][0], np.array([0, 0, 1.0]))
+        sig.append(math.atan2(-d3[2], d3[0]))
+    tc = _zero_crossings(np.array(sig), h)
+    assert len(tc) >= 6
+    np.testing.assert_allclose(math.pi / np.diff(tc).mean(), math.atan(w * h) / h, rtol=5e-5)
+
+
+def _planar_scene(n_rods=3, n=6, lbar=0.01, r=0.012, seed=5):
+    """Rods curved in the xy-plane (rest frames from the tangents, so one
+    frame axis is +-z): planar motion stays planar."""
+    rng = np.random.default_rng(seed)
+    pos, quat = [], []
+    for k in range(n_rods):
+        ang = np.cumsum(np.r_[rng.uniform(0, 2 * math.pi), rng.uniform(-0.5, 0.5, n - 2)])
+        d = np.stack([np.cos(ang), np.sin(ang), np.zeros(n - 1)], 1)
+        pos.append(np.vstack([np.zeros(3), np.cumsum(lbar * d, 0)]) + np.array([0.04 * k, 0.01 * k, 0]))
+        quat.append(S.quat_from_z(d))
+    return S.Scene(
+        name="planar", rod_offsets=np.arange(n_rods + 1, dtype=np.int32) * n, rest_pos=np.concatenate(pos),
+        rest_quat=np.concatenate(quat), radius=np.full(n_rods * n, r), density=np.full(n_rods, 1000.0),
+        c_stretch=np.full(n_rods, 1e-6), c_bend=np.full(n_rods, 1e-6), c_volume=np.full(n_rods, 1e-6),
+        group=np.arange(n_rods, dtype=np.int32), gravity=np.zeros(3),
+        pin_vertex=np.zeros(0, np.int32), pin_bone=np.zeros(0, np.int32), pin_offset=np.zeros((0, 3)),
+        bones=None, planes=np.zeros((0, 4)), contact_compliance=1e-9, contacts=False, volume=True,
+        dt=1 / 60, substeps=10, iterations=4, frames=1)
+
+
+def _angular_momentum(sc, st):
+    """sum m_i x_i x v_i + sum_j I_j w_j with the closed-form inertias: vertex
+    masses lumped from M_j = pi r_m^2 rho l_j, segment inertia
+    s_m^2 R diag(M r_m^2 / 4, M r_m^2 / 4, M r_m^2 / 2) R^T (App. B)."""
+    x, v, q, w, s = st["x"], st["v"], st["q"], st["w"], st["s"]
+    L = np.zeros(3)
+    g = 0
+    for r in range(sc.n_rods):
+        for j in range(sc.rod_offsets[r], sc.rod_offsets[r + 1] - 1):
+            lj = np.linalg.norm(sc.rest_pos[j + 1] - sc.rest_pos[j])
+            rm = 0.5 * (sc.radius[j] + sc.radius[j + 1])
+            Mj = math.pi * rm * rm * sc.density[r] * lj
+            L += 0.5 * Mj * (np.cross(x[j], v[j]) + np.cross(x[j + 1], v[j + 1]))
+            R = np.stack([S.quat_rotate(q[g], e) for e in np.eye(3)], 1)
+            sm = 0.5 * (s[j] + s[j + 1])
+            I = sm * sm * Mj * rm * rm * (R @ np.diag([0.25, 0.25, 0.5]) @ R.T)
+            L += I @ w[g]
+            g += 1
+    return L
+
+
+def test_angular_momentum_conserved_in_planar_motion():
+    """Without gravity, pins or contacts every constraint is invariant under
+    rotations, so each update changes sum m x dx + sum I dtheta by zero: the
+    angular momentum counted with the closed-form inertias is conserved.  The
+    motion is kept planar (velocities in the plane, spins about its normal, a
+    principal axis of every segment), because the paper's prediction carries
+    the angular velocity without a gyroscopic term and so does not conserve
+    the momentum of spins about non-principal axes.  Counting the spin with
+    half or twice the transverse inertia breaks the balance by > 15 %."""
+    sc = _planar_scene()
+    o = oracle.OracleScene(sc)
+    rng = np.random.default_rng(3)
+    st = o.get_state()
+    v = rng.normal(scale=0.02, size=st["v"].shape)
+    v[:, 2] = 0
+    w = np.zeros(st["w"].shape)
+    w[:, 2] = rng.normal(scale=5.0, size=len(w))
+    o.set_state(v=v, w=w)
+    L0 = _angular_momentum(sc, o.get_state())
+    spin0 = L0 - _angular_momentum(sc, dict(o.get_state(), w=np.zeros_like(w)))
+    assert np.linalg.norm(spin0) > 0.2 * np.linalg.norm(L0)  # the spins carry a real share
+    for _ in range(10):
+        assert o.step() == 0
+    L1 = _angular_momentum(sc, o.get_state())
+    assert np.linalg.norm(L1 - L0) < 1e-3 * np.linalg.norm(L0)
+
 def test_contact_conserves_momentum_and_separates():
     """Two crossing two-vertex rods driven into each other (g = 0, no pins):
     the contact keeps total momentum and leaves the pills non-penetrating."""
