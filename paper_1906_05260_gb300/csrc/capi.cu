@@ -750,6 +750,7 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
             size_t cap = (size_t)pair_capacity(d, (int)ns);
             size_t table = (size_t)next_pow2(std::max<long long>(2LL * (long long)ns, 4096));
             b += 20 * cap + 16 * ns + 4 * (2 * ns) + 4 * (2 * table + 1) + 4 * 4096;  // pairs, their vertices, lambda
+            b += 4 * (kBoundsWords + (size_t)broadphase_big_cap((int)ns));  // radius histogram, oversized pills
             b += 16 * (ns + ns / 32 + 1);  // pair-search chunk records
         }
     }
@@ -908,7 +909,10 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     P.table = pills ? next_pow2(std::max<long long>(2LL * ns, 4096)) : 1;
     A(P.pairs, pills ? P.max_pairs : 1); A(P.lam_pair, pills ? P.max_pairs : 1); A(P.npairs, 1);
     A(P.pair_v, pills ? P.max_pairs : 1);
-    A(P.spheres, pills ? ns : 1); A(P.bounds, 8); A(P.grid, 1);
+    A(P.spheres, pills ? ns : 1); A(P.bounds, kBoundsWords); A(P.grid, 1);
+    P.bp_hist = reinterpret_cast<int *>(P.bounds + 8);
+    P.big_cap = broadphase_big_cap(ns);
+    A(P.big_list, pills ? P.big_cap : 1);
     A(P.cell_of, pills ? ns : 1); A(P.cell_pills, pills ? ns : 1);
     A(P.cell_sph, pills ? ns : 1); A(P.cell_grp, pills ? ns : 1);
     // at most one chunk per occupied cell plus one per 32 pills

@@ -3,7 +3,11 @@
 // Broadphase (Sec. 7.1): every pill (segment) is bounded by a sphere; sphere
 // centres are binned into a uniform grid whose cell width is the diameter of
 // the largest bounding sphere (slightly enlarged so rounding cannot separate
-// an overlapping pair by more than one cell).  The grid is built with a
+// an overlapping pair by more than one cell) -- of the largest one below a cut
+// that leaves at most big_cap oversized pills out of the cells, which are then
+// paired from their own side against the cells in their reach and against
+// each other (a stretched outlier would otherwise coarsen the whole grid).
+// The grid is built with a
 // count / exclusive-scan / scatter pass that also copies each pill's sphere
 // and group into cell order.  Candidate pairs are then built in parallel (the
 // paper's extension of Green's particle grid): one warp per cell holds the
@@ -24,25 +28,55 @@
 
 namespace viper {
 
-// bounds zeroed before (see merge_bounds)
-__global__ void bp_bounds_kernel(Params P)
+// Bounding spheres, their bounds and the histogram of their radii (the
+// kBoundsWords bounds words are zeroed before; see merge_bounds, choose_cut).
+constexpr int kBpThreads = 256;  // choose_cut takes two histogram bins per thread
+__global__ void __launch_bounds__(kBpThreads) bp_bounds_kernel(Params P)
 {
+    __shared__ int hist[kRadBins];
+    for (int b = threadIdx.x; b < kRadBins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.f;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x)
-        bound_pill(P, g, mn, mx, mr);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
+        const float4 sp = bp_sphere(P, g);
+        P.spheres[g] = sp;
+        mn[0] = fminf(mn[0], sp.x); mn[1] = fminf(mn[1], sp.y); mn[2] = fminf(mn[2], sp.z);
+        mx[0] = fmaxf(mx[0], sp.x); mx[1] = fmaxf(mx[1], sp.y); mx[2] = fmaxf(mx[2], sp.z);
+        mr = fmaxf(mr, sp.w);
+        atomicAdd(hist + rad_bin(sp.w), 1);
+    }
     merge_bounds(P, mn, mx, mr);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kRadBins; b += blockDim.x)
+        if (hist[b]) atomicAdd(P.bp_hist + b, hist[b]);
 }
 
-__global__ void bp_count_kernel(Params P)
+// Grid for this substep (the cut radius from the histogram, the same in every
+// block); pills above the cut go to the oversized list instead of a cell.
+__global__ void __launch_bounds__(kBpThreads) bp_count_kernel(Params P)
 {
+    __shared__ int sh[kRadBins + 33];
+    float r_cut;
+    const int b_cut = choose_cut(P.bp_hist, P.big_cap, ord_dec(P.bounds[6]), sh, &r_cut);
     bool ok;
-    Grid G = make_grid(P, ok);
+    const Grid G = make_grid_from(P.bounds, P.table, ok, r_cut, b_cut);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *P.grid = G;
         *P.npairs = 0;  // pair cursor of bp_emit_kernel
         if (!ok) atomicOr(P.err, ERR_NONFINITE);
     }
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) count_pill(P, G, g);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
+        const float4 sp = P.spheres[g];
+        if (rad_bin(sp.w) > G.b_cut) {
+            P.cell_of[g] = -1;
+            const int slot = atomicAdd(P.bp_hist + kRadBins, 1);
+            if (slot < P.big_cap) P.big_list[slot] = g;
+        } else {
+            const int cell = bp_cell(G, sp);
+            P.cell_of[g] = cell;
+            atomicAdd(P.cell_count + cell, 1);
+        }
+    }
 }
 
 // cell_count is returned to zero here (each pill takes one slot), ready for the next substep
@@ -50,22 +84,30 @@ __global__ void bp_scatter_kernel(Params P)
 {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.ns; g += gridDim.x * blockDim.x) {
         const int cell = P.cell_of[g];
-        scatter_pill(P, g, cell, P.cell_start[cell]);
+        if (cell >= 0) scatter_pill(P, g, cell, P.cell_start[cell]);
     }
 }
 
+// Pair search: the work list is kEmitUnits units per cell (emit_cell) followed
+// by one unit per oversized pill (emit_big), one warp per unit.
 constexpr int kEmitWarps = 8;
 __global__ void __launch_bounds__(32 * kEmitWarps) bp_emit_kernel(Params P)
 {
     const Grid G = *P.grid;
     if (G.pad) return;  // no valid grid: no candidates
-    const int wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * kEmitWarps;
     const int cells = grid_cells(P.grid, P.table);
+    const int nb = min(P.bp_hist[kRadBins], P.big_cap);
+    const int units = kEmitUnits * cells;
     const int *cs = P.cell_start;
     auto start = [cs](int c) { return cs[c]; };
-    for (int u = blockIdx.x * kEmitWarps + wib; u < kEmitUnits * cells; u += nwarps)
-        emit_cell<4>(P, G, u, start);
+    for (int u = blockIdx.x * kEmitWarps + wib; u < units + nb; u += nwarps) {
+        if (u < units)
+            emit_cell<4>(P, G, u, start);
+        else
+            emit_big(P, G, u - units, nb, lane);
+    }
 }
 
 // ---------------------------------------------------------------- exclusive scan
@@ -184,14 +226,14 @@ static void scan(viper_scene *s, cudaStream_t st, int *tmp, const int *in, int n
 void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s)
 {
     const int grid = (P.ns + 255) / 256 < 4 * device_sm_count() ? (P.ns + 255) / 256 + 1 : 4 * device_sm_count();
-    cudaMemsetAsync(P.bounds, 0, 8 * sizeof(unsigned int), st);
+    cudaMemsetAsync(P.bounds, 0, kBoundsWords * sizeof(unsigned int), st);
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_bounds_kernel<<<grid, 256, 0, st>>>(P);
+        bp_bounds_kernel<<<grid, kBpThreads, 0, st>>>(P);
     }
     {
         ProfScope ps(s, PROF_BROADPHASE);
-        bp_count_kernel<<<grid, 256, 0, st>>>(P);
+        bp_count_kernel<<<grid, kBpThreads, 0, st>>>(P);
     }
     scan(s, st, scan_tmp, P.cell_count, P.table, P.cell_start, P.grid);
     {
@@ -211,38 +253,53 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
 void launch_broadphase(viper_scene *s) { broadphase_enqueue(s->P, s->ls, s->d_scan_tmp, s); }
 
 // ---------------------------------------------------------------- contact pass
-__global__ void contact_kernel(Params P)
+constexpr int kContactThreads = 256;
+__global__ void __launch_bounds__(kContactThreads) contact_kernel(Params P)
 {
+    __shared__ int queue[kContactThreads / 32][64];
     const int np_all = *P.npairs;
     const int np = min(np_all, P.max_pairs);
     if (blockIdx.x == 0 && threadIdx.x == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
     const int nvp = P.n_planes > 0 ? P.nv : 0;
     const float at = P.contact_alpha * P.inv_h2;
     const int threads = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
     if (!P.contact_threads && (long long)np * 16 <= threads) {
         // few pairs: a warp per pair (at most two per warp), as in the batched pass
-        const int lane = threadIdx.x & 31;
         for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < np; i += threads >> 5)
             contact_pair_warp(P, i, at, lane);
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nvp; i += threads) contact_planes(P, i, at);
-        return;
+    } else {
+        // many pairs: a thread per pair, the pairs that may touch compacted per warp
+        contact_pairs_compacted(P, np, at, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threads >> 5,
+                                queue[threadIdx.x >> 5], lane);
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nvp; i += threads) {
-        if (i < np)
-            contact_pair(P, i, at);
-        else
-            contact_planes(P, i - np, at);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nvp; i += threads) contact_planes(P, i, at);
+}
+
+// CTAs of the contact pass: as many as stay resident (grid-stride loops inside)
+static int contact_grid(int cap)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contact_kernel, kContactThreads, 0) != cudaSuccess ||
+            n < 1) {
+            cudaGetLastError();
+            n = 2;
+        }
+        per_sm = n;
     }
+    int grid = (cap + kContactThreads - 1) / kContactThreads;
+    if (grid > per_sm * device_sm_count()) grid = per_sm * device_sm_count();
+    return grid < 1 ? 1 : grid;
 }
 
 void launch_contacts(viper_scene *s)
 {
     const int cap = s->P.max_pairs + (s->P.n_planes > 0 ? s->P.nv : 0);
-    int grid = (cap + 255) / 256;
-    if (grid > 2 * device_sm_count()) grid = 2 * device_sm_count();
-    if (grid < 1) grid = 1;
+    const int grid = contact_grid(cap);
     ProfScope ps(s, PROF_CONTACT);
-    contact_kernel<<<grid, 256, 0, s->ls>>>(s->P);
+    contact_kernel<<<grid, kContactThreads, 0, s->ls>>>(s->P);
     s->launches++;
 }
 

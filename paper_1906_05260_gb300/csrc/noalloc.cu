@@ -1,14 +1,16 @@
 // noalloc.cu -- allocation-free variant of the stand-alone broadphase query.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// query: code running while a CUDA graph is being captured (where
-// cudaMalloc/cudaFree are not permitted), real-time loops that must not
-// block on the allocator, and hosts whose device memory belongs to another
-// allocator that this library cannot call into.  viper_broadphase_noalloc
-// serves them: it runs the same kernels as viper_broadphase, but its scratch
-// lives in one fixed, file-scope device array instead of a per-call
-// allocation.  It never calls cudaMalloc, cudaMallocAsync, cudaFree or any
-// other allocating routine.
+// query: real-time loops with a fixed per-frame budget (cudaMalloc and a
+// growing stream-ordered pool can block or synchronise the device for an
+// unbounded time), and hosts whose device memory is owned by another
+// allocator (a framework's caching allocator, an engine's memory manager)
+// that this library cannot call into.  viper_broadphase_noalloc serves them:
+// it runs the same kernels as viper_broadphase, but its scratch lives in one
+// fixed, file-scope device array instead of a per-call allocation.  It never
+// calls cudaMalloc, cudaMallocAsync, cudaFree or any other allocating routine.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "viper_device.cuh"
@@ -33,7 +35,8 @@ constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kTable = 131072;
 constexpr size_t kScratchBytes = 2 * round256(16 * (size_t)kMaxSegments) + 5 * round256(4 * (size_t)kMaxSegments) +
                                  round256(4 * kTable) + round256(4 * (kTable + 1)) + round256(4 * 4096) +
-                                 round256(sizeof(unsigned int) * 8 + sizeof(Grid) + 4 * sizeof(int));
+                                 round256(sizeof(unsigned int) * kBoundsWords + sizeof(Grid) + 4 * sizeof(int)) +
+                                 round256(4 * (size_t)(kMaxSegments / 16));
 
 // The scratch itself: every GPU that loads this library holds these ~4.3 MiB
 // until the process exits.  In host code the symbol is only a host-side
@@ -42,9 +45,48 @@ constexpr size_t kScratchBytes = 2 * round256(16 * (size_t)kMaxSegments) + 5 * r
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_addr[64] = {nullptr};
 
-// Device address of g_scratch on the current device, looked up once per device.
+// The array's device address is looked up once per device and CUDA context:
+// a context created after a device reset holds the array at another address.
+struct ScratchSlot {
+    unsigned long long ctx = 0;  // cuCtxGetId of the context the address belongs to
+    void *addr = nullptr;
+};
+ScratchSlot g_slot[64];
+
+// Identifier of the calling thread's current CUDA context (unique for the
+// life of the process), or 0 when there is none or the driver cannot say.
+// The two driver functions are reached through the runtime's entry-point
+// query, so the library needs no link against the driver library.
+unsigned long long current_context_id()
+{
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_scratch on the current device and context.  The first
+// call of a context looks it up (cudaGetSymbolAddress, with that device
+// current); later calls reuse it.
 int scratch_address(void **out)
 {
     int dev = 0;
@@ -53,15 +95,19 @@ int scratch_address(void **out)
         return VIPER_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    ScratchSlot &e = g_slot[dev];
+    unsigned long long ctx = current_context_id();
+    if (!e.addr || !ctx || e.ctx != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return VIPER_ECUDA;
         }
-        g_addr[dev] = p;
+        if (!ctx) ctx = current_context_id();  // the lookup may have created the device's primary context
+        e.addr = p;
+        e.ctx = ctx;
     }
-    *out = g_addr[dev];
+    *out = e.addr;
     return VIPER_OK;
 }
 

@@ -722,10 +722,13 @@ __device__ __forceinline__ float ord_dec(unsigned int u)
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// Grid from the bounds: cell = 2 R_max (1 + 2^-8); grown until the dense grid
+// Grid from the bounds: cell = 2 r_cut (1 + 2^-8) with r_cut the largest
+// bounding radius (or, in the multi-kernel broadphase, the cut radius below
+// which all but a bounded number of pills lie); grown until the dense grid
 // fits the table and spans at most 4096 cells per axis.  Non-finite bounds
 // (a diverged state) give an empty grid and raise the non-finite flag.
-__device__ __forceinline__ Grid make_grid_from(const unsigned int *bounds, int table, bool &ok)
+__device__ __forceinline__ Grid make_grid_from(const unsigned int *bounds, int table, bool &ok, float r_cut = -1.f,
+                                               int b_cut = kRadBins - 1)
 {
     Grid G;
     float lo[3], hi[3];
@@ -735,7 +738,10 @@ __device__ __forceinline__ Grid make_grid_from(const unsigned int *bounds, int t
         hi[c] = ord_dec(bounds[3 + c]);
         ok = ok && isfinite(lo[c]) && isfinite(hi[c]) && hi[c] >= lo[c];
     }
-    float cell = 2.f * ord_dec(bounds[6]) * 1.00390625f;
+    if (!(r_cut >= 0.f)) r_cut = ord_dec(bounds[6]);
+    G.r_cut = r_cut;
+    G.b_cut = b_cut;
+    float cell = 2.f * r_cut * 1.00390625f;
     ok = ok && isfinite(cell);
     if (!ok) {
         for (int c = 0; c < 3; ++c) {
@@ -870,6 +876,48 @@ __device__ __forceinline__ void merge_bounds(const Params &P, float mn[3], float
     merge_bounds_to(P.bounds, mn, mx, mr);
 }
 
+// ---------------------------------------------------------------- oversized pills
+// One pill far longer than the rest (a segment stretched by an impact) would
+// set the cell of the whole grid through the largest bounding radius and put
+// thousands of pills in each cell.  The multi-kernel broadphase therefore
+// histograms the radii (16 bins per octave: the float's exponent and top four
+// mantissa bits) and sizes the cell for the cut radius below which all but at
+// most big_cap pills lie; the pills above it stay out of the cells and are
+// paired from their own side (bp_big_kernel).  The pair set is unchanged:
+// every candidate is still decided by spheres_overlap.
+constexpr unsigned int kRadBinBase = (127u - 20u) << 4;  // bin 0 starts at 2^-20
+__device__ __forceinline__ int rad_bin(float R)
+{
+    const int b = (int)(__float_as_uint(R) >> 19) - (int)kRadBinBase;
+    return min(max(b, 0), kRadBins - 1);
+}
+// Upper edge of bin b (exclusive): every radius of bins <= b is below it.
+__device__ __forceinline__ float rad_bin_top(int b) { return __uint_as_float(((unsigned)b + 1u + kRadBinBase) << 19); }
+
+// Cut bin from the histogram, by every thread of a 256-thread block (the same
+// result in every block): the smallest b such that bins above b hold at most
+// `cap` pills.  Returns b_cut; *r_cut = the top edge of bin b_cut, or the
+// largest radius when no pill lies above it.  sh: kRadBins + 33 ints of shared memory.
+__device__ __forceinline__ int choose_cut(const int *hist, int cap, float r_max, int *sh, float *r_cut)
+{
+    int *h = sh, *ws = sh + kRadBins;
+    const int t = threadIdx.x;  // bins 511 - 2t and 510 - 2t (suffix sums from the top)
+    const int b0 = kRadBins - 1 - 2 * t, b1 = b0 - 1;
+    const int h0 = hist[b0], h1 = hist[b1];
+    int tot;
+    const int above = block_excl_scan(h0 + h1, ws, &tot);  // pills in bins > b0
+    h[b0] = above;            // pills in bins > b0
+    h[b1] = above + h0;       // pills in bins > b1
+    __syncthreads();
+    // bins b with (pills above b) <= cap form a top range [b_cut, kRadBins); its size
+    const int n_ok = __syncthreads_count(h[b0] <= cap) + __syncthreads_count(h[b1] <= cap);
+    const int b_cut = max(kRadBins - n_ok, 0);
+    const bool none_above = h[b_cut] == 0;
+    __syncthreads();
+    *r_cut = none_above ? r_max : rad_bin_top(b_cut);
+    return none_above ? kRadBins - 1 : b_cut;
+}
+
 __device__ __forceinline__ void count_pill(const Params &P, const Grid &G, int g)
 {
     const int cell = bp_cell(G, P.spheres[g]);
@@ -977,6 +1025,75 @@ __device__ __forceinline__ void emit_cell(const Params &P, const Grid &G, int u,
                 }
             }
         }
+    }
+}
+
+// Writes the warp's hits (lane: pair (a, b) when `hit`) as (lower id, higher
+// id) with their segments' first vertices and zero multipliers, reserving the
+// output slots with one atomic.  Every lane of the warp calls it.
+__device__ __forceinline__ void emit_warp_hits(const Params &P, bool hit, int a, int b, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned hm = __ballot_sync(full, hit);
+    if (!hm) return;
+    int out = 0;
+    if (lane == 0) out = atomicAdd(P.npairs, __popc(hm));
+    out = __shfl_sync(full, out, 0);
+    if (hit) {
+        const int idx = out + __popc(hm & ((1u << lane) - 1u));
+        if (idx < P.max_pairs) {
+            const int lo = min(a, b), hi = max(a, b);
+            P.pairs[idx] = make_int2(lo, hi);
+            if (P.pair_v) P.pair_v[idx] = make_int2(P.seg_v0[lo], P.seg_v0[hi]);
+            if (P.lam_pair) P.lam_pair[idx] = 0.f;
+        }
+    }
+}
+
+// Candidate pairs of oversized pill i of the list (bounding radius above the
+// grid's cut), by one warp: (1) against the pills in the cells of the box
+// centre +- (R_i + r_cut)(1 + 2^-8) -- a grid pill overlapping pill i has its
+// centre within R_i + r_cut, and the enlargement covers the rounding of the
+// box corners -- tested 32 at a time from the cell-order copies; (2) against
+// the oversized pills after i in the list, so that each pair is found once.
+__device__ __forceinline__ void emit_big(const Params &P, const Grid &G, int i, int nb, int lane)
+{
+    const int gi = P.big_list[i];
+    const float4 si = P.spheres[gi];
+    const int grp = P.seg_group[gi];
+    const float reach = __fmul_rn(__fadd_rn(si.w, G.r_cut), 1.00390625f);
+    const float c[3] = {si.x, si.y, si.z};
+    int lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = cell_coord(__fsub_rn(c[k], reach), G.lo[k], G.inv_cell, G.dim[k]);
+        hi[k] = cell_coord(__fadd_rn(c[k], reach), G.lo[k], G.inv_cell, G.dim[k]);
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            // the cells x = lo .. hi of one row are contiguous in cell order
+            const int row = G.dim[0] * (y + G.dim[1] * z);
+            const int p0 = P.cell_start[row + lo[0]], p1 = P.cell_start[row + hi[0] + 1];
+            for (int pb = p0; pb < p1; pb += 32) {
+                const int q = pb + lane;
+                bool hit = false;
+                int b = 0;
+                if (q < p1) {
+                    hit = P.cell_grp[q] != grp && spheres_overlap(si, P.cell_sph[q]);
+                    if (hit) b = P.cell_pills[q];
+                }
+                emit_warp_hits(P, hit, gi, b, lane);
+            }
+        }
+    for (int j0 = i + 1; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        int b = 0;
+        if (j < nb) {
+            b = P.big_list[j];
+            hit = P.seg_group[b] != grp && spheres_overlap(si, P.spheres[b]);
+        }
+        emit_warp_hits(P, hit, gi, b, lane);
     }
 }
 
@@ -1212,11 +1329,32 @@ __device__ __forceinline__ void contact_apply(const Params &P, int i, float at, 
             acc_add(P, c.vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * c.rbar[t] * dl);
 }
 
+// Certified early-out of the narrowphase.  The distance D of the two axis
+// segments is at least the gap between their projections on the line through
+// their midpoints, |e| - (|e.da| + |e.db|) / (2 |e|) (e = ma - mb).  Every probe
+// of the search evaluates C = |pa - pb| - ra - rb >= D - max(ra) - max(rb), so
+// when the gap exceeds the larger radius of each pill by a margin (1e-3 of the
+// radii plus 1e-5 of the coordinates' magnitude, far above the FP32 rounding
+// of either computation) the search could only find C > 0: the pair is
+// inactive and skipping it changes no result.  Returns false in that case.
+__device__ __forceinline__ bool contact_may_touch(const PillPair &Q)
+{
+    const V3 ma = 0.5f * (Q.a1 + Q.a2), mb = 0.5f * (Q.b1 + Q.b2);
+    const V3 e = ma - mb, da = Q.a2 - Q.a1, db = Q.b2 - Q.b1;
+    const float d2 = dot(e, e), el = sqrtf(d2);
+    const float rho = fmaxf(Q.ra1, Q.ra2) + fmaxf(Q.rb1, Q.rb2);
+    const float mag = fmaxf(fmaxf(fmaxf(fabsf(ma.x), fabsf(ma.y)), fmaxf(fabsf(ma.z), fabsf(mb.x))),
+                            fmaxf(fabsf(mb.y), fabsf(mb.z)));
+    const float margin = 1e-3f * rho + 1e-5f * mag;
+    return !(d2 - 0.5f * (fabsf(dot(e, da)) + fabsf(dot(e, db))) > (rho + margin) * el);
+}
+
 // Pair i by one thread.
 __device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
 {
     ContactPair c;
     contact_load(P, i, c);
+    if (!contact_may_touch(c.Q)) return;
     contact_apply(P, i, at, c, dichotomous(c.Q), 0, 1, true, false);
 }
 
@@ -1227,8 +1365,51 @@ __device__ __forceinline__ void contact_pair_warp(const Params &P, int i, float 
 {
     ContactPair c;
     contact_load(P, i, c);
+    if (!contact_may_touch(c.Q)) return;  // uniform over the warp
     const float al = dichotomous_warp(c.Q, lane);
     contact_apply(P, i, at, c, al, lane, 4, lane == 0, true);
+}
+
+// Pairs [0, np) a thread each, by the calling warp from chunk `chunk` of 32
+// pairs on, every `stride`-th chunk.  The pairs that may touch
+// (contact_may_touch) are queued in the warp's buffer q (64 ints of shared
+// memory) and searched 32 at a time, so that the search runs on full warps
+// however sparse the touching pairs are.  Same results as contact_pair.
+__device__ __forceinline__ void contact_pairs_compacted(const Params &P, int np, float at, int chunk, int stride,
+                                                        int *q, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    int qn = 0;  // queued pairs (uniform over the warp)
+    for (int base = chunk * 32; base < np; base += stride * 32) {
+        const int i = base + lane;
+        bool maybe = false;
+        if (i < np) {
+            ContactPair c;
+            contact_load(P, i, c);
+            maybe = contact_may_touch(c.Q);
+        }
+        const unsigned m = __ballot_sync(full, maybe);
+        if (maybe) q[qn + __popc(m & ((1u << lane) - 1u))] = i;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            const int j = q[lane];
+            ContactPair c;
+            contact_load(P, j, c);
+            contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+            __syncwarp();
+            qn -= 32;
+            if (lane < qn) q[lane] = q[lane + 32];
+            __syncwarp();
+        }
+    }
+    if (lane < qn) {
+        const int j = q[lane];
+        ContactPair c;
+        contact_load(P, j, c);
+        contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+    }
+    __syncwarp();
 }
 
 // Half-plane constraints of vertex v's sphere (Sec. 7).

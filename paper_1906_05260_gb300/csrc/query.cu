@@ -42,9 +42,11 @@ size_t broadphase_scratch_layout(int ns, int table, size_t off[kBpSections])
                                     4 * (size_t)table,         // cell_count (zero between calls)
                                     4 * ((size_t)table + 1),   // cell_start
                                     4 * 4096,                  // scan tile sums
-                                    sizeof(unsigned int) * 8 + sizeof(Grid) + 4 * sizeof(int),  // bounds, grid, err
+                                    // bounds and radius histogram, grid, err
+                                    sizeof(unsigned int) * kBoundsWords + sizeof(Grid) + 4 * sizeof(int),
                                     16 * (size_t)ns,           // spheres in cell order
-                                    4 * (size_t)ns};           // groups in cell order
+                                    4 * (size_t)ns,            // groups in cell order
+                                    4 * (size_t)broadphase_big_cap(ns)};  // oversized pills
     size_t o = 0;
     for (int k = 0; k < kBpSections; ++k) {
         off[k] = o;
@@ -80,10 +82,13 @@ void broadphase_params(Params &P, char *base, const size_t off[kBpSections], int
     P.cell_count = reinterpret_cast<int *>(base + off[5]);
     P.cell_start = reinterpret_cast<int *>(base + off[6]);
     P.bounds = reinterpret_cast<unsigned int *>(base + off[8]);
-    P.grid = reinterpret_cast<Grid *>(base + off[8] + 32);
-    P.err = reinterpret_cast<int *>(base + off[8] + 32 + sizeof(Grid));
+    P.bp_hist = reinterpret_cast<int *>(P.bounds + 8);
+    P.grid = reinterpret_cast<Grid *>(base + off[8] + 4 * kBoundsWords);
+    P.err = reinterpret_cast<int *>(base + off[8] + 4 * kBoundsWords + sizeof(Grid));
     P.cell_sph = reinterpret_cast<float4 *>(base + off[9]);
     P.cell_grp = reinterpret_cast<int *>(base + off[10]);
+    P.big_list = reinterpret_cast<int *>(base + off[11]);
+    P.big_cap = broadphase_big_cap(P.ns);
     P.table = table;
     P.pairs = reinterpret_cast<int2 *>(pairs);
     P.max_pairs = max_pairs;

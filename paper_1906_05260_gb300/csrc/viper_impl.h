@@ -18,12 +18,24 @@ enum : int { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
 // vertices 2p+1, 2p+2 (when they exist).
 
 // Uniform grid of the broadphase, recomputed on the device every substep.
+// r_cut: pills with a larger bounding radius are kept out of the cells and
+// searched from their own side (the multi-kernel broadphase); elsewhere the
+// largest radius.  b_cut: the radius-histogram bin of r_cut (kRadBins - 1: none).
 struct Grid {
     float lo[3];
     float inv_cell;
     int dim[3];
     int pad;
+    float r_cut;
+    int b_cut;
 };
+
+// Bounding-radius histogram of the multi-kernel broadphase: 16 bins per octave
+// over 2^-20 .. 2^12 (radii outside clamp to the end bins).  It sits behind
+// the 8 bounds words, followed by the count of oversized pills; kBoundsWords
+// words in all are cleared before every broadphase.
+constexpr int kRadBins = 512;
+constexpr int kBoundsWords = 8 + kRadBins + 8;
 
 // Kernel arguments shared by every kernel (passed by value).
 struct Params {
@@ -89,7 +101,10 @@ struct Params {
     const float *bp_rbar;
     int bp_rbar_stride;
     float4 *spheres;
-    unsigned int *bounds;
+    unsigned int *bounds;  // kBoundsWords: bounds, radius histogram (bp_hist), oversized-pill count
+    int *bp_hist;          // = bounds + 8
+    int *big_list;         // oversized pills of this substep (at most big_cap)
+    int big_cap;
     int *cell_of, *cell_count, *cell_start, *cell_pills;
     float4 *cell_sph;  // bounding spheres in cell order
     int *cell_grp;     // collision groups in cell order
@@ -104,7 +119,11 @@ struct Params {
 constexpr int kSlotLam = 24;
 
 // Sections of the scene-free broadphase scratch (query.cu).
-constexpr int kBpSections = 11;
+constexpr int kBpSections = 12;
+
+// Capacity of the oversized-pill list for ns pills (the grid cell is chosen so
+// that at most this many pills lie above it).
+inline int broadphase_big_cap(int ns) { return ns / 16 > 256 ? ns / 16 : 256; }
 
 struct Alloc {
     void *(*alloc)(size_t, void *) = nullptr;

@@ -68,3 +68,39 @@ def test_standalone_broadphase_equals_scene_pairs_on_hair(V):
                               max_pairs=2 * len(scene_pairs) + 16)
     assert total == len(scene_pairs)
     np.testing.assert_array_equal(got, scene_pairs)
+
+
+def _rods_with_outliers(seed, n_rods=4000, n_long=900, huge=False):
+    """Short four-vertex rods, some with a middle segment stretched 5-50x (and
+    optionally one segment across the whole domain): the bounding radii then
+    have a long tail, so the grid's cell is cut below the largest radius and
+    the pills above the cut are paired from their own side."""
+    rng = np.random.default_rng(seed)
+    off = (np.arange(n_rods + 1) * 4).astype(np.int32)
+    nv = 4 * n_rods
+    x4 = np.zeros((nv, 4), np.float32)
+    base = rng.uniform(-0.5, 0.5, (n_rods, 3))
+    d = rng.normal(size=(n_rods, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    steps = np.full((n_rods, 3), 0.01)
+    steps[:n_long, 1] *= rng.uniform(5, 50, n_long)
+    if huge:
+        steps[n_long, 1] = 1.5
+    pos = base[:, None, :] + np.concatenate([np.zeros((n_rods, 1)), np.cumsum(steps, 1)], 1)[:, :, None] * d[:, None, :]
+    x4[:, :3] = pos.reshape(nv, 3)
+    x4[:, 3] = rng.uniform(0.8, 1.2, nv)
+    rbar = rng.uniform(0.003, 0.01, nv).astype(np.float32)
+    group = np.arange(n_rods, dtype=np.int32)
+    return off, group, x4, rbar
+
+
+@pytest.mark.parametrize("seed,huge", [(0, False), (1, True)])
+def test_broadphase_with_oversized_pills_matches_brute_force(V, seed, huge):
+    import torch
+    off, group, x4, rbar = _rods_with_outliers(seed, huge=huge)
+    ref = oracle.broadphase_f32(off, group, x4, rbar, brute=True)
+    assert len(ref) > 1000
+    t = lambda a: torch.from_numpy(a).cuda()
+    got, total = V.broadphase(t(off), t(group), t(x4), t(rbar), max_pairs=2 * len(ref) + 16)
+    assert total == len(ref)
+    np.testing.assert_array_equal(got, ref)
