@@ -266,19 +266,22 @@ int viper_broadphase(int n_rods, int n_verts, const int *rod_offsets, const int 
 /*
  * Allocation-free variant of viper_broadphase (the paper has no counterpart;
  * this is a library service).  For callers that cannot allocate device memory
- * when they run the query -- work enqueued while a CUDA graph is being
- * captured, real-time loops that must not wait on an allocator, hosts whose
- * device memory is owned by another allocator.  Same arguments, results and
+ * when they run the query: real-time loops with a fixed per-frame budget, where
+ * cudaMalloc or a growing stream-ordered pool may block or synchronise the
+ * device for an unbounded time, and hosts whose device memory is owned by
+ * another allocator (a framework's caching allocator, an engine's memory
+ * manager) that this library cannot call into.  Same arguments, results and
  * alignment rules as viper_broadphase, but the scratch is one fixed
  * file-scope device array (about 4.3 MiB, held on every GPU that loads the
  * library until the process exits), so the call never allocates or frees.
  * Limits: at most VIPER_NOALLOC_MAX_SEGMENTS segments (n_verts - n_rods);
  * larger queries return VIPER_EINVAL without doing any work.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and
- * corrupt each other's results -- order them on one stream.
+ * The first call on each device (and again after a device reset, in the new
+ * context) looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and corrupt each other's results -- order them on one stream.
  */
 #define VIPER_NOALLOC_MAX_SEGMENTS 65536
 int viper_broadphase_noalloc(int n_rods, int n_verts, const int *rod_offsets, const int *group, const float *x4,

@@ -1,12 +1,14 @@
 """viper_broadphase_noalloc: the allocation-free broadphase query.
 
-Callers that cannot allocate device memory when they run the query (work
-enqueued during CUDA graph capture, real-time loops, hosts whose memory belongs
-to another allocator) use this entry point; its scratch is a fixed device array
-inside the library.  These tests call it through the C ABI and check that two
-calls in a row return exactly what the allocating viper_broadphase returns on
-the same inputs (the pair set is integer data: compared bit for bit), and that
-queries above the fixed limit are refused.  This file is collected last.
+Callers that cannot allocate device memory when they run the query use this
+entry point: real-time loops with a fixed per-frame budget (an allocation can
+block or synchronise the device) and hosts whose device memory belongs to
+another allocator.  Its scratch is a fixed device array inside the library.
+These tests call it through the C ABI and check that two calls in a row
+return exactly what the allocating viper_broadphase returns on the same inputs
+(the pair set is integer data: compared bit for bit), that a call leaves
+torch's allocator untouched, and that queries above the fixed limit are
+refused.  This file is collected last.
 """
 import ctypes as C
 
@@ -79,3 +81,25 @@ def test_noalloc_refuses_queries_above_its_fixed_scratch(V):
     n = C.c_void_p(256)
     rc = L.viper_broadphase_noalloc(n_rods, nv, dummy, None, dummy, dummy, dummy, 16, n, None)
     assert rc == V.EINVAL
+
+
+def test_noalloc_leaves_the_torch_allocator_untouched(V):
+    import torch
+    L = V.lib()
+    off, group, x4, rbar = _rods(13, 1500)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_off, d_grp, d_x4, d_rb = t(off), t(group), t(x4), t(rbar)
+    cap = 200_000
+    pairs = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    args = (len(off) - 1, x4.shape[0], C.c_void_p(d_off.data_ptr()), C.c_void_p(d_grp.data_ptr()),
+            C.c_void_p(d_x4.data_ptr()), C.c_void_p(d_rb.data_ptr()), C.c_void_p(pairs.data_ptr()), cap,
+            C.c_void_p(n.data_ptr()), C.c_void_p(st.cuda_stream))
+    assert L.viper_broadphase_noalloc(*args) == 0  # the device's first call: address lookup
+    st.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+    assert L.viper_broadphase_noalloc(*args) == 0
+    st.synchronize()
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == before
+    assert int(n.item()) > 0
