@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
                 and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))):
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -61,6 +61,7 @@ def lib():
         L.vo_create.restype = C.c_void_p
         L.vo_create.argtypes = [C.POINTER(_Desc)]
         L.vo_destroy.argtypes = [C.c_void_p]
+        L.vo_set_threads.argtypes = [C.c_void_p, C.c_int]
         L.vo_set_state.argtypes = [C.c_void_p] + [_dp] * 6
         L.vo_get_state.argtypes = [C.c_void_p] + [_dp] * 6
         L.vo_set_bones.argtypes = [C.c_void_p, _dp, _dp]
@@ -106,7 +107,7 @@ def _i(a):
 class OracleScene:
     """FP64 oracle scene built from a ``scenes.Scene``."""
 
-    def __init__(self, scene):
+    def __init__(self, scene, threads=1):
         L = lib()
         self.scene = scene
         keep = []
@@ -163,6 +164,8 @@ class OracleScene:
         if not h:
             raise ValueError("vo_create rejected the scene")
         self._h = h
+        if threads != 1 and L.vo_set_threads(h, int(threads)) != 0:
+            raise ValueError("vo_set_threads rejected the thread count")
         self.n_rods, self.nv, self.ns = scene.n_rods, scene.nv, scene.ns
         self.t = 0.0
         if scene.init_pos is not None or scene.init_quat is not None:

@@ -69,6 +69,11 @@ struct vo_scene {
     int npairs, cap_pairs;
     double *acc;
     int *cnt;
+    /* host threads of the colour sweeps and the contact pass (OpenMP; 1: serial) */
+    int threads;
+    /* contact pass: per pair an activity flag and its 16 corrections */
+    double *cdelta;
+    size_t cap_cdelta;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -641,6 +646,8 @@ static void jacobi_pass(vo_scene *S, double h)
  */
 static void colour_sweep(vo_scene *S, int colour, double h)
 {
+    /* rods are independent within a colour: the result does not depend on the threads */
+#pragma omp parallel for schedule(dynamic, 64) num_threads(S->threads) if (S->threads > 1)
     for (int r = 0; r < S->n_rods; ++r) {
         int v0 = S->off[r], n = S->off[r + 1] - v0;
         if (colour < 2) {
@@ -1088,12 +1095,31 @@ int vo_narrowphase(const double *a1, double ra1, const double *a2, double ra2, c
  * Half-plane (Sec. 7): per vertex sphere C = n.x - d - s rbar (the capsule's
  * distance to a plane is linear along the pill, so its end spheres suffice).
  */
+/*
+ * Contact pass (Sec. 7, 7.2): every candidate pair from the state at the start
+ * of the pass -- narrowphase, one XPBD update of its multiplier, corrections of
+ * its four vertices -- then the corrections summed per vertex in ascending pair
+ * order, the half-planes' after them, and each vertex moved by its sum over the
+ * number of constraints acting on it (Jacobi with averaging).  The pairs are
+ * independent until the summation, so the first phase may run on several
+ * threads; the sums, taken in pair order by one thread, make the result
+ * independent of the thread count.
+ */
 static void contact_pass(vo_scene *S, double h)
 {
     memset(S->acc, 0, sizeof(double) * 4 * (size_t)S->nv);
     memset(S->cnt, 0, sizeof(int) * (size_t)S->nv);
-    if (S->contacts) {
+    if (S->contacts && S->npairs > 0) {
+        const size_t need = 17 * (size_t)S->npairs;
+        if (need > S->cap_cdelta) {
+            free(S->cdelta);
+            S->cdelta = malloc(sizeof(double) * need);
+            S->cap_cdelta = need;
+        }
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(S->threads) if (S->threads > 1)
         for (int k = 0; k < S->npairs; ++k) {
+            double *out = S->cdelta + 17 * (size_t)k;
+            out[0] = 0.0;
             int ga = S->pairs[2 * k], gb = S->pairs[2 * k + 1];
             int va = S->seg_v0[ga], vb = S->seg_v0[gb];
             int vs[4] = {va, va + 1, vb, vb + 1};
@@ -1123,29 +1149,43 @@ static void contact_pass(vo_scene *S, double h)
             }
             double alpha = S->ccomp;
             xpbd_solve(S, 1, &C, b, 8, &alpha, &S->lam_pair[k], h);
+            out[0] = 1.0;
             for (int t = 0; t < 4; ++t) {
-                for (int c = 0; c < 3; ++c) S->acc[4 * vs[t] + c] += b[t].delta[c];
-                S->acc[4 * vs[t] + 3] += b[4 + t].delta[0];
+                for (int c = 0; c < 3; ++c) out[1 + 4 * t + c] = b[t].delta[c];
+                out[1 + 4 * t + 3] = b[4 + t].delta[0];
+            }
+        }
+        for (int k = 0; k < S->npairs; ++k) {
+            const double *in = S->cdelta + 17 * (size_t)k;
+            if (in[0] == 0.0) continue;
+            int va = S->seg_v0[S->pairs[2 * k]], vb = S->seg_v0[S->pairs[2 * k + 1]];
+            int vs[4] = {va, va + 1, vb, vb + 1};
+            for (int t = 0; t < 4; ++t) {
+                for (int c = 0; c < 4; ++c) S->acc[4 * vs[t] + c] += in[1 + 4 * t + c];
                 S->cnt[vs[t]] += 1;
             }
         }
     }
-    for (int i = 0; i < S->nv && S->np > 0; ++i) {
-        for (int p = 0; p < S->np; ++p) {
-            const double *pl = S->planes + 4 * p;
-            double C = dot3(pl, S->x + 3 * i) - pl[3] - S->s[i] * S->rbar[i];
-            if (!(C < 0.0)) continue;
-            blk_t b[2];
-            b[0].type = BLK_POS; b[0].idx = i;
-            for (int c = 0; c < 3; ++c) b[0].J[c] = pl[c];
-            b[1].type = BLK_SCALE; b[1].idx = i; b[1].J[0] = -S->rbar[i];
-            double alpha = S->ccomp;
-            xpbd_solve(S, 1, &C, b, 2, &alpha, &S->lam_plane[(size_t)i * S->np + p], h);
-            for (int c = 0; c < 3; ++c) S->acc[4 * i + c] += b[0].delta[c];
-            S->acc[4 * i + 3] += b[1].delta[0];
-            S->cnt[i] += 1;
+    if (S->np > 0) {
+#pragma omp parallel for schedule(static) num_threads(S->threads) if (S->threads > 1)
+        for (int i = 0; i < S->nv; ++i) {
+            for (int p = 0; p < S->np; ++p) {
+                const double *pl = S->planes + 4 * p;
+                double C = dot3(pl, S->x + 3 * i) - pl[3] - S->s[i] * S->rbar[i];
+                if (!(C < 0.0)) continue;
+                blk_t b[2];
+                b[0].type = BLK_POS; b[0].idx = i;
+                for (int c = 0; c < 3; ++c) b[0].J[c] = pl[c];
+                b[1].type = BLK_SCALE; b[1].idx = i; b[1].J[0] = -S->rbar[i];
+                double alpha = S->ccomp;
+                xpbd_solve(S, 1, &C, b, 2, &alpha, &S->lam_plane[(size_t)i * S->np + p], h);
+                for (int c = 0; c < 3; ++c) S->acc[4 * i + c] += b[0].delta[c];
+                S->acc[4 * i + 3] += b[1].delta[0];
+                S->cnt[i] += 1;
+            }
         }
     }
+#pragma omp parallel for schedule(static) num_threads(S->threads) if (S->threads > 1)
     for (int i = 0; i < S->nv; ++i) {
         if (S->cnt[i] == 0) continue;
         double inv = 1.0 / S->cnt[i];
@@ -1310,6 +1350,7 @@ vo_scene *vo_create(const vo_desc *d)
     S->planes = xcalloc(4 * (size_t)S->np, sizeof(double));
     if (S->np) memcpy(S->planes, d->planes, sizeof(double) * 4 * S->np);
     S->ccomp = d->contact_compliance;
+    S->threads = 1;
     S->contacts = d->contacts;
     S->volume = d->volume;
     S->surface = d->surface_bending;
@@ -1363,6 +1404,13 @@ vo_scene *vo_create(const vo_desc *d)
     return S;
 }
 
+int vo_set_threads(vo_scene *S, int threads)
+{
+    if (!S || threads < 1) return -1;
+    S->threads = threads;
+    return 0;
+}
+
 void vo_destroy(vo_scene *S)
 {
     if (!S) return;
@@ -1372,7 +1420,7 @@ void vo_destroy(vo_scene *S)
                     S->bt, S->planes, S->x, S->s, S->v, S->sd, S->q, S->w, S->xp, S->sp, S->qp,
                     S->lam_seg, S->lam_vtx, S->lam_lap, S->jdx, S->jds, S->jdth, S->jcx, S->jcs, S->jcq,
                     S->bund_off, S->bund_rods, S->lbar0, S->rbar0, S->rho,
-                    S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt};
+                    S->lam_pair, S->lam_plane, S->pairs, S->acc, S->cnt, S->cdelta};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(S);
 }

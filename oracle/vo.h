@@ -59,6 +59,10 @@ typedef struct vo_desc {
 
 vo_scene *vo_create(const vo_desc *d);
 void vo_destroy(vo_scene *s);
+
+/* Host threads for the colour sweeps and the contact pass (OpenMP); the
+ * result is the same for every thread count.  -1 for threads < 1. */
+int vo_set_threads(vo_scene *s, int threads);
 int vo_counts(const vo_scene *s, int *n_rods, int *nv, int *ns);
 
 /* Any pointer may be NULL (that part is left unchanged / not returned). */
