@@ -1213,7 +1213,7 @@ def test_oracle_threads_give_identical_results(name):
     """The OpenMP colour sweeps and contact pass (pairs in parallel, sums in
     pair order) give bitwise the single-thread result."""
     # hair: 400 strands on a 3 cm sphere (about 8k pairs), reaching the floor plane by frame 3
-    sc = S.hair(n_rods=400, sphere=0.03, box=0.12) if name == "hair" else S.muscle_rig(n_rods=40, mesh_verts=0)
+    sc = S.hair(n_rods=400, sphere=0.03, box=0.12) if name == "hair" else S.muscle_rig(mesh_verts=0)
     out = []
     for threads in (1, 3):
         o = oracle.OracleScene(sc, threads=threads)
