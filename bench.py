@@ -1,17 +1,21 @@
 """Benchmark of the VIPER per-substep rod solve on GB300.
 
-A step is one frame of the muscle-rig workload: kinematic bones animated
-towards the frame's pose, 10 substeps x 4 iterations of prediction, constraint
-projection, pill-pill contacts and velocity update, then linear blend skinning
-of the 200k-vertex mesh.  Reported metric: rod-vertex substeps per second
-(vertices x substeps / frame time), whole job.
+A step is one frame of the contact-heavy hair workload, the largest
+single-GPU configuration: 20,000 rods x 16 vertices falling from a sphere into
+a box, 10 substeps x 4 iterations of prediction, constraint projection,
+pill-pill contacts (grid broadphase, dichotomous narrowphase) with six
+half-planes, and velocity update.  Reported metric: rod-vertex substeps per
+second (vertices x substeps / frame time), whole job.  The muscle rig with
+skinning, the batching workload, the multi-scene step and the serving loop
+are measured as sections of the same line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Timing: W untimed frames; then K frames each bracketed by CUDA events on the
 scene stream, with a 256 MB buffer written between frames (outside the events)
 so that every frame starts with a cold L2; barrier + synchronize around the
-timed region; max over ranks.  Under torchrun every rank steps its own
+timed region; max over ranks.  Frames are those of the trajectory from the
+start (frame W to W + K - 1).  Under torchrun every rank steps its own
 independent seeded scene (weak scaling; no data-path collective).
 """
 from __future__ import annotations
@@ -32,9 +36,82 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD_DESC = ("muscle_rig: 200 tapered rods of 8-64 vertices pinned to 20 animated bones, "
-                 "pill-pill contacts, volume on, dt=1/60 s, 10 substeps x 4 iterations, "
-                 "LBS of a 200k-vertex mesh (4 weights)")
+WORKLOAD_DESC = ("hair: 20,000 rods x 16 vertices (320,000 vertices, 300,000 pills), radius 2 mm, 5 mm segments, "
+                 "roots at Poisson-disk sites of a 0.2 m sphere falling into a 0.3 m box (six half-planes), "
+                 "pill-pill contacts (uniform-grid broadphase, dichotomous narrowphase, compliance 1e-9), "
+                 "volume on, dt=1/60 s, 10 substeps x 4 iterations")
+MUSCLE_DESC = ("muscle_rig: 200 tapered rods of 8-64 vertices pinned to 20 animated bones, "
+               "pill-pill contacts, volume on, dt=1/60 s, 10 substeps x 4 iterations, "
+               "LBS of a 200k-vertex mesh (4 weights)")
+HAIR_PAIRS_PER_PILL = 64  # pair-list capacity of the hair scene (peak use about 36 per pill)
+
+# FP32 work per unit of the contact pass (ncu SASS counts of FADD + FMUL + 2 FFMA on the
+# hair scene; see the contact-pass profile): the certified early-out test per
+# candidate pair, and the dichotomous search + constraint update per searched pair
+CONTACT_FLOP_PER_CANDIDATE = 40.8
+CONTACT_FLOP_PER_SEARCHED = 1876.0
+# FP32 work of the shared-memory rod kernel per vertex per colour sweep (ncu SASS
+# counts on the batching workload: 2.133 GFLOP per launch over 250,612 vertices x 8
+# sweeps, prediction and velocity update included)
+ROD_FLOP_PER_VERTEX_SWEEP = 1064.0
+
+
+def hair_scene(rank=0):
+    from paper_1906_05260_gb300 import scenes as S
+    return S.hair(seed=3 + rank)
+
+
+def hair_octant(sc):
+    """The rods of the hair scene whose roots lie in the octant x, y, z > 0 of
+    the sphere: a sample with the scene's own local density of strands and
+    contacts (about an eighth of its rods; planes and material kept)."""
+    import dataclasses as dc
+    roots = sc.rest_pos[sc.rod_offsets[:-1]]
+    keep = np.nonzero((roots > 0).all(axis=1))[0]
+    sub = sc.subset(keep)
+    return dc.replace(sub, name="hair_octant", group=np.arange(len(keep), dtype=np.int32))
+
+
+def kernel_source_hash():
+    """sha256 of the CUDA sources (csrc/*.cu, *.cuh, *.h, sorted by name): the
+    build an ncu summary under profiles/ was captured from."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1906_05260_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(summary, key):
+    """DRAM bytes per unit of one kernel from a committed ncu summary
+    (profiles/<summary>): the line 'traffic <key>: <bytes> bytes per <unit>',
+    used only while the summary's 'csrc sha256:' line matches the sources of
+    this build; else None (the kernel changed since the counters were taken)."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    sha, val = None, None
+    with open(path) as f:
+        for line in f:
+            line = line.strip().strip("`")
+            if line.startswith("csrc sha256:"):
+                sha = line.split(":", 1)[1].strip()
+            elif line.startswith(f"traffic {key}:"):
+                try:
+                    val = float(line.split(":", 1)[1].split()[0])
+                except ValueError:
+                    val = None
+    return val if sha == kernel_source_hash() else None
+
+
+def fp32_peak_tflops(sm_max_mhz):
+    """FP32 SIMT peak: SMs (read from the device) x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12, sms
 
 
 def load_peaks():
@@ -161,68 +238,63 @@ def whole_job(dist, units, ms):
 
 # ---------------------------------------------------------------------------- oracle arm
 
-def oracle_run(scene, frames: int, skin: bool = True):
-    """Step the FP64 oracle `frames` frames (plus LBS); returns seconds."""
+def oracle_substep_time(scene, threads=1):
+    """Seconds of one substep of the FP64 oracle on `scene` from its initial state
+    (h = dt / substeps, the scene's iterations), on `threads` host threads."""
     import oracle
-    o = oracle.OracleScene(scene)
+    o = oracle.OracleScene(scene, threads=threads)
     t0 = time.perf_counter()
-    for _ in range(frames):
-        o.frame()
-        if skin and scene.mesh is not None:
-            o.skin()
-    return time.perf_counter() - t0
+    rc = o.step(dt=scene.dt / scene.substeps, substeps=1, iterations=scene.iterations)
+    t = time.perf_counter() - t0
+    if rc != 0:
+        raise SystemExit(f"oracle step failed: {rc}")
+    return t
 
 
-def cpu_baseline(scene, budget_s: float = 20.0):
-    """The oracle on this host's cores (single-threaded), on a bounded sample."""
-    t1 = oracle_run(scene, 1)
-    frames = max(1, min(10, int(budget_s / max(t1, 1e-3))))
-    t = oracle_run(scene, frames)
-    val = scene.nv * scene.substeps * frames / t
-    return {"value": val, "unit": "rod-vertex substeps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{frames} frame(s) of the same muscle_rig scene incl. LBS of {scene.mesh.n} vertices, "
-                      f"FP64, single thread, {os.cpu_count()} host cores present"}
+def cpu_baseline(scene):
+    """The oracle on this host's cores on a bounded sample of the hair workload:
+    one substep of the full scene from its initial state (2.19 M candidate pairs),
+    single-threaded and with one thread per host core."""
+    t1 = oracle_substep_time(scene, threads=1)
+    cores = os.cpu_count() or 1
+    tn = oracle_substep_time(scene, threads=cores)
+    return {"value": scene.nv / t1, "unit": "rod-vertex substeps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one substep (h = dt/{scene.substeps}, {scene.iterations} iterations, contacts) of the full "
+                      f"hair scene from its initial state, FP64, {t1:.1f} s on one thread",
+            "threads": {"value": scene.nv / tn, "unit": "rod-vertex substeps/s", "cores": cores,
+                        "kind": "oracle",
+                        "sample": f"the same substep with OpenMP over the constraints of each colour and the "
+                                  f"pairs of each contact pass, {tn:.2f} s on {cores} threads"}}
 
 
 def run_reference(args):
-    from paper_1906_05260_gb300 import scenes as S
     # the oracle runs on rank 0's host cores alone; the other ranks exit without work
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     import oracle
     oracle.build()
-    sc = S.muscle_rig(seed=1)
-    # bound the whole run to a few minutes: each step is one oracle frame of a
-    # rod sample of the workload if full frames would not fit
-    t1 = oracle_run(sc, 1)
-    budget = 150.0
-    per_step_budget = budget / max(1, args.steps + args.warmup)
-    sample_desc = "full frame"
-    if t1 > per_step_budget:
-        frac = max(0.02, per_step_budget / t1)
-        n_rods = max(4, int(sc.n_rods * frac))
-        sc = S.muscle_rig(seed=1, n_rods=n_rods, mesh_verts=max(1000, int(sc.mesh.n * frac)))
-        sample_desc = f"{n_rods} of 200 rods and a {sc.mesh.n}-vertex mesh per frame"
-    import oracle as O
-    o = O.OracleScene(sc)
+    sample = hair_octant(hair_scene(0))
+    h = sample.dt / sample.substeps
+    o = oracle.OracleScene(sample)
     for _ in range(args.warmup):
-        o.frame()
-        o.skin()
+        o.step(dt=h, substeps=1, iterations=sample.iterations)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.frame()
-        o.skin()
+        rc = o.step(dt=h, substeps=1, iterations=sample.iterations)
         times.append(time.perf_counter() - t0)
+        if rc != 0:
+            raise SystemExit(f"oracle step failed: {rc}")
     mean = sum(times) / len(times)
-    val = sc.nv * sc.substeps / mean
+    val = sample.nv / mean
+    desc = (f"one substep per step of the rods rooted in one octant of the hair scene ({sample.n_rods} rods, "
+            f"{sample.nv} vertices, same local density), FP64, one thread")
     line = {
         "impl": "reference", "metric": "rod-vertex substeps/sec", "value": val, "unit": "rod-vertex substeps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "sample": sample_desc},
-        "cpu_baseline": {"value": val, "unit": "rod-vertex substeps/s", "cores": 1, "kind": "oracle",
-                         "sample": sample_desc},
+        "config": {"workload": WORKLOAD_DESC, "sample": desc},
+        "cpu_baseline": {"value": val, "unit": "rod-vertex substeps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": val, "unit": "rod-vertex substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -272,7 +344,7 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
                 nl += n
             us = 1e3 * tot / max(nl, 1)
             per_launch = sc.substeps if mode == V.SOLVER_FRAME else 1  # substeps per launch
-            flops = sc.nv * sc.iterations * 1030.0 * per_launch
+            flops = sc.nv * sc.iterations * ROD_FLOP_PER_VERTEX_SWEEP * per_launch
             bytes_ = sc.nv * 140.0 * (1 if mode == V.SOLVER_FRAME else 1)  # state in/out + rest once per launch
             out["rod_kernel" if mode == V.SOLVER_BATCHED else "frame_kernel"] = {
                 "us_per_launch": us, "launches_per_frame": nl / min(frames, 10),
@@ -553,43 +625,118 @@ def bench_muscles(V, torch, flush, dist, frames, rank=0):
     return res
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-batching", action="store_true")
-    ap.add_argument("--no-multi", action="store_true")
-    ap.add_argument("--no-muscles", action="store_true")
-    ap.add_argument("--no-lbs", action="store_true")
-    ap.add_argument("--serving", type=float, default=10.0,
-                    help="seconds of the real-time serving load (0 disables)")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    if args.impl == "reference":
-        return run_reference(args)
+def events_timed(torch, stream, flush, nframes, fn):
+    """Device time of each call of fn() between CUDA events on `stream`, L2
+    flushed before each (outside the events); ms per call."""
+    ts = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for i in range(nframes):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
 
-    import torch
-    from paper_1906_05260_gb300 import build as B
-    B.build()
+
+HAIR_CLASSES = ("rod", "contact", "broadphase", "pairs", "elementwise")
+
+
+def per_class_times(V, torch, g, stream, flush, frames, step):
+    """Device time per frame of each kernel class (events around its launches
+    inside the frame graph), over `frames` frames per class."""
+    classes = {"rod": V.PROF_ROD, "contact": V.PROF_CONTACT, "broadphase": V.PROF_BROADPHASE,
+               "pairs": V.PROF_PAIRS, "lbs_gather": V.PROF_LBS, "elementwise": V.PROF_ELEMENTWISE}
+    out = {}
+    for name, cls in classes.items():
+        g.profile(cls)
+        step()
+        g.profile_read()
+        tot, nl = 0.0, 0
+        for i in range(frames):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+            step()
+            ms, n = g.profile_read()
+            tot += ms
+            nl += n
+        if nl:
+            out[name] = {"ms_per_frame": tot / frames, "launches_per_frame": nl / frames,
+                         "us_per_launch": 1e3 * tot / nl}
+    g.profile(V.PROF_NONE)
+    return out
+
+
+def contact_roofline(per_class, stats, sc, peak_tflops, peak_kind, sms, sm_max):
+    """ALU roofline of the contact pass: FP32 work = candidates x the early-out
+    test + searched pairs x (dichotomous search + update), per launch, over its
+    event-timed duration."""
+    d = per_class["contact"]
+    launches = stats["passes"]
+    cand = stats["candidates"] / launches
+    searched = stats["searched"] / launches
+    if CONTACT_FLOP_PER_CANDIDATE is None or CONTACT_FLOP_PER_SEARCHED is None:
+        return {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
+                "kernel": "contact_kernel", "note": "per-unit FP32 work not calibrated"}
+    flops = cand * CONTACT_FLOP_PER_CANDIDATE + searched * CONTACT_FLOP_PER_SEARCHED
+    ach = flops / (d["us_per_launch"] * 1e-6) / 1e12
+    tr = profile_traffic("contact_kernel_hair.md", "per candidate pair")
+    return {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+            "traffic": None if tr is None else tr * cand,
+            "traffic_unit": "DRAM bytes per launch (ncu bytes per candidate pair x candidates per launch)",
+            "kernel": "contact_kernel",
+            "peak_kind": f"FP32 SIMT {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz ({peak_kind} clock)",
+            "work": {"candidates_per_launch": cand, "searched_per_launch": searched,
+                     "active_per_launch": stats["active"] / launches,
+                     "flop_per_candidate": CONTACT_FLOP_PER_CANDIDATE,
+                     "flop_per_searched_pair": CONTACT_FLOP_PER_SEARCHED},
+            "us_per_launch": d["us_per_launch"]}
+
+
+def pairs_roofline(per_class, pairs_per_substep, sc, peaks, peak_kind):
+    """HBM roofline of the pair search: 60 B per pill (spheres, cells, groups in
+    cell order) + 20 B per emitted pair (pair, its first vertices, multiplier)."""
+    d = per_class["pairs"]
+    bytes_ = sc.ns * 60.0 + pairs_per_substep * 20.0
+    ach = bytes_ / (d["us_per_launch"] * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+            "traffic": None, "kernel": "bp_emit_kernel", "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "us_per_launch": d["us_per_launch"]}
+
+
+def bench_hair_trajectory(V, torch, flush, dist, sc, cap):
+    """All frames of the hair workload (the configuration's 200) from the start,
+    on a fresh scene: per-frame device time, p50/p99, whole-run throughput."""
+    g = V.Scene(sc, max_pairs=cap)
+    ts = events_timed(torch, g.stream, flush, sc.frames, g.step)
+    rc = g.sync()
+    pairs_last = int(g.pairs().shape[0])
+    g.close()
+    if rc != 0:
+        raise SystemExit(f"hair trajectory failed: {rc}")
+    tot = sum(ts)
+    units = reduce_sum(dist, sc.nv * sc.substeps * sc.frames)
+    tot = reduce_max(dist, tot)
+    return {"frames": sc.frames, "value": units / (tot * 1e-3), "unit": "rod-vertex substeps/s",
+            "ms_total": tot, "ms_per_frame_mean": tot / sc.frames, "p50_ms": float(np.percentile(ts, 50)),
+            "p99_ms": float(np.percentile(ts, 99)), "max_ms": float(max(ts)), "pairs_last_substep": pairs_last,
+            "ms_per_frame_every_10": [round(x, 2) for x in ts[::10]]}
+
+
+def bench_muscle_rig(V, torch, flush, dist, K, W, sec_frames, peaks, peak_kind, fp32_peak, sms, rank, no_plain):
+    """The muscle rig (configs' 200-rod rig with bones, contacts and a 200k-vertex
+    LBS mesh): frame time on the graph path, e2e through the C ABI with host
+    operands, per-class times and the plain one-launch-per-colour path."""
     from paper_1906_05260_gb300 import scenes as S
-    from paper_1906_05260_gb300 import viper as V
-
-    dist, rank, ws, local = dist_setup()
-    torch.cuda.set_device(local)
+    import ctypes as C
     sc = S.muscle_rig(seed=1 + rank)
     g = V.Scene(sc)
     mesh = V.Mesh(sc.mesh)
     stream = g.stream
     nb = sc.bones.n
-    K, W = args.steps, args.warmup
-    sec_frames = max(10, min(K, 60) // 2)  # frames per timed section beside the main line
-
-    # per-frame bone poses: the inputs, generated before timing
     total_frames = 10 * (W + K) + 400
     poses_q = np.zeros((total_frames, nb, 4), np.float32)
     poses_t = np.zeros((total_frames, nb, 3), np.float32)
@@ -600,7 +747,6 @@ def main():
     dev_t = torch.from_numpy(poses_t).cuda()
     pin_q = torch.from_numpy(poses_q).pin_memory()
     pin_t = torch.from_numpy(poses_t).pin_memory()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     frame_no = [0]
 
     def device_frame():
@@ -610,55 +756,30 @@ def main():
         g.step()
         g.skin(mesh)
 
-    def timed(nframes, fn):
-        ts = []
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        for i in range(nframes):
-            with torch.cuda.stream(stream):
-                flush.fill_(i & 0xFF)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return ts
-
-    # ---- batched (graph) path: warmup + timed region
     for _ in range(W):
         device_frame()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier(dist)
-    torch.cuda.synchronize()
     l0 = g.launch_count()
-    clocks.begin()
-    ts = timed(K, device_frame)
-    torch.cuda.synchronize()
-    clocks.end()
-    barrier(dist)
-    launches = g.launch_count() - l0
-    clk = clocks.stop()
+    ts = events_timed(torch, stream, flush, K, device_frame)
+    launches = (g.launch_count() - l0) / K
     rc = g.sync()
     if rc != 0:
-        raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
-    mean_ms = sum(ts) / len(ts)
-    value, mean_ms_max = whole_job(dist, sc.nv * sc.substeps, mean_ms)
+        raise SystemExit(f"muscle rig: solver error {rc}: {V.error_string(rc)}")
     units = reduce_sum(dist, sc.nv * sc.substeps)
-    p50 = float(np.percentile(ts, 50))
-    p99 = float(np.percentile(ts, 99))
+    ms = reduce_max(dist, sum(ts) / len(ts))
+    out = {"workload": MUSCLE_DESC, "rods": sc.n_rods, "vertices": sc.nv, "mesh_vertices": sc.mesh.n,
+           "value": units / (ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_frame": ms,
+           "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+           "skinned_vertices_per_s": reduce_sum(dist, sc.mesh.n) / (ms * 1e-3), "launches_per_frame": launches,
+           "solver": "batched: multi-scene kernels for this scene alone, frame replayed as a CUDA graph"}
 
-    # ---- end to end through the public API with host buffers
+    # end to end through the C ABI with host buffers (bones in, skinned mesh out)
     out_host = torch.empty((sc.mesh.n, 4), dtype=torch.float32).pin_memory()
     rest4 = np.zeros((sc.mesh.n, 4), np.float32)
     rest4[:, :3] = sc.mesh.rest
-    idx4 = np.ascontiguousarray(sc.mesh.idx, np.int32)
-    w4 = np.ascontiguousarray(sc.mesh.w, np.float32)
     rest_pin = torch.from_numpy(rest4).pin_memory()
-    idx_pin = torch.from_numpy(idx4).pin_memory()
-    w_pin = torch.from_numpy(w4).pin_memory()
-    import ctypes as C
+    idx_pin = torch.from_numpy(np.ascontiguousarray(sc.mesh.idx, np.int32)).pin_memory()
+    w_pin = torch.from_numpy(np.ascontiguousarray(sc.mesh.w, np.float32)).pin_memory()
 
     def host_frame():
         f = frame_no[0]
@@ -668,155 +789,194 @@ def main():
         rck = V.lib().viper_skin(g.handle, sc.mesh.n, C.c_void_p(rest_pin.data_ptr()), C.c_void_p(idx_pin.data_ptr()),
                                  C.c_void_p(w_pin.data_ptr()), C.c_void_p(out_host.data_ptr()))
         if rcb or rcs or rck:
-            raise SystemExit(f"e2e frame failed: {rcb} {rcs} {rck}")
+            raise SystemExit(f"muscle rig e2e frame failed: {rcb} {rcs} {rck}")
 
     for _ in range(3):
         host_frame()
-    torch.cuda.synchronize()
-    barrier(dist)
     te = []
-    for i in range(K):
+    for i in range(sec_frames):
         with torch.cuda.stream(stream):
             flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         host_frame()
         te.append((time.perf_counter() - t0) * 1e3)
-    barrier(dist)
     e2e_ms = reduce_max(dist, sum(te) / len(te))
-    e2e = {"value": units / (e2e_ms * 1e-3), "unit": "rod-vertex substeps/s",
-           "h2d_bytes_per_step": int(nb * (16 + 12) + sc.mesh.n * 48),
-           "d2h_bytes_per_step": int(sc.mesh.n * 16), "ms_per_step": e2e_ms,
-           "note": "host pinned bone poses and mesh operands in, skinned mesh out, wall clock per frame"}
-
-    # ---- per-kernel-class device time (events around each launch inside the graph)
-    classes = {"rod": V.PROF_ROD, "contact": V.PROF_CONTACT, "broadphase": V.PROF_BROADPHASE,
-               "pairs": V.PROF_PAIRS, "lbs_gather": V.PROF_LBS, "elementwise": V.PROF_ELEMENTWISE}
-    per_class = {}
-    prof_frames = min(K, 20)
-    for name, cls in classes.items():
-        g.profile(cls)
-        device_frame()
-        g.profile_read()
-        tot = 0.0
-        nl = 0
-        for i in range(prof_frames):
-            with torch.cuda.stream(stream):
-                flush.fill_(i & 0xFF)
+    out["e2e"] = {"value": units / (e2e_ms * 1e-3), "unit": "rod-vertex substeps/s", "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": int(nb * (16 + 12) + sc.mesh.n * 48),
+                  "d2h_bytes_per_step": int(sc.mesh.n * 16),
+                  "note": "host pinned bone poses and mesh operands in, skinned mesh out, wall clock per frame"}
+    out["per_class"] = per_class_times(V, torch, g, stream, flush, min(sec_frames, 20), device_frame)
+    if not no_plain:
+        g.set_solver(V.SOLVER_PLAIN)
+        for _ in range(3):
             device_frame()
-            ms, n = g.profile_read()
-            tot += ms
-            nl += n
-        if nl == 0:
-            continue  # class not launched by this solver (the frame kernel fuses it)
-        per_class[name] = {"ms_per_frame": tot / prof_frames, "launches_per_frame": nl / prof_frames,
-                           "us_per_launch": 1e3 * tot / max(nl, 1)}
-    g.profile(V.PROF_NONE)
-    dominant = max(per_class, key=lambda k: per_class[k]["ms_per_frame"])
+        tp = events_timed(torch, stream, flush, sec_frames, device_frame)
+        pm = reduce_max(dist, sum(tp) / len(tp))
+        out["plain"] = {"value": units / (pm * 1e-3), "ms_per_frame": pm, "p50_ms": float(np.percentile(tp, 50)),
+                        "p99_ms": float(np.percentile(tp, 99)), "solver": "plain: one launch per constraint colour"}
+        out["batched_over_plain"] = out["value"] / out["plain"]["value"]
+    g.close()
+    return out
 
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=195)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-trajectory", action="store_true")
+    ap.add_argument("--no-rig", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-muscles", action="store_true")
+    ap.add_argument("--no-lbs", action="store_true")
+    ap.add_argument("--serving", type=float, default=60.0,
+                    help="seconds of the real-time serving load (0 disables)")
+    ap.add_argument("--serving-serial", type=float, default=10.0,
+                    help="seconds of the same load served one scene per step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import ctypes as C
+    import torch
+    from paper_1906_05260_gb300 import build as B
+    B.build()
+    from paper_1906_05260_gb300 import viper as V
+
+    dist, rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
     peaks, peak_kind = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max clock
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    nv, ns = sc.nv, sc.ns
-    d = per_class[dominant]
-    # algorithmic work per launch of each class: 1030 FP32 flop per vertex per colour
-    # sweep, 1500 per candidate pair per contact pass, 64 B per skinned vertex, and for
-    # the broadphase about 60 B per pill plus 8 B per emitted pair
-    pairs_last = g.pairs().shape[0]
-    if dominant == "rod" and g.solver == V.SOLVER_FRAME:
-        # the whole frame: colour sweeps (1030 flop per vertex per sweep) + contact passes
-        # (1500 flop per candidate pair per pass, pair count of the frame's last substep)
-        flops = sc.substeps * sc.iterations * (nv * 1030.0 + pairs_last * 1500.0)
-        roof = {"bound": "alu", "achieved": flops / (d["us_per_launch"] * 1e-6) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "peak_kind": f"FP32 SIMT 152x128x2x{sm_max:.0f} MHz ({peak_kind} clock)",
-                "kernel_name": "frame_kernel<true,true>", "pairs": pairs_last}
-    elif dominant == "rod":
-        flops = nv * 1030.0  # FP32 flop per vertex per colour sweep (segment + vertex constraints)
-        roof = {"bound": "alu", "achieved": flops / (d["us_per_launch"] * 1e-6) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "peak_kind": f"FP32 SIMT 152x128x2x{sm_max:.0f} MHz ({peak_kind} clock)"}
-    elif dominant == "lbs_gather":
-        bytes_ = sc.mesh.n * 64.0
-        roof = {"bound": "hbm", "achieved": bytes_ / (d["us_per_launch"] * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "peak_kind": f"{peak_kind} HBM copy bandwidth"}
+    fp32_peak, sms = fp32_peak_tflops(sm_max)
+    K, W = args.steps, args.warmup
+    sec_frames = max(10, min(K, 60) // 2)  # frames per timed section beside the main line
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    sc = hair_scene(rank)
+    cap = HAIR_PAIRS_PER_PILL * sc.ns
+    units = sc.nv * sc.substeps
+
+    # ---- main line: the hair workload, frames W .. W + K - 1 of its trajectory
+    g = V.Scene(sc, max_pairs=cap)
+    stream = g.stream
+    for _ in range(W):
+        g.step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    l0 = g.launch_count()
+    clocks.begin()
+    ts = events_timed(torch, stream, flush, K, g.step)
+    torch.cuda.synchronize()
+    clocks.end()
+    barrier(dist)
+    launches = g.launch_count() - l0
+    clk = clocks.stop()
+    rc = g.sync()
+    if rc != 0:
+        raise SystemExit(f"solver error {rc}: {V.error_string(rc)}")
+    mean_ms = sum(ts) / len(ts)
+    value, mean_ms_max = whole_job(dist, units, mean_ms)
+    p50 = float(np.percentile(ts, 50))
+    p99 = float(np.percentile(ts, 99))
+    pairs_last = int(g.pairs().shape[0])
+
+    # ---- kernel classes and contact counters over the frames that follow
+    prof_frames = min(K, 10)
+    per_class = per_class_times(V, torch, g, stream, flush, prof_frames, g.step)
+    g.contact_stats()
+    for _ in range(prof_frames):
+        g.step()
+    cand, searched, active = g.contact_stats()
+    stats = {"candidates": cand, "searched": searched, "active": active,
+             "passes": prof_frames * sc.substeps * sc.iterations}
+    g.close()
+    dominant = max(per_class, key=lambda k: per_class[k]["ms_per_frame"])
+    if dominant == "pairs":
+        roof = pairs_roofline(per_class, pairs_last, sc, peaks, peak_kind)
     else:
-        pairs = g.pairs().shape[0]
-        if dominant == "contact":
-            flops = pairs * 1500.0
-            roof = {"bound": "alu", "achieved": flops / (d["us_per_launch"] * 1e-6) / 1e12,
-                    "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                    "peak_kind": f"FP32 SIMT 152x128x2x{sm_max:.0f} MHz ({peak_kind} clock)", "pairs": pairs}
-        else:
-            bytes_ = (ns * 60.0 + pairs * 8.0) / max(d["launches_per_frame"] / sc.substeps, 1)
-            roof = {"bound": "hbm", "achieved": bytes_ / (d["us_per_launch"] * 1e-6) / 1e9,
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                    "pairs": pairs}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dominant
-    # DRAM bytes per launch of the dominant class from one ncu capture of this workload
-    # (first sweep 0.716 MB, later sweeps 1.092 MB, one and three per substep; the
-    # velocity update and prediction run in the advance kernel before them); other
-    # classes or solvers: not captured
-    roof["traffic"] = (0.716e6 + 3 * 1.092e6) / 4 if (dominant == "rod" and g.solver == V.SOLVER_BATCHED) else None
-    roof["traffic_unit"] = "bytes per launch (dram read + write, ncu)"
+        roof = contact_roofline(per_class, stats, sc, fp32_peak, peak_kind, sms, sm_max)
+        roof["dominant_class"] = dominant
     roof["per_class"] = per_class
+    roof["contact_counters"] = stats
 
-    # ---- the other solvers on the same scene: graph-replayed launches and plain per-colour launches
-    main_solver = g.solver
+    # ---- end to end through the C ABI: a fresh scene, the same frames, each
+    # frame's positions and radii read back into pinned host memory
+    ge = V.Scene(sc, max_pairs=cap)
+    x4_host = torch.empty((sc.nv, 4), dtype=torch.float32).pin_memory()
+
+    def host_frame():
+        rcs = V.lib().viper_step(ge.handle, float(sc.dt), sc.substeps, sc.iterations)
+        rcg = V.lib().viper_get_state(ge.handle, C.c_void_p(x4_host.data_ptr()), None, None, None)
+        if rcs or rcg:
+            raise SystemExit(f"e2e frame failed: {rcs} {rcg}")
+
+    for _ in range(W):
+        host_frame()
+    barrier(dist)
+    te = []
+    for i in range(K):
+        with torch.cuda.stream(ge.stream):
+            flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        host_frame()
+        te.append((time.perf_counter() - t0) * 1e3)
+    barrier(dist)
+    ge.close()
+    e2e_ms = reduce_max(dist, sum(te) / len(te))
+    e2e = {"value": reduce_sum(dist, units) / (e2e_ms * 1e-3), "unit": "rod-vertex substeps/s",
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(sc.nv * 16), "ms_per_step": e2e_ms,
+           "note": "viper_step then viper_get_state of every vertex's position and scale into pinned host "
+                   "memory, wall clock per frame; the frame's only inputs are its scalars (dt, substeps, "
+                   "iterations), the state stays on the device"}
+
+    # ---- the plain one-launch-per-colour path on the same frames
     plain = None
-    graph = None
     if not args.no_plain:
-        for mode, label in ((V.SOLVER_BATCHED, "batched: one shared-memory rod launch per iteration, broadphase and "
-                                               "contact launches, frame replayed as a CUDA graph"),
-                            (V.SOLVER_PLAIN, "plain: one launch per constraint colour")):
-            if mode == main_solver:
-                continue
-            g.set_solver(mode)
-            for _ in range(3):
-                device_frame()
-            tp = timed(sec_frames, device_frame)
-            pm = reduce_max(dist, sum(tp) / len(tp))
-            res = {"value": units / (pm * 1e-3), "ms_per_step": pm, "p50_ms": float(np.percentile(tp, 50)),
-                   "p99_ms": float(np.percentile(tp, 99)), "solver": label}
-            if mode == V.SOLVER_PLAIN:
-                plain = res
-            else:
-                graph = res
-        g.set_solver(main_solver)
+        gp = V.Scene(sc, max_pairs=cap, solver=V.SOLVER_PLAIN)
+        for _ in range(W):
+            gp.step()
+        tp = events_timed(torch, gp.stream, flush, K, gp.step)
+        if gp.sync() != 0:
+            raise SystemExit("plain hair path failed")
+        gp.close()
+        pm = reduce_max(dist, sum(tp) / len(tp))
+        plain = {"value": reduce_sum(dist, units) / (pm * 1e-3), "ms_per_step": pm,
+                 "p50_ms": float(np.percentile(tp, 50)), "p99_ms": float(np.percentile(tp, 99)),
+                 "solver": "plain: one launch per constraint colour", "graph_over_plain": pm / mean_ms_max}
 
-    # ---- batching workload (4096 rods, 20 x 8, no contacts): batched vs plain and
-    # the shared-memory rod kernel's roofline
-    batching = None
-    convergence = None
+    trajectory = None if args.no_trajectory else bench_hair_trajectory(V, torch, flush, dist, sc, cap)
+
+    rig = None
+    if not args.no_rig:
+        rig = bench_muscle_rig(V, torch, flush, dist, min(K, 60), W, sec_frames, peaks, peak_kind, fp32_peak, sms,
+                               rank, args.no_plain)
+
+    batching = convergence = None
     if not args.no_batching:
-        batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, sec_frames)
+        batching = bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak, sec_frames)
         convergence = bench_convergence(V, np)
+    lbs = None if args.no_lbs else bench_lbs(V, torch, flush, dist, sec_frames, peaks, peak_kind, rank=rank)
+    muscles = None if args.no_muscles else bench_muscles(V, torch, flush, dist, sec_frames, rank=rank)
+    multi = None if args.no_multi else bench_multi_scene(V, torch, flush, dist, sec_frames, rank=rank)
 
-    # ---- skinning alone on a large mesh: the HBM-streaming stage's roofline
-    lbs = None
-    if not args.no_lbs:
-        lbs = bench_lbs(V, torch, flush, dist, sec_frames, peaks, peak_kind, rank=rank)
-
-    # ---- muscle features: activation + warm start, bundled muscles
-    muscles = None
-    if not args.no_muscles:
-        muscles = bench_muscles(V, torch, flush, dist, sec_frames, rank=rank)
-
-    # ---- many scenes at once: the multi-scene step against per-scene graphs
-    multi = None
-    if not args.no_multi:
-        g.close()
-        multi = bench_multi_scene(V, torch, flush, dist, sec_frames, rank=rank)
-
-    # ---- serving: Poisson stream of muscle-rig scenes, 60 Hz frame requests each
     serving = None
     if args.serving > 0:
         from paper_1906_05260_gb300 import serving as SV
-        g.close()
         temps = SV.scene_templates(seed=4 + rank)
         conc = SV.run_load(duration=args.serving, rate=6.4, mean_life=10.0, budget=150 << 30, max_inflight=256,
                            seed=4 + rank, templates=temps, warm_scenes=64)
-        ser = SV.run_load(duration=max(3.0, args.serving / 2), rate=6.4, mean_life=10.0, budget=150 << 30,
+        ser = SV.run_load(duration=max(3.0, args.serving_serial), rate=6.4, mean_life=10.0, budget=150 << 30,
                           max_inflight=1, seed=4 + rank, templates=temps, warm_scenes=64)
         serving = {
             "workload": "Poisson arrivals 6.4/s, lifetimes Exp(10 s), 64 scenes live at start (mean 64 "
@@ -837,18 +997,17 @@ def main():
         "metric": "rod-vertex substeps/sec", "value": value, "unit": "rod-vertex substeps/s", "n_gpus": ws,
         "steps": K, "warmup": W, "ms_per_step": mean_ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "rods": sc.n_rods, "vertices": sc.nv, "mesh_vertices": sc.mesh.n,
-                   "solver": ("frame: one persistent cooperative launch per frame, rods resident in shared memory, "
-                              "grid barriers between broadphase / sweep / contact phases")
-                             if main_solver == V.SOLVER_FRAME else
-                             "batched: shared-memory rod kernel, frame replayed as a CUDA graph",
+        "config": {"workload": WORKLOAD_DESC, "rods": sc.n_rods, "vertices": sc.nv, "pills": sc.ns,
+                   "frames_timed": f"{W} .. {W + K - 1} of the trajectory",
+                   "solver": "batched: shared-memory rod kernel per sweep, multi-kernel grid broadphase beside "
+                             "the first sweep, contact pass after every sweep, frame replayed as a CUDA graph",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{ws} (independent seeded scenes)"},
-        "latency_ms": {"p50": p50, "p99": p99},
-        "skinned_vertices_per_s": reduce_sum(dist, sc.mesh.n) / (mean_ms_max * 1e-3),
+        "latency_ms": {"p50": p50, "p99": p99}, "pairs_last_substep": pairs_last,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
         "plain": plain,
-        "graph_batched": graph,
+        "trajectory": trajectory,
+        "muscle_rig": rig,
         "batching": batching,
         "convergence": convergence,
         "multi_scene": multi,

@@ -333,6 +333,18 @@ int viper_cuda_error(const viper_scene *scene);
 /* Number of kernel launches the scene enqueued since creation. */
 long long viper_launch_count(const viper_scene *scene);
 
+/*
+ * Contact-pass counters of the scene's pill-pill passes (Sec. 7.2) since the
+ * previous call (or creation), summed over passes: out[0] candidate pairs,
+ * out[1] pairs the narrowphase searched (those not excluded by the certified
+ * early-out, whose projections on the line through the pill midpoints leave
+ * a gap larger than both radii), out[2] active constraints (C < 0).  Counted
+ * by the multi-kernel contact pass of large scenes; zero for solvers that do
+ * not use it.  Synchronises the scene stream and resets the counters.
+ * VIPER_EINVAL for a null scene or output.
+ */
+int viper_contact_stats(viper_scene *scene, long long out[3]);
+
 /* ------------------------------------------------------------------------
  * Multi-scene step: one frame of many scenes with one launch sequence.
  * (The paper steps one scene at a time; this applies the same per-substep

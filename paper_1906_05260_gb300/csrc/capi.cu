@@ -920,10 +920,13 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     A(P.cell_count, P.table); A(P.cell_start, P.table + 1);
     A(s->d_scan_tmp, 4096);
     A(P.bar, 4); A(P.tile_sums, 1024);
+    A(P.contact_stats, pills ? 3 : 1);
+    A(s->xw, pills ? nv : 1);
 #undef A
 #undef AC
     cudaMemsetAsync(P.err, 0, sizeof(int), s->stream);
     cudaMemsetAsync(P.npairs, 0, sizeof(int), s->stream);
+    cudaMemsetAsync(P.contact_stats, 0, sizeof(unsigned long long) * (pills ? 3 : 1), s->stream);
     cudaMemsetAsync(P.acc, 0, sizeof(unsigned long long) * 4 * (size_t)(cp ? nv : 1), s->stream);
     cudaMemsetAsync(P.cnt, 0, sizeof(int) * (size_t)(cp ? nv : 1), s->stream);
     cudaMemsetAsync(P.cell_count, 0, sizeof(int) * (size_t)P.table, s->stream);
@@ -1074,6 +1077,19 @@ int viper_scene_counts(const viper_scene *s, int *n_rods, int *n_verts, int *n_s
 }
 
 long long viper_launch_count(const viper_scene *s) { return s ? s->launches : 0; }
+
+int viper_contact_stats(viper_scene *s, long long out[3])
+{
+    if (!s || !out) return VIPER_EINVAL;
+    out[0] = out[1] = out[2] = 0;
+    if (!(s->flags & VIPER_FLAG_CONTACTS)) return VIPER_OK;
+    unsigned long long h[3] = {0, 0, 0};
+    VCHECK(cudaStreamSynchronize(s->stream));
+    VCHECK(cudaMemcpy(h, s->P.contact_stats, sizeof h, cudaMemcpyDeviceToHost));
+    VCHECK(cudaMemset(s->P.contact_stats, 0, sizeof h));
+    for (int k = 0; k < 3; ++k) out[k] = (long long)h[k];
+    return VIPER_OK;
+}
 
 int viper_cuda_error(const viper_scene *s) { return s ? s->last_cuda : 0; }
 

@@ -88,26 +88,20 @@ __global__ void bp_scatter_kernel(Params P)
     }
 }
 
-// Pair search: the work list is kEmitUnits units per cell (emit_cell) followed
-// by one unit per oversized pill (emit_big), one warp per unit.
+// Pair search: a thread per grid pill in cell order (emit_pills), then a warp
+// per oversized pill (emit_big).
 constexpr int kEmitWarps = 8;
-__global__ void __launch_bounds__(32 * kEmitWarps) bp_emit_kernel(Params P)
+__global__ void __launch_bounds__(32 * kEmitWarps, 4) bp_emit_kernel(Params P)
 {
+    __shared__ int2 buf[kEmitWarps][kPairBuf];
     const Grid G = *P.grid;
     if (G.pad) return;  // no valid grid: no candidates
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * kEmitWarps;
-    const int cells = grid_cells(P.grid, P.table);
+    const int warp = blockIdx.x * kEmitWarps + wib, nwarps = gridDim.x * kEmitWarps;
+    const int n_grid = P.cell_start[grid_cells(P.grid, P.table)];  // pills in the cells
+    emit_pills(P, G, n_grid, warp, nwarps, buf[wib], lane);
     const int nb = min(P.bp_hist[kRadBins], P.big_cap);
-    const int units = kEmitUnits * cells;
-    const int *cs = P.cell_start;
-    auto start = [cs](int c) { return cs[c]; };
-    for (int u = blockIdx.x * kEmitWarps + wib; u < units + nb; u += nwarps) {
-        if (u < units)
-            emit_cell<4>(P, G, u, start);
-        else
-            emit_big(P, G, u - units, nb, lane);
-    }
+    for (int i = warp; i < nb; i += nwarps) emit_big(P, G, i, nb, lane);
 }
 
 // ---------------------------------------------------------------- exclusive scan
@@ -241,7 +235,7 @@ void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_s
         bp_scatter_kernel<<<grid, 256, 0, st>>>(P);
     }
     {
-        int eg = (P.ns + 8 * kEmitWarps - 1) / (8 * kEmitWarps);  // a warp per 8 pills: a few units each
+        int eg = (P.ns + 32 * kEmitWarps - 1) / (32 * kEmitWarps);  // a thread per pill
         if (eg > 8 * device_sm_count()) eg = 8 * device_sm_count();
         if (eg < 1) eg = 1;
         ProfScope ps(s, PROF_PAIRS);
@@ -254,9 +248,12 @@ void launch_broadphase(viper_scene *s) { broadphase_enqueue(s->P, s->ls, s->d_sc
 
 // ---------------------------------------------------------------- contact pass
 constexpr int kContactThreads = 256;
-__global__ void __launch_bounds__(kContactThreads) contact_kernel(Params P)
+__global__ void __launch_bounds__(kContactThreads, 3) contact_kernel(Params P)
 {
     __shared__ int queue[kContactThreads / 32][64];
+    __shared__ unsigned long long stats[2];
+    if (threadIdx.x < 2) stats[threadIdx.x] = 0;
+    __syncthreads();
     const int np_all = *P.npairs;
     const int np = min(np_all, P.max_pairs);
     if (blockIdx.x == 0 && threadIdx.x == 0 && np_all > P.max_pairs) atomicOr(P.err, ERR_OVERFLOW);
@@ -264,16 +261,29 @@ __global__ void __launch_bounds__(kContactThreads) contact_kernel(Params P)
     const float at = P.contact_alpha * P.inv_h2;
     const int threads = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    int2 counts = make_int2(0, 0);
     if (!P.contact_threads && (long long)np * 16 <= threads) {
         // few pairs: a warp per pair (at most two per warp), as in the batched pass
-        for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < np; i += threads >> 5)
-            contact_pair_warp(P, i, at, lane);
+        for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < np; i += threads >> 5) {
+            const int r = contact_pair_warp(P, i, at, lane);
+            counts.x += r & 1;
+            counts.y += r >> 1;
+        }
     } else {
         // many pairs: a thread per pair, the pairs that may touch compacted per warp
-        contact_pairs_compacted(P, np, at, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threads >> 5,
-                                queue[threadIdx.x >> 5], lane);
+        counts = contact_pairs_compacted(P, np, at, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threads >> 5,
+                                         queue[threadIdx.x >> 5], lane);
+    }
+    if (P.contact_stats && lane == 0 && (counts.x | counts.y)) {
+        atomicAdd(stats, (unsigned long long)counts.x);
+        atomicAdd(stats + 1, (unsigned long long)counts.y);
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nvp; i += threads) contact_planes(P, i, at);
+    if (P.contact_stats) {
+        __syncthreads();
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(P.contact_stats, (unsigned long long)np);
+        if (threadIdx.x < 2 && stats[threadIdx.x]) atomicAdd(P.contact_stats + 1 + threadIdx.x, stats[threadIdx.x]);
+    }
 }
 
 // CTAs of the contact pass: as many as stay resident (grid-stride loops inside)
@@ -299,7 +309,7 @@ void launch_contacts(viper_scene *s)
     const int cap = s->P.max_pairs + (s->P.n_planes > 0 ? s->P.nv : 0);
     const int grid = contact_grid(cap);
     ProfScope ps(s, PROF_CONTACT);
-    contact_kernel<<<grid, kContactThreads, 0, s->ls>>>(s->P);
+    contact_kernel<<<grid, kContactThreads, 0, s->ls>>>(contact_path_params(s));
     s->launches++;
 }
 

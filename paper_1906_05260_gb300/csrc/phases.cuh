@@ -101,6 +101,14 @@ __device__ __forceinline__ float4 warm_vertex(const Params &P, int v, float4 x)
     return x;
 }
 
+// World position and radius of vertex v (x + its rod's origin, scale x rest
+// radius) with the operations contact_load uses: the packed form of XW.
+__device__ __forceinline__ float4 world_pack(const Params &P, int v, float4 x)
+{
+    const float4 o = P.rod_origin[P.rod_of_v[v]];
+    return make_float4(__fadd_rn(x.x, o.x), __fadd_rn(x.y, o.y), __fadd_rn(x.z, o.z), __fmul_rn(x.w, P.RV0[v].w));
+}
+
 __device__ __forceinline__ float4 to_world(const Params &P, int v, float4 x)
 {
     float4 o = P.rod_origin[P.rod_of_v[v]];
@@ -641,6 +649,7 @@ __device__ __forceinline__ void rod_item(const Params &P, int b, int n_iter, boo
             check_finite(P, x);
         }
         P.X[v] = x;
+        if (P.XW) P.XW[v] = world_pack(P, v, x);
     }
     for (int j = threadIdx.x; j < item.w; j += blockDim.x) {
         const int g = item.z + j;
@@ -1050,6 +1059,92 @@ __device__ __forceinline__ void emit_warp_hits(const Params &P, bool hit, int a,
     }
 }
 
+// Candidate pairs of the grid's pills, a thread per pill in cell order
+// (lane: entry p of the cell-order copies, pills p0 .. p0 + 31 per warp step):
+// each tests the pills of its own cell after it and those of the 13 forward
+// neighbour cells (dz = 1; dz = 0, dy = 1; dz = dy = 0, dx = 1), so every pair
+// of pills in neighbouring cells is tested once.  Consecutive lanes mostly
+// share a cell, hence the same neighbour lists (their loads are broadcasts).
+// Each list is walked for the warp's longest length (shorter lanes idle), so
+// that every step ends with one ballot: hits go to the warp's shared buffer
+// buf (kPairBuf pairs), which is flushed to the pair list with one atomic.
+constexpr int kPairBuf = 128;
+
+__device__ __forceinline__ void flush_pairs(const Params &P, const int2 *buf, int cnt, int lane)
+{
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(P.npairs, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int t = lane; t < cnt; t += 32) {
+        const int idx = base + t;
+        if (idx < P.max_pairs) {
+            const int2 pr = buf[t];
+            const int lo = min(pr.x, pr.y), hi = max(pr.x, pr.y);
+            P.pairs[idx] = make_int2(lo, hi);
+            if (P.pair_v) P.pair_v[idx] = make_int2(P.seg_v0[lo], P.seg_v0[hi]);
+            if (P.lam_pair) P.lam_pair[idx] = 0.f;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void emit_pills(const Params &P, const Grid &G, int n_grid, int warp, int nwarps,
+                                           int2 *buf, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    int cnt = 0;  // pairs in buf (uniform over the warp)
+    for (int p0 = warp * 32; p0 < n_grid; p0 += nwarps * 32) {
+        const int p = p0 + lane;
+        const bool own = p < n_grid;
+        float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
+        int ga = 0, ia = 0, ix = 0, iy = 0, iz = 0;
+        if (own) {
+            sa = P.cell_sph[p];
+            ga = P.cell_grp[p];
+            ia = P.cell_pills[p];
+            ix = cell_coord(sa.x, G.lo[0], G.inv_cell, G.dim[0]);
+            iy = cell_coord(sa.y, G.lo[1], G.inv_cell, G.dim[1]);
+            iz = cell_coord(sa.z, G.lo[2], G.inv_cell, G.dim[2]);
+        }
+        for (int k = 0; k < 14; ++k) {
+            int d0 = 0, d1 = 0;
+            if (own) {
+                int dx = 0, dy = 0, dz = 0;
+                if (k < 9) {
+                    dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
+                } else if (k < 12) {
+                    dx = k - 10; dy = 1;
+                } else if (k == 12) {
+                    dx = 1;
+                }
+                const int x = ix + dx, y = iy + dy, z = iz + dz;
+                if (x >= 0 && x < G.dim[0] && y >= 0 && y < G.dim[1] && z < G.dim[2]) {
+                    const int d = x + G.dim[0] * (y + G.dim[1] * z);
+                    d0 = k == 13 ? p + 1 : P.cell_start[d];
+                    d1 = P.cell_start[d + 1];
+                }
+            }
+            const int len = d1 - d0;
+            const int steps = __reduce_max_sync(full, len > 0 ? len : 0);
+            for (int j = 0; j < steps; ++j) {
+                const int q = d0 + j;
+                const bool hit = j < len && P.cell_grp[q] != ga && spheres_overlap(sa, P.cell_sph[q]);
+                const unsigned m = __ballot_sync(full, hit);
+                if (m) {
+                    if (cnt + 32 > kPairBuf) {
+                        flush_pairs(P, buf, cnt, lane);
+                        cnt = 0;
+                    }
+                    if (hit) buf[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(ia, P.cell_pills[q]);
+                    cnt += __popc(m);
+                }
+            }
+        }
+    }
+    if (cnt) flush_pairs(P, buf, cnt, lane);
+}
+
 // Candidate pairs of oversized pill i of the list (bounding radius above the
 // grid's cut), by one warp: (1) against the pills in the cells of the box
 // centre +- (R_i + r_cut)(1 + 2^-8) -- a grid pill overlapping pill i has its
@@ -1281,6 +1376,16 @@ struct ContactPair {
 
 __device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair &c)
 {
+    if (P.XW) {
+        // world positions and radii packed by the preceding sweep: the pair's
+        // first vertices and four 16-byte gathers (rest radii: only if active)
+        const int2 pv = P.pair_v[i];
+        const float4 xa1 = P.XW[pv.x], xa2 = P.XW[pv.x + 1], xb1 = P.XW[pv.y], xb2 = P.XW[pv.y + 1];
+        c.vs[0] = pv.x; c.vs[1] = pv.x + 1; c.vs[2] = pv.y; c.vs[3] = pv.y + 1;
+        c.Q.a1 = xyz(xa1); c.Q.a2 = xyz(xa2); c.Q.b1 = xyz(xb1); c.Q.b2 = xyz(xb2);
+        c.Q.ra1 = xa1.w; c.Q.ra2 = xa2.w; c.Q.rb1 = xb1.w; c.Q.rb2 = xb2.w;
+        return;
+    }
     const int2 pr = P.pairs[i];
     // the segments' first vertices, stored beside the pair by the pair search
     // (one dependent load less on the contact pass's chain)
@@ -1296,29 +1401,33 @@ __device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair
     c.vs[0] = va; c.vs[1] = va + 1; c.vs[2] = vb; c.vs[3] = vb + 1;
     c.rbar[0] = P.RV0[va].w; c.rbar[1] = P.RV0[va + 1].w; c.rbar[2] = P.RV0[vb].w; c.rbar[3] = P.RV0[vb + 1].w;
     c.Q.a1 = xyz(xa1); c.Q.a2 = xyz(xa2); c.Q.b1 = xyz(xb1); c.Q.b2 = xyz(xb2);
-    c.Q.ra1 = xa1.w * c.rbar[0]; c.Q.ra2 = xa2.w * c.rbar[1]; c.Q.rb1 = xb1.w * c.rbar[2]; c.Q.rb2 = xb2.w * c.rbar[3];
+    c.Q.ra1 = __fmul_rn(xa1.w, c.rbar[0]); c.Q.ra2 = __fmul_rn(xa2.w, c.rbar[1]);
+    c.Q.rb1 = __fmul_rn(xb1.w, c.rbar[2]); c.Q.rb2 = __fmul_rn(xb2.w, c.rbar[3]);
 }
 
 // The update of pair i at contact parameter al; vertices t0, t0 + tstep, ...
 // of the four are accumulated by this thread, and the multiplier is stored if
 // write_lam.  With `warp` all 32 lanes handle the same pair (the early return
 // is uniform) and the multiplier is written only after every lane has read it.
-__device__ __forceinline__ void contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
+__device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
                                               int tstep, bool write_lam, bool warp)
 {
     float be;
     const float C = coll_f(c.Q, al, be);
     V3 d = lerp3(c.Q.a1, c.Q.a2, al) - lerp3(c.Q.b1, c.Q.b2, be);
     float dist = sqrtf(dot(d, d));
-    if (!(C < 0.f) || dist < 1e-12f) return;
+    if (!(C < 0.f) || dist < 1e-12f) return false;
     V3 n = (1.f / dist) * d;
+    float rbar[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) rbar[t] = P.XW ? P.RV0[c.vs[t]].w : c.rbar[t];
     const float4 m1 = P.RV1[c.vs[0]], m2 = P.RV1[c.vs[1]], m3 = P.RV1[c.vs[2]], m4 = P.RV1[c.vs[3]];
     const float wt[4] = {1.f - al, al, -(1.f - be), -be};
     const float wx[4] = {inv_mass(m1), inv_mass(m2), inv_mass(m3), inv_mass(m4)};
     const float wsv[4] = {m1.y, m2.y, m3.y, m4.y};
     float den = at;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * c.rbar[t] * c.rbar[t];
+    for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * rbar[t] * rbar[t];
     const float lam = P.lam_pair[i];
     const float dl = (-C - at * lam) / den;
     if (warp) __syncwarp();
@@ -1326,7 +1435,8 @@ __device__ __forceinline__ void contact_apply(const Params &P, int i, float at, 
 #pragma unroll
     for (int t = 0; t < 4; ++t)
         if (t >= t0 && (t - t0) % tstep == 0)
-            acc_add(P, c.vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * c.rbar[t] * dl);
+            acc_add(P, c.vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * rbar[t] * dl);
+    return true;
 }
 
 // Certified early-out of the narrowphase.  The distance D of the two axis
@@ -1355,19 +1465,22 @@ __device__ __forceinline__ void contact_pair(const Params &P, int i, float at)
     ContactPair c;
     contact_load(P, i, c);
     if (!contact_may_touch(c.Q)) return;
+    pill_pair_axis(c.Q);
     contact_apply(P, i, at, c, dichotomous(c.Q), 0, 1, true, false);
 }
 
 // Pair i by one warp (all lanes call): the search four steps per round
 // (dichotomous_warp), lane t < 4 accumulates vertex t, lane 0 stores the
-// multiplier.  Same result as contact_pair, bit for bit.
-__device__ __forceinline__ void contact_pair_warp(const Params &P, int i, float at, int lane)
+// multiplier.  Same result as contact_pair, bit for bit.  Returns 0 (skipped
+// by the early-out), 1 (searched) or 3 (searched, constraint active).
+__device__ __forceinline__ int contact_pair_warp(const Params &P, int i, float at, int lane)
 {
     ContactPair c;
     contact_load(P, i, c);
-    if (!contact_may_touch(c.Q)) return;  // uniform over the warp
+    if (!contact_may_touch(c.Q)) return 0;  // uniform over the warp
+    pill_pair_axis(c.Q);
     const float al = dichotomous_warp(c.Q, lane);
-    contact_apply(P, i, at, c, al, lane, 4, lane == 0, true);
+    return contact_apply(P, i, at, c, al, lane, 4, lane == 0, true) ? 3 : 1;
 }
 
 // Pairs [0, np) a thread each, by the calling warp from chunk `chunk` of 32
@@ -1375,11 +1488,13 @@ __device__ __forceinline__ void contact_pair_warp(const Params &P, int i, float 
 // (contact_may_touch) are queued in the warp's buffer q (64 ints of shared
 // memory) and searched 32 at a time, so that the search runs on full warps
 // however sparse the touching pairs are.  Same results as contact_pair.
-__device__ __forceinline__ void contact_pairs_compacted(const Params &P, int np, float at, int chunk, int stride,
+// Returns the warp's counts (searched, active), the same in every lane.
+__device__ __forceinline__ int2 contact_pairs_compacted(const Params &P, int np, float at, int chunk, int stride,
                                                         int *q, int lane)
 {
     const unsigned full = 0xffffffffu;
     int qn = 0;  // queued pairs (uniform over the warp)
+    int2 counts = make_int2(0, 0);
     for (int base = chunk * 32; base < np; base += stride * 32) {
         const int i = base + lane;
         bool maybe = false;
@@ -1396,20 +1511,28 @@ __device__ __forceinline__ void contact_pairs_compacted(const Params &P, int np,
             const int j = q[lane];
             ContactPair c;
             contact_load(P, j, c);
-            contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+            pill_pair_axis(c.Q);
+            const bool act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+            counts.x += 32;
+            counts.y += __popc(__ballot_sync(full, act));
             __syncwarp();
             qn -= 32;
             if (lane < qn) q[lane] = q[lane + 32];
             __syncwarp();
         }
     }
+    bool act = false;
     if (lane < qn) {
         const int j = q[lane];
         ContactPair c;
         contact_load(P, j, c);
-        contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+        pill_pair_axis(c.Q);
+        act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
     }
+    counts.x += qn;
+    counts.y += __popc(__ballot_sync(full, act));
     __syncwarp();
+    return counts;
 }
 
 // Half-plane constraints of vertex v's sphere (Sec. 7).

@@ -262,12 +262,21 @@ void launch_rod_full(viper_scene *s, int n_iter)
     s->launches++;
 }
 
+Params contact_path_params(const viper_scene *s)
+{
+    Params P = s->P;
+    P.XW = (s->mode == VIPER_SOLVER_BATCHED && (s->flags & VIPER_FLAG_CONTACTS) && s->resident_nv == s->nv)
+               ? s->xw
+               : nullptr;
+    return P;
+}
+
 void launch_rod_iter(viper_scene *s, bool first, bool apply)
 {
     if (s->n_items <= 0) return;
     ProfScope ps(s, PROF_ROD);
-    rod_kernel<false><<<s->n_items, s->block_threads, s->smem_iter, s->ls>>>(s->P, 1, first ? 1 : 0,
-                                                                                 apply ? 1 : 0);
+    rod_kernel<false><<<s->n_items, s->block_threads, s->smem_iter, s->ls>>>(contact_path_params(s), 1,
+                                                                                 first ? 1 : 0, apply ? 1 : 0);
     s->launches++;
 }
 

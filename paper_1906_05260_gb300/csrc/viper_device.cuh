@@ -486,28 +486,67 @@ __device__ __forceinline__ void project_laplacian(float &sp, float &s, float &sn
 // Closed-form closest sphere of a tapered capsule (App. D): t = (a - h tan th)/l
 // clamped, sin th = (r1 - r2)/l; one end sphere containing the other -> the
 // larger one; degenerate axis -> 0.
-__device__ __forceinline__ float pill_project(V3 c1, float r1, V3 c2, float r2, V3 x)
+// The axis of pill (c1, r1) -> (c2, r2) as pill_project needs it: unit
+// direction, length and the tangent of the cone angle, computed once per pill
+// and reused for every point projected onto it (the same operations as a
+// fresh projection, hence the same result bit for bit).  fixed >= 0: the
+// projection of every point (degenerate axis, or one end sphere containing
+// the other).
+struct PillAxis {
+    V3 c1, u;
+    float l, tn, fixed;
+};
+
+__device__ __forceinline__ PillAxis pill_axis(V3 c1, float r1, V3 c2, float r2)
 {
+    PillAxis A;
+    A.c1 = c1;
+    A.u = v3(0.f, 0.f, 0.f);
+    A.tn = 0.f;
     V3 e = c2 - c1;
     float l = sqrtf(dot(e, e));
-    if (l < 1e-12f) return 0.f;
-    V3 u = (1.f / l) * e;
-    V3 rel = x - c1;
-    float a = dot(rel, u);
-    V3 perp = rel - a * u;
-    float hh = sqrtf(dot(perp, perp));
+    A.l = l;
+    if (l < 1e-12f) {
+        A.fixed = 0.f;
+        return A;
+    }
+    A.u = (1.f / l) * e;
     float dr = r1 - r2;
-    if (fabsf(dr) >= l) return dr >= 0.f ? 0.f : 1.f;
+    if (fabsf(dr) >= l) {
+        A.fixed = dr >= 0.f ? 0.f : 1.f;
+        return A;
+    }
     float sn = dr / l;
-    float tn = sn * rsqrtf(1.f - sn * sn);
-    float t = (a - hh * tn) / l;
+    A.tn = sn * rsqrtf(1.f - sn * sn);
+    A.fixed = -1.f;
+    return A;
+}
+
+__device__ __forceinline__ float pill_project_on(const PillAxis &A, V3 x)
+{
+    if (A.fixed >= 0.f) return A.fixed;
+    V3 rel = x - A.c1;
+    float a = dot(rel, A.u);
+    V3 perp = rel - a * A.u;
+    float hh = sqrtf(dot(perp, perp));
+    float t = (a - hh * A.tn) / A.l;
     return fminf(fmaxf(t, 0.f), 1.f);
 }
 
+__device__ __forceinline__ float pill_project(V3 c1, float r1, V3 c2, float r2, V3 x)
+{
+    return pill_project_on(pill_axis(c1, r1, c2, r2), x);
+}
+
+// A pair of pills for the narrowphase; axb (pill b's axis) is set by
+// pill_pair_axis before the search.
 struct PillPair {
     V3 a1, a2, b1, b2;
     float ra1, ra2, rb1, rb2;
+    PillAxis axb;
 };
+
+__device__ __forceinline__ void pill_pair_axis(PillPair &P) { P.axb = pill_axis(P.b1, P.rb1, P.b2, P.rb2); }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return (1.f - t) * a + t * b; }
 __device__ __forceinline__ V3 lerp3(V3 a, V3 b, float t) { return (1.f - t) * a + t * b; }
@@ -517,7 +556,7 @@ __device__ __forceinline__ float coll_f(const PillPair &P, float al, float &be)
 {
     V3 pa = lerp3(P.a1, P.a2, al);
     float ra = lerpf(P.ra1, P.ra2, al);
-    be = pill_project(P.b1, P.rb1, P.b2, P.rb2, pa);
+    be = pill_project_on(P.axb, pa);
     V3 d = pa - lerp3(P.b1, P.b2, be);
     return sqrtf(dot(d, d)) - ra - lerpf(P.rb1, P.rb2, be);
 }

@@ -97,6 +97,12 @@ struct Params {
     float *lam_pair, *lam_plane;
     unsigned long long *acc;
     int *cnt;
+    // world position and radius per vertex (x + rod origin, s rbar), written by the
+    // shared-memory sweep before each contact pass and read by it; null: not used
+    float4 *XW;
+    // contact-pass counters (null: not counted): candidate pairs, pairs searched by
+    // the narrowphase (not excluded by the certified early-out), active constraints
+    unsigned long long *contact_stats;
     // broadphase: rest radius of vertex v is bp_rbar[v * bp_rbar_stride]
     const float *bp_rbar;
     int bp_rbar_stride;
@@ -203,6 +209,9 @@ struct viper_scene {
     int *h_err = nullptr;
     int *d_herr = nullptr;  // its device address
     void *self_table = nullptr;  // one-scene table of the multi-scene kernels (graph path)
+    // world pack of the multi-kernel contact path (Params::XW), set only in the
+    // launch arguments of its sweeps and contact passes
+    float4 *xw = nullptr;
     // scratch for host-pointer skinning
     float4 *skin_buf = nullptr;
     size_t skin_cap = 0;
@@ -250,6 +259,9 @@ void launch_broadphase(viper_scene *s);
 // seg_v0, seg_group, grid buffers, pairs, npairs); `s` may be null (no scene).
 void broadphase_enqueue(const Params &P, cudaStream_t st, int *scan_tmp, viper_scene *s);
 void launch_contacts(viper_scene *s);
+// Params of the multi-kernel contact path's sweeps and contact passes: the
+// scene's, with the world pack when every rod runs in the shared-memory sweep.
+Params contact_path_params(const viper_scene *s);
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out);
 int device_sm_count();  // SMs of the current device (cached)
 void launch_bundles(viper_scene *s);

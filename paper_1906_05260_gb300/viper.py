@@ -130,6 +130,7 @@ def lib():
         L.viper_batch_launch_count.restype = C.c_longlong
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
+        L.viper_contact_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.viper_error_string.argtypes = [C.c_int]
         L.viper_error_string.restype = C.c_char_p
         _lib = L
@@ -421,6 +422,13 @@ class Scene:
 
     def launch_count(self) -> int:
         return int(lib().viper_launch_count(self._h))
+
+    def contact_stats(self):
+        """(candidate pairs, searched pairs, active constraints) summed over the
+        contact passes since the previous call; resets the counters."""
+        out = (C.c_longlong * 3)()
+        _check(lib().viper_contact_stats(self._h, out), "viper_contact_stats")
+        return int(out[0]), int(out[1]), int(out[2])
 
 
 def broadphase(rod_offsets, group, x4, rbar, max_pairs, stream=None):
