@@ -49,6 +49,7 @@ extern "C" {
 #define VIPER_EOVERFLOW -5   /* more candidate pairs than the pair buffer holds   */
 #define VIPER_ETIMEOUT -6    /* a bounded device wait expired                     */
 #define VIPER_EBUDGET -7     /* admission refused: memory budget exceeded         */
+#define VIPER_ENOCONV -8     /* a bundle's rotation extraction did not converge   */
 
 #define VIPER_FLAG_CONTACTS 1 /* pill-pill contacts (Sec. 7.1, 7.2)                */
 #define VIPER_FLAG_VOLUME 2   /* volume constraints (Sec. 5 "Volume potential")    */

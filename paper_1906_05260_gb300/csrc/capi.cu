@@ -585,6 +585,7 @@ int decode_err(int e)
     if (e & ERR_NONFINITE) return VIPER_ENONFINITE;
     if (e & ERR_OVERFLOW) return VIPER_EOVERFLOW;
     if (e & ERR_TIMEOUT) return VIPER_ETIMEOUT;
+    if (e & ERR_NOCONV) return VIPER_ENOCONV;
     return VIPER_OK;
 }
 
@@ -666,6 +667,7 @@ const char *viper_error_string(int code)
     case VIPER_EOVERFLOW: return "candidate-pair buffer overflow";
     case VIPER_ETIMEOUT: return "bounded device wait expired";
     case VIPER_EBUDGET: return "memory budget exceeded";
+    case VIPER_ENOCONV: return "rotation extraction of a bundle did not converge";
     default: return "unknown error";
     }
 }

@@ -1068,7 +1068,7 @@ __device__ __forceinline__ void emit_warp_hits(const Params &P, bool hit, int a,
 // Each list is walked for the warp's longest length (shorter lanes idle), so
 // that every step ends with one ballot: hits go to the warp's shared buffer
 // buf (kPairBuf pairs), which is flushed to the pair list with one atomic.
-constexpr int kPairBuf = 128;
+constexpr int kPairBuf = 160;  // after a flush it holds one step's hits (at most 4 x 32)
 
 __device__ __forceinline__ void flush_pairs(const Params &P, const int2 *buf, int cnt, int lane)
 {
@@ -1127,17 +1127,37 @@ __device__ __forceinline__ void emit_pills(const Params &P, const Grid &G, int n
             }
             const int len = d1 - d0;
             const int steps = __reduce_max_sync(full, len > 0 ? len : 0);
-            for (int j = 0; j < steps; ++j) {
-                const int q = d0 + j;
-                const bool hit = j < len && P.cell_grp[q] != ga && spheres_overlap(sa, P.cell_sph[q]);
-                const unsigned m = __ballot_sync(full, hit);
-                if (m) {
-                    if (cnt + 32 > kPairBuf) {
+            // four candidates per step: their loads are issued before any test
+            for (int j = 0; j < steps; j += 4) {
+                float4 cs[4];
+                int cg[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int q = d0 + j + t;
+                    if (j + t < len) {
+                        cs[t] = P.cell_sph[q];
+                        cg[t] = P.cell_grp[q];
+                    }
+                }
+                unsigned m[4];
+                bool hit[4];
+                int nh = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    hit[t] = j + t < len && cg[t] != ga && spheres_overlap(sa, cs[t]);
+                    m[t] = __ballot_sync(full, hit[t]);
+                    nh += __popc(m[t]);
+                }
+                if (nh) {
+                    if (cnt + nh > kPairBuf) {
                         flush_pairs(P, buf, cnt, lane);
                         cnt = 0;
                     }
-                    if (hit) buf[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2(ia, P.cell_pills[q]);
-                    cnt += __popc(m);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (hit[t]) buf[cnt + __popc(m[t] & ((1u << lane) - 1u))] = make_int2(ia, P.cell_pills[d0 + j + t]);
+                        cnt += __popc(m[t]);
+                    }
                 }
             }
         }
@@ -1439,24 +1459,49 @@ __device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, 
     return true;
 }
 
-// Certified early-out of the narrowphase.  The distance D of the two axis
-// segments is at least the gap between their projections on the line through
-// their midpoints, |e| - (|e.da| + |e.db|) / (2 |e|) (e = ma - mb).  Every probe
-// of the search evaluates C = |pa - pb| - ra - rb >= D - max(ra) - max(rb), so
-// when the gap exceeds the larger radius of each pill by a margin (1e-3 of the
+// Certified early-out of the narrowphase.  Every probe of the search
+// evaluates C = |pa - pb| - ra - rb >= D - max(ra) - max(rb), D the distance
+// of the two axis segments, and for any direction n, D is at least the gap
+// between the segments' projections on n:
+//   gap(n) |n| = |n.e| - (|n.da| + |n.db|) / 2,   e = ma - mb (midpoints).
+// When gap(n) exceeds the larger radius of each pill by a margin (1e-3 of the
 // radii plus 1e-5 of the coordinates' magnitude, far above the FP32 rounding
-// of either computation) the search could only find C > 0: the pair is
-// inactive and skipping it changes no result.  Returns false in that case.
+// of either computation), the search could only find C > 0: the pair is
+// inactive and skipping it changes no result.  Two directions are tried: the
+// line through the midpoints, then the direction between the closest points
+// of the axes (clamped closed form; its rounding only loosens the bound).
+// Returns false when either certifies the pair inactive.
+__device__ __forceinline__ bool sat_separated(V3 n, V3 e, V3 da, V3 db, float lim)
+{
+    const float nn = dot(n, n);
+    return nn > 0.f && fabsf(dot(n, e)) - 0.5f * (fabsf(dot(n, da)) + fabsf(dot(n, db))) > lim * sqrtf(nn);
+}
+
 __device__ __forceinline__ bool contact_may_touch(const PillPair &Q)
 {
     const V3 ma = 0.5f * (Q.a1 + Q.a2), mb = 0.5f * (Q.b1 + Q.b2);
     const V3 e = ma - mb, da = Q.a2 - Q.a1, db = Q.b2 - Q.b1;
-    const float d2 = dot(e, e), el = sqrtf(d2);
     const float rho = fmaxf(Q.ra1, Q.ra2) + fmaxf(Q.rb1, Q.rb2);
     const float mag = fmaxf(fmaxf(fmaxf(fabsf(ma.x), fabsf(ma.y)), fmaxf(fabsf(ma.z), fabsf(mb.x))),
                             fmaxf(fabsf(mb.y), fabsf(mb.z)));
-    const float margin = 1e-3f * rho + 1e-5f * mag;
-    return !(d2 - 0.5f * (fabsf(dot(e, da)) + fabsf(dot(e, db))) > (rho + margin) * el);
+    const float lim = rho + 1e-3f * rho + 1e-5f * mag;
+    if (sat_separated(e, e, da, db, lim)) return false;
+    // closest points a1 + s da, b1 + t db of the two axes, s, t in [0, 1]
+    const V3 r = Q.a1 - Q.b1;
+    const float a = dot(da, da), b = dot(da, db), c = dot(da, r), ee = dot(db, db), f = dot(db, r);
+    if (!(a > 0.f) || !(ee > 0.f)) return true;
+    const float den = a * ee - b * b;
+    float sp = den > 1e-6f * a * ee ? fminf(fmaxf((b * f - c * ee) / den, 0.f), 1.f) : 0.f;
+    float tq = (b * sp + f) / ee;
+    if (tq < 0.f) {
+        tq = 0.f;
+        sp = fminf(fmaxf(-c / a, 0.f), 1.f);
+    } else if (tq > 1.f) {
+        tq = 1.f;
+        sp = fminf(fmaxf((b - c) / a, 0.f), 1.f);
+    }
+    const V3 n = (Q.a1 + sp * da) - (Q.b1 + tq * db);
+    return !sat_separated(n, e, da, db, lim);
 }
 
 // Pair i by one thread.
@@ -1559,10 +1604,14 @@ __device__ __forceinline__ void contact_planes(const Params &P, int v, float at)
 // rotation extraction of Mueller et al. 2016 ("A Robust Method to Extract the
 // Rotational Part of Deformations"): with r_k, a_k the columns of R(q) and A,
 // turn q by the axis-angle w = sum_k r_k x a_k / (|sum_k r_k . a_k| + eps)
-// until the step vanishes.  Starts from the identity.
-__device__ __forceinline__ float4 extract_rotation(const float *A)
+// until the step vanishes.  Starts from q0 (the method converges in a few
+// steps from a start near the answer; from far away, e.g. the identity
+// against a half turn, it needs many).  *converged is false when the 32-step
+// cap is reached with a step above 1e-5 rad.
+__device__ __forceinline__ float4 extract_rotation(const float *A, float4 q0, bool *converged)
 {
-    float4 q = make_float4(0.f, 0.f, 0.f, 1.f);
+    float4 q = q0;
+    bool done = false;
 #pragma unroll 1
     for (int it = 0; it < 32; ++it) {
         const V3 r0 = qrot(q, v3(1.f, 0.f, 0.f)), r1 = qrot(q, v3(0.f, 1.f, 0.f)), r2 = qrot(q, v3(0.f, 0.f, 1.f));
@@ -1571,10 +1620,15 @@ __device__ __forceinline__ float4 extract_rotation(const float *A)
         const float den = fabsf(dot(r0, a0) + dot(r1, a1) + dot(r2, a2)) + 1e-20f;
         const V3 w = (1.f / den) * num;
         const float ang = sqrtf(dot(w, w));
-        if (!(ang > 1e-7f)) break;
+        if (!(ang > 1e-7f)) {
+            done = true;
+            break;
+        }
         const float sh = sinf(0.5f * ang) / ang;
         q = qnormalize(qmul(make_float4(sh * w.x, sh * w.y, sh * w.z, cosf(0.5f * ang)), q));
+        if (it == 31) done = ang <= 1e-5f;
     }
+    *converged = done;
     return q;
 }
 
@@ -1635,7 +1689,19 @@ __device__ __forceinline__ void match_cross_section(const Params &P, int c)
     for (int k = 0; k < 9; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) A[k] += __shfl_xor_sync(full, A[k], o);
-    const float4 qs = extract_rotation(A);
+    // start from the frame rotation R R_bar^T of the first member with a frame
+    // segment (the members' frames turn with the cross-section)
+    const unsigned framed = __ballot_sync(full, mine && g >= 0);
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (framed) {
+        const int src = __ffs(framed) - 1;
+        const float4 qq = qnormalize(qmul(q, qconj(qb)));
+        q0 = make_float4(__shfl_sync(full, qq.x, src), __shfl_sync(full, qq.y, src), __shfl_sync(full, qq.z, src),
+                         __shfl_sync(full, qq.w, src));
+    }
+    bool converged;
+    const float4 qs = extract_rotation(A, q0, &converged);
+    if (!converged && lane == 0) atomicOr(P.err, ERR_NOCONV);
     const V3 r0 = qrot(qs, v3(1.f, 0.f, 0.f)), r1 = qrot(qs, v3(0.f, 1.f, 0.f)), r2 = qrot(qs, v3(0.f, 0.f, 1.f));
     const float num = r0.x * A[0] + r0.y * A[3] + r0.z * A[6] + r1.x * A[1] + r1.y * A[4] + r1.z * A[7] +
                       r2.x * A[2] + r2.y * A[5] + r2.z * A[8];

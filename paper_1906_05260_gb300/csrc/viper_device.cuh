@@ -494,8 +494,17 @@ __device__ __forceinline__ void project_laplacian(float &sp, float &s, float &sn
 // the other).
 struct PillAxis {
     V3 c1, u;
-    float l, tn, fixed;
+    float inv_l, tn, fixed;
 };
+
+// Square root by the SFU's approximation (PTX sqrt.approx.f32: a few ulp,
+// +0 for +0), for the narrowphase probes, which need about 1e-6 relative.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 __device__ __forceinline__ PillAxis pill_axis(V3 c1, float r1, V3 c2, float r2)
 {
@@ -505,12 +514,13 @@ __device__ __forceinline__ PillAxis pill_axis(V3 c1, float r1, V3 c2, float r2)
     A.tn = 0.f;
     V3 e = c2 - c1;
     float l = sqrtf(dot(e, e));
-    A.l = l;
+    A.inv_l = 0.f;
     if (l < 1e-12f) {
         A.fixed = 0.f;
         return A;
     }
-    A.u = (1.f / l) * e;
+    A.inv_l = 1.f / l;
+    A.u = A.inv_l * e;
     float dr = r1 - r2;
     if (fabsf(dr) >= l) {
         A.fixed = dr >= 0.f ? 0.f : 1.f;
@@ -528,8 +538,8 @@ __device__ __forceinline__ float pill_project_on(const PillAxis &A, V3 x)
     V3 rel = x - A.c1;
     float a = dot(rel, A.u);
     V3 perp = rel - a * A.u;
-    float hh = sqrtf(dot(perp, perp));
-    float t = (a - hh * A.tn) / A.l;
+    float hh = sqrt_approx(dot(perp, perp));
+    float t = (a - hh * A.tn) * A.inv_l;
     return fminf(fmaxf(t, 0.f), 1.f);
 }
 
@@ -558,7 +568,7 @@ __device__ __forceinline__ float coll_f(const PillPair &P, float al, float &be)
     float ra = lerpf(P.ra1, P.ra2, al);
     be = pill_project_on(P.axb, pa);
     V3 d = pa - lerp3(P.b1, P.b2, be);
-    return sqrtf(dot(d, d)) - ra - lerpf(P.rb1, P.rb2, be);
+    return sqrt_approx(dot(d, d)) - ra - lerpf(P.rb1, P.rb2, be);
 }
 
 // Dichotomous search, 10 iterations (Sec. 7.2): probes mid -+ eps/2 with
