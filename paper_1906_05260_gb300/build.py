@@ -60,5 +60,32 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     return LIB
 
 
+WAIT_TEST_LIB = os.path.join(HERE, "libviper_waittest.so")
+
+
+def build_wait_test(force: bool = False) -> str:
+    """A test build of the library (libviper_waittest.so) whose frame kernel has
+    a short barrier spin limit and leaves the last CTA's barrier arrival out,
+    so that every grid-barrier wait runs out: the bounded-wait path (timeout
+    error, every CTA returns) exercised without a hang.  The other objects are
+    those of libviper.so."""
+    build()
+    if not force and os.path.exists(WAIT_TEST_LIB) and os.path.getmtime(WAIT_TEST_LIB) >= _newest_input():
+        return WAIT_TEST_LIB
+    obj = os.path.join(BUILD, "frame_waittest.o")
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-DVIPER_TEST_MISSING_ARRIVAL", "-DVIPER_BARRIER_SPINS=4096", "-c",
+           os.path.join(CSRC, "frame.cu"), "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for the wait-test frame.cu:\n{r.stdout}\n{r.stderr}")
+    objs = [os.path.join(BUILD, src.replace(".cu", ".o")) for src in SOURCES if src != "frame.cu"] + [obj]
+    tmp = WAIT_TEST_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, WAIT_TEST_LIB)
+    return WAIT_TEST_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))

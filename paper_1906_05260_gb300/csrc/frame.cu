@@ -25,7 +25,15 @@
 
 namespace viper {
 
-constexpr long long kBarrierSpins = 1LL << 24;  // ~1 s of 32 ns naps
+// Spin limit of a barrier wait: about 1 s of 32 ns naps.  A test build may set
+// a short one (VIPER_BARRIER_SPINS) and leave the last CTA's arrival out
+// (VIPER_TEST_MISSING_ARRIVAL), so that every wait runs out: the kernel then
+// raises ERR_TIMEOUT and every CTA returns -- the timeout path, exercised
+// without a hang.
+#ifndef VIPER_BARRIER_SPINS
+#define VIPER_BARRIER_SPINS (1LL << 24)
+#endif
+constexpr long long kBarrierSpins = VIPER_BARRIER_SPINS;
 constexpr int kScanPerThread = 16;
 constexpr int kMaxTiles = 1024;
 constexpr int kFrameWarps = 8;  // largest CTA: 256 threads
@@ -42,8 +50,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int nbl
         if (ok) {
             const unsigned int gen = vb[1];
             __threadfence();
-            const unsigned int prev = atomicAdd(bar, 1u);
-            if (prev == nblocks - 1u) {
+#ifdef VIPER_TEST_MISSING_ARRIVAL
+            const bool arrives = blockIdx.x + 1u != nblocks;
+#else
+            const bool arrives = true;
+#endif
+            const unsigned int prev = arrives ? atomicAdd(bar, 1u) : 0u;
+            if (arrives && prev == nblocks - 1u) {
                 vb[0] = 0u;  // nobody arrives again before the generation moves
                 __threadfence();
                 atomicAdd(bar + 1, 1u);
