@@ -311,8 +311,19 @@ def bench_batching(V, torch, flush, dist, peaks, peak_kind, fp32_peak_tflops, fr
     out = {"workload": "batching: 4096 rods, log-uniform 4-256 vertices (250,612 total), "
                        "random initial bends, 20 substeps x 8 iterations, no contacts"}
     units = sc.nv * sc.substeps
+    # the batched solver's CTA size and residency threshold from the autotuner
+    # (cached per GPU and scene under the package's build folder)
+    g = V.Scene(sc)
+    t0 = time.perf_counter()
+    (bw, rm), cached = g.autotune_cached(os.path.join(ROOT, "paper_1906_05260_gb300", "_build", "autotune.json"))
+    n_items, threads, resident = g.schedule()
+    out["autotuned"] = {"block_warps": bw, "resident_max": rm, "threads_per_cta": threads, "ctas": n_items,
+                        "rods_per_cta": sc.n_rods / max(n_items, 1), "resident_vertices": resident,
+                        "cached": cached, "tune_s": time.perf_counter() - t0}
+    g.close()
     for mode, name in ((V.SOLVER_FRAME, "frame"), (V.SOLVER_BATCHED, "batched"), (V.SOLVER_PLAIN, "plain")):
-        g = V.Scene(sc, solver=mode, resident_max=256)
+        g = (V.Scene(sc, solver=mode, block_warps=bw, resident_max=rm) if mode == V.SOLVER_BATCHED
+             else V.Scene(sc, solver=mode, resident_max=256))
         st = g.stream
         for _ in range(3):
             g.step()
@@ -672,29 +683,27 @@ def per_class_times(V, torch, g, stream, flush, frames, step):
 
 
 def contact_roofline(per_class, stats, sc, peak_tflops, peak_kind, sms, sm_max):
-    """ALU roofline of the contact pass: FP32 work = candidates x the early-out
-    test + searched pairs x (dichotomous search + update), per launch, over its
-    event-timed duration."""
+    """ALU roofline of the contact pass (contact_kernel, one launch per pass):
+    FP32 work = candidates x the early-out test + searched pairs x (dichotomous
+    search + update), per pass, over its event-timed duration."""
     d = per_class["contact"]
-    launches = stats["passes"]
-    cand = stats["candidates"] / launches
-    searched = stats["searched"] / launches
-    if CONTACT_FLOP_PER_CANDIDATE is None or CONTACT_FLOP_PER_SEARCHED is None:
-        return {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
-                "kernel": "contact_kernel", "note": "per-unit FP32 work not calibrated"}
+    passes = stats["passes"]
+    cand = stats["candidates"] / passes
+    searched = stats["searched"] / passes
+    us_pass = 1e3 * d["ms_per_frame"] / (sc.substeps * sc.iterations)
     flops = cand * CONTACT_FLOP_PER_CANDIDATE + searched * CONTACT_FLOP_PER_SEARCHED
-    ach = flops / (d["us_per_launch"] * 1e-6) / 1e12
+    ach = flops / (us_pass * 1e-6) / 1e12
     tr = profile_traffic("contact_kernel_hair.md", "per candidate pair")
     return {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
             "traffic": None if tr is None else tr * cand,
-            "traffic_unit": "DRAM bytes per launch (ncu bytes per candidate pair x candidates per launch)",
+            "traffic_unit": "DRAM bytes per pass (ncu bytes per candidate pair x candidates per pass)",
             "kernel": "contact_kernel",
             "peak_kind": f"FP32 SIMT {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz ({peak_kind} clock)",
-            "work": {"candidates_per_launch": cand, "searched_per_launch": searched,
-                     "active_per_launch": stats["active"] / launches,
+            "work": {"candidates_per_pass": cand, "searched_per_pass": searched,
+                     "active_per_pass": stats["active"] / passes,
                      "flop_per_candidate": CONTACT_FLOP_PER_CANDIDATE,
                      "flop_per_searched_pair": CONTACT_FLOP_PER_SEARCHED},
-            "us_per_launch": d["us_per_launch"]}
+            "us_per_pass": us_pass}
 
 
 def pairs_roofline(per_class, pairs_per_substep, sc, peaks, peak_kind):

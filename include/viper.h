@@ -162,11 +162,19 @@ int viper_scene_counts(const viper_scene *scene, int *n_rods, int *n_verts, int 
 int viper_set_solver(viper_scene *scene, int mode, int block_warps, int resident_max);
 
 /*
- * Time the batched solver over candidate CTA sizes and residency thresholds
- * on a scratch copy of the state (the scene state is restored afterwards) and
- * keep the fastest.  *chosen receives block_warps * 1000 + resident_max.
+ * Time the batched solver over candidate CTA sizes (1, 2, 4, 8 warps) and
+ * residency thresholds (64 .. 512 vertices) on a scratch copy of the state --
+ * per candidate two untimed frames, then five timed with CUDA events -- restore
+ * the state and keep the fastest.  *chosen receives block_warps * 1000 +
+ * resident_max.  Returns the first failing step's error (the solver is then
+ * the candidate being timed); a pair-buffer overflow does not stop the search.
  */
 int viper_autotune(viper_scene *scene, float dt, int substeps, int iterations, int *chosen);
+
+/* The batched solver's schedule: work items (CTAs of the shared-memory rod
+ * kernel), threads per CTA, and the vertices of the rods they hold (the rest
+ * go through the per-colour kernels).  VIPER_EINVAL for null pointers. */
+int viper_schedule(const viper_scene *scene, int *n_items, int *block_threads, int *resident_nv);
 
 /*
  * Advance one frame: `substeps` substeps of h = dt / substeps, each with

@@ -753,6 +753,7 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
             size_t table = (size_t)next_pow2(std::max<long long>(2LL * (long long)ns, 4096));
             b += 20 * cap + 16 * ns + 4 * (2 * ns) + 4 * (2 * table + 1) + 4 * 4096;  // pairs, their vertices, lambda
             b += 4 * (kBoundsWords + (size_t)broadphase_big_cap((int)ns));  // radius histogram, oversized pills
+            b += 16 * nv;  // world pack
             b += 16 * (ns + ns / 32 + 1);  // pair-search chunk records
         }
     }
@@ -1449,6 +1450,15 @@ int viper_profile_read(viper_scene *s, double *ms, int *launches)
     return VIPER_OK;
 }
 
+int viper_schedule(const viper_scene *s, int *n_items, int *block_threads, int *resident_nv)
+{
+    if (!s || !n_items || !block_threads || !resident_nv) return VIPER_EINVAL;
+    *n_items = s->n_items;
+    *block_threads = s->block_threads;
+    *resident_nv = s->resident_nv;
+    return VIPER_OK;
+}
+
 int viper_autotune(viper_scene *s, float dt, int substeps, int iterations, int *chosen)
 {
     if (!s || !(dt > 0) || substeps <= 0 || iterations < 0) return VIPER_EINVAL;
@@ -1470,13 +1480,22 @@ int viper_autotune(viper_scene *s, float dt, int substeps, int iterations, int *
             if ((rc = viper_set_solver(s, VIPER_SOLVER_BATCHED, warps[wi], res[ri]))) goto done;
             if ((rc = viper_set_state(s, (float *)x.data(), (float *)v.data(), (float *)q.data(), (float *)w.data())))
                 goto done;
-            if ((rc = viper_step(s, dt, substeps, iterations)) < 0 && rc != VIPER_EOVERFLOW) goto done;
-            cudaEventRecord(e0, s->stream);
-            for (int f = 0; f < 3; ++f) viper_step(s, dt, substeps, iterations);
-            cudaEventRecord(e1, s->stream);
-            cudaEventSynchronize(e1);
+            // two untimed frames (the first captures the frame graph), then five timed
+            for (int f = 0; f < 2; ++f)
+                if ((rc = viper_step(s, dt, substeps, iterations)) < 0 && rc != VIPER_EOVERFLOW) goto done;
+            if (cudaEventRecord(e0, s->stream) != cudaSuccess) {
+                rc = VIPER_ECUDA;
+                goto done;
+            }
+            for (int f = 0; f < 5; ++f)
+                if ((rc = viper_step(s, dt, substeps, iterations)) < 0 && rc != VIPER_EOVERFLOW) goto done;
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = VIPER_ECUDA;
+                goto done;
+            }
+            if ((rc = viper_sync(s)) < 0 && rc != VIPER_EOVERFLOW) goto done;
             if (ms < best) {
                 best = ms;
                 best_w = warps[wi];

@@ -28,6 +28,25 @@ __global__ void lbs_gather_kernel(int n, int ns, const float4 *__restrict__ rest
         lbs_vertices(base + threadIdx.x, blockDim.x, n, ns, rest, idx, w, frames, out, err);
 }
 
+// The same with the frame table staged in shared memory (tables of up to
+// kLbsSmemFrames frames): one CTA per SM copies the table once (coalesced
+// 128-bit loads from L2, where lbs_frames_kernel left it), then skins its
+// grid-stride share of the mesh, its four frame gathers per vertex served by
+// shared memory instead of L1.
+constexpr int kLbsSmemThreads = 1024;
+constexpr int kLbsSmemFrames = (227 * 1024) / (16 * kLbsFrame);  // 7,264 frames in 227 KB
+__global__ void __launch_bounds__(kLbsSmemThreads) lbs_gather_smem_kernel(
+    int n, int ns, const float4 *__restrict__ rest, const int4 *__restrict__ idx, const float4 *__restrict__ w,
+    const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
+{
+    extern __shared__ float4 sframes[];
+    for (int i = threadIdx.x; i < kLbsFrame * ns; i += blockDim.x) sframes[i] = __ldcg(frames + i);
+    __syncthreads();
+    const int span = blockDim.x * kLbsBatch;
+    for (int base = blockIdx.x * span; base < n; base += gridDim.x * span)
+        lbs_vertices<true>(base + threadIdx.x, blockDim.x, n, ns, rest, idx, w, sframes, out, err);
+}
+
 int device_sm_count()
 {
     static int n = 0;
@@ -43,11 +62,21 @@ int device_sm_count()
 void launch_lbs(viper_scene *s, int n, const float4 *rest, const int4 *idx, const float4 *w, float4 *out)
 {
     lbs_frames_kernel<<<(s->ns + 255) / 256, 256, 0, s->ls>>>(s->P, s->LQ, s->LC, s->d_sperm, s->frames);
-    int grid = (n + 256 * kLbsBatch - 1) / (256 * kLbsBatch);
-    if (grid > 8 * device_sm_count()) grid = 8 * device_sm_count();
-    if (grid < 1) grid = 1;
     ProfScope ps(s, PROF_LBS);
-    lbs_gather_kernel<<<grid, 256, 0, s->ls>>>(n, s->ns, rest, idx, w, s->frames, out, s->P.err);
+    // the shared-memory kernel's opt-in limit (raised once per device)
+    const bool smem_ok = raise_smem_limit(reinterpret_cast<const void *>(lbs_gather_smem_kernel),
+                                          kLbsSmemFrames * kLbsFrame * (int)sizeof(float4)) == 0;
+    const int per_cta = kLbsSmemThreads * kLbsBatch;
+    if (smem_ok && s->ns <= kLbsSmemFrames && n >= device_sm_count() * per_cta) {
+        // large meshes on a table that fits: one CTA per SM
+        lbs_gather_smem_kernel<<<device_sm_count(), kLbsSmemThreads, kLbsFrame * sizeof(float4) * (size_t)s->ns,
+                                 s->ls>>>(n, s->ns, rest, idx, w, s->frames, out, s->P.err);
+    } else {
+        int grid = (n + 256 * kLbsBatch - 1) / (256 * kLbsBatch);
+        if (grid > 8 * device_sm_count()) grid = 8 * device_sm_count();
+        if (grid < 1) grid = 1;
+        lbs_gather_kernel<<<grid, 256, 0, s->ls>>>(n, s->ns, rest, idx, w, s->frames, out, s->P.err);
+    }
     s->launches += 2;
 }
 

@@ -1751,6 +1751,14 @@ __device__ __forceinline__ void ld_frame(const float4 *f, float4 &r, float4 &ts)
 // frame is 32 bytes: the relative rotation r = R_j Rbar_j^T as a unit
 // quaternion and (t, s_m) with t = c_m - s_m r cbar_m, so T Tbar^-1 p = s_m r p + t.
 // Frame ids outside [0, ns) contribute nothing and raise the error word.
+// Frame k of a table in shared memory (two 128-bit shared loads).
+__device__ __forceinline__ void ld_frame_shared(const float4 *f, float4 &r, float4 &ts)
+{
+    r = f[0];
+    ts = f[1];
+}
+
+template <bool SHARED>
 __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns, const float4 *__restrict__ frames,
                                            int *err)
 {
@@ -1765,7 +1773,10 @@ __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns
         }
         const float4 *f = frames + kLbsFrame * (size_t)ids[k];
         float4 r, ts;
-        ld_frame(f, r, ts);
+        if (SHARED)
+            ld_frame_shared(f, r, ts);
+        else
+            ld_frame(f, r, ts);
         const V3 y = qrot(r, v3(p.x, p.y, p.z));
         ox += wv[k] * (ts.w * y.x + ts.x);
         oy += wv[k] * (ts.w * y.y + ts.y);
@@ -1779,6 +1790,7 @@ __device__ __forceinline__ float4 lbs_blend(float4 p, int4 id, float4 ww, int ns
 // read once per frame and bypasses L1), then each blends its frames (L2
 // resident) and is written with a streaming 128-bit store.
 constexpr int kLbsBatch = 2;
+template <bool SHARED = false>
 __device__ __forceinline__ void lbs_vertices(int i0, int stride, int n, int ns, const float4 *__restrict__ rest,
                                              const int4 *__restrict__ idx, const float4 *__restrict__ w,
                                              const float4 *__restrict__ frames, float4 *__restrict__ out, int *err)
@@ -1797,7 +1809,7 @@ __device__ __forceinline__ void lbs_vertices(int i0, int stride, int n, int ns, 
 #pragma unroll
     for (int k = 0; k < kLbsBatch; ++k) {
         const int i = i0 + k * stride;
-        if (i < n) __stcs(out + i, lbs_blend(p[k], id[k], ww[k], ns, frames, err));
+        if (i < n) __stcs(out + i, lbs_blend<SHARED>(p[k], id[k], ww[k], ns, frames, err));
     }
 }
 

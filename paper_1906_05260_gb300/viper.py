@@ -131,6 +131,7 @@ def lib():
         L.viper_launch_count.argtypes = [vp]
         L.viper_launch_count.restype = C.c_longlong
         L.viper_contact_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.viper_schedule.argtypes = [vp, _ip, _ip, _ip]
         L.viper_error_string.argtypes = [C.c_int]
         L.viper_error_string.restype = C.c_char_p
         _lib = L
@@ -324,6 +325,46 @@ class Scene:
                                     int(iterations if iterations is not None else sc.iterations),
                                     C.byref(out)), "viper_autotune")
         return divmod(out.value, 1000)
+
+    def autotune_cached(self, path, dt=None, substeps=None, iterations=None):
+        """autotune(), its choice kept in the JSON file `path` under a key of the
+        GPU's name and a hash of the rod lengths, step parameters and contact
+        flag; a cached choice is applied without timing.  Returns
+        ((block_warps, resident_max), cached)."""
+        import hashlib
+        import json
+        import torch
+        sc = self.scene
+        params = (float(dt or sc.dt), int(substeps or sc.substeps),
+                  int(iterations if iterations is not None else sc.iterations), bool(sc.contacts))
+        digest = hashlib.sha256(np.ascontiguousarray(np.diff(sc.rod_offsets), np.int64).tobytes() +
+                                repr(params).encode()).hexdigest()[:16]
+        key = f"{torch.cuda.get_device_name()}:{digest}"
+        cache = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        if key in cache:
+            bw, rm = cache[key]
+            self.set_solver(SOLVER_BATCHED, bw, rm)
+            return (bw, rm), True
+        bw, rm = self.autotune(dt, substeps, iterations)
+        cache[key] = [bw, rm]
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f)
+        os.replace(tmp, path)
+        return (bw, rm), False
+
+    def schedule(self):
+        """(work items, threads per CTA, resident vertices) of the batched solver."""
+        n, t, r = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().viper_schedule(self._h, C.byref(n), C.byref(t), C.byref(r)), "viper_schedule")
+        return n.value, t.value, r.value
 
     # -- stepping
     def step(self, dt=None, substeps=None, iterations=None, check=True):
