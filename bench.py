@@ -682,6 +682,48 @@ def per_class_times(V, torch, g, stream, flush, frames, step):
     return out
 
 
+def per_class_replay(V, torch, sc, cap, flush, W, K, classes=HAIR_CLASSES):
+    """Kernel-class device times over the timed frames: a fresh scene replays
+    the trajectory (W untimed frames, then frames W .. W+K-1), frame i timing
+    class classes[i % n] (events around that class's launches in the frame
+    graph).  The contact counters are read after every frame and kept for the
+    frames that timed the contact pass, so that the contact pass's work and
+    its time come from the same frames."""
+    ids = {"rod": V.PROF_ROD, "contact": V.PROF_CONTACT, "broadphase": V.PROF_BROADPHASE,
+           "pairs": V.PROF_PAIRS, "elementwise": V.PROF_ELEMENTWISE}
+    g = V.Scene(sc, max_pairs=cap)
+    for _ in range(W):
+        g.step()
+    g.contact_stats()
+    tot = {c: 0.0 for c in classes}
+    nl = {c: 0 for c in classes}
+    nf = {c: 0 for c in classes}
+    cstats = [0, 0, 0]
+    for i in range(K):
+        c = classes[i % len(classes)]
+        g.profile(ids[c])
+        with torch.cuda.stream(g.stream):
+            flush.fill_(i & 0xFF)
+        g.step()
+        ms, n = g.profile_read()
+        st = g.contact_stats()
+        tot[c] += ms
+        nl[c] += n
+        nf[c] += 1
+        if c == "contact":
+            cstats = [a + b for a, b in zip(cstats, st)]
+    g.profile(V.PROF_NONE)
+    rc = g.sync()
+    g.close()
+    if rc != 0:
+        raise SystemExit(f"per-class replay failed: {rc}")
+    out = {c: {"ms_per_frame": tot[c] / nf[c], "launches_per_frame": nl[c] / nf[c],
+               "us_per_launch": 1e3 * tot[c] / max(nl[c], 1), "frames": nf[c]} for c in classes if nf[c]}
+    stats = {"candidates": cstats[0], "searched": cstats[1], "active": cstats[2],
+             "passes": nf.get("contact", 0) * sc.substeps * sc.iterations}
+    return out, stats
+
+
 def contact_roofline(per_class, stats, sc, peak_tflops, peak_kind, sms, sm_max):
     """ALU roofline of the contact pass (contact_kernel, one launch per pass):
     FP32 work = candidates x the early-out test + searched pairs x (dichotomous
@@ -900,16 +942,9 @@ def main():
     p99 = float(np.percentile(ts, 99))
     pairs_last = int(g.pairs().shape[0])
 
-    # ---- kernel classes and contact counters over the frames that follow
-    prof_frames = min(K, 10)
-    per_class = per_class_times(V, torch, g, stream, flush, prof_frames, g.step)
-    g.contact_stats()
-    for _ in range(prof_frames):
-        g.step()
-    cand, searched, active = g.contact_stats()
-    stats = {"candidates": cand, "searched": searched, "active": active,
-             "passes": prof_frames * sc.substeps * sc.iterations}
     g.close()
+    # ---- kernel classes and contact counters over the same frames, replayed
+    per_class, stats = per_class_replay(V, torch, sc, cap, flush, W, K)
     dominant = max(per_class, key=lambda k: per_class[k]["ms_per_frame"])
     if dominant == "pairs":
         roof = pairs_roofline(per_class, pairs_last, sc, peaks, peak_kind)

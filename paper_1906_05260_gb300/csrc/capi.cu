@@ -747,7 +747,7 @@ size_t viper_scene_footprint(const viper_scene_desc *d)
     bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;
     if (d->n_bundles > 0) b += (size_t)d->bundle_offsets[d->n_bundles] * 48 * 64;  // cross-sections (bound)
     if (cp) {
-        b += 36 * nv + 4 * nv * (size_t)(d->n_planes > 0 ? d->n_planes : 0);
+        b += 20 * nv + 4 * nv * (size_t)(d->n_planes > 0 ? d->n_planes : 0);
         if (d->flags & VIPER_FLAG_CONTACTS) {
             size_t cap = (size_t)pair_capacity(d, (int)ns);
             size_t table = (size_t)next_pow2(std::max<long long>(2LL * (long long)ns, 4096));
@@ -881,6 +881,13 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     if (P.vvec) s->mode = VIPER_SOLVER_PLAIN;  // the vector volume form runs on the plain path only
     P.contact_threads = (d->flags & VIPER_FLAG_CONTACT_THREADS) ? 1 : 0;
     P.contact_alpha = (float)d->contact_compliance;
+    {
+        double rmax = 0.0;  // fixed-point units of the contact sums from the largest rest radius
+        for (double r : s->h_rbar0) rmax = std::max(rmax, r);
+        if (!(rmax > 0.0) || !std::isfinite(rmax)) rmax = 1.0;
+        P.fix_scale = (float)(kFixUnitsPerRadius / rmax);
+        P.fix_inv = (float)(rmax / kFixUnitsPerRadius);
+    }
     P.bp_rbar_stride = 4;
     const bool cp = (d->flags & VIPER_FLAG_CONTACTS) || d->n_planes > 0 || d->n_bundles > 0;
     const bool pills = (d->flags & VIPER_FLAG_CONTACTS) != 0;
@@ -906,7 +913,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     AC(P.bq0, float4, std::max(d->n_bones, 1)); AC(P.bq1, float4, std::max(d->n_bones, 1));
     AC(P.bt0, float, 3 * std::max(d->n_bones, 1)); AC(P.bt1, float, 3 * std::max(d->n_bones, 1));
     AC(P.planes, float4, std::max(d->n_planes, 1));
-    A(P.acc, 4 * (size_t)(cp ? nv : 1)); A(P.cnt, cp ? nv : 1);
+    A(P.acc, 2 * (size_t)(cp ? nv : 1)); A(P.cnt, cp ? nv : 1);
     A(P.lam_plane, (size_t)(cp ? nv : 1) * std::max(d->n_planes, 1));
     P.max_pairs = pills ? pair_capacity(d, ns) : 0;
     P.table = pills ? next_pow2(std::max<long long>(2LL * ns, 4096)) : 1;
@@ -930,7 +937,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     cudaMemsetAsync(P.err, 0, sizeof(int), s->stream);
     cudaMemsetAsync(P.npairs, 0, sizeof(int), s->stream);
     cudaMemsetAsync(P.contact_stats, 0, sizeof(unsigned long long) * (pills ? 3 : 1), s->stream);
-    cudaMemsetAsync(P.acc, 0, sizeof(unsigned long long) * 4 * (size_t)(cp ? nv : 1), s->stream);
+    cudaMemsetAsync(P.acc, 0, sizeof(unsigned long long) * 2 * (size_t)(cp ? nv : 1), s->stream);
     cudaMemsetAsync(P.cnt, 0, sizeof(int) * (size_t)(cp ? nv : 1), s->stream);
     cudaMemsetAsync(P.cell_count, 0, sizeof(int) * (size_t)P.table, s->stream);
     cudaMemsetAsync(P.V, 0, sizeof(float4) * nv, s->stream);

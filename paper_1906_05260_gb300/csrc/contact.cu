@@ -21,9 +21,9 @@
 // Contact handling (Sec. 7, Sec. 7.2): each candidate pair runs the
 // dichotomous narrowphase and, if the pills interpenetrate, one XPBD update of
 // the contact constraint; half-planes act on vertex spheres.  Corrections are
-// summed per vertex in 64-bit fixed point (order independent, hence
-// deterministic) and averaged by the number of active constraints (Jacobi
-// with averaging).
+// summed per vertex as packed fixed-point integers (two fields per 64-bit
+// atomic; order independent, hence deterministic) and averaged by the number
+// of active constraints (Jacobi with averaging).
 #include "phases.cuh"
 
 namespace viper {

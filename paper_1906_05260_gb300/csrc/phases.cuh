@@ -155,13 +155,18 @@ __device__ __forceinline__ float4 apply_pending(const Params &P, int v, float4 x
 {
     int c = P.cnt[v];
     if (c) {
-        float inv = 1.f / (float)c;
-        unsigned long long *a = P.acc + 4 * (size_t)v;
-        x.x += from_fix(a[0]) * inv;
-        x.y += from_fix(a[1]) * inv;
-        x.z += from_fix(a[2]) * inv;
-        x.w += from_fix(a[3]) * inv;
-        a[0] = a[1] = a[2] = a[3] = 0ull;
+        if (c > kFixMaxCount) atomicOr(P.err, ERR_OVERFLOW);  // the field sums may have wrapped
+        const float inv = 1.f / (float)c;
+        unsigned long long *a = P.acc + 2 * (size_t)v;
+        float dx, dy, dz, dr;
+        fix_unpack(a[0], P.fix_inv, dx, dy);
+        fix_unpack(a[1], P.fix_inv, dz, dr);
+        x.x += dx * inv;
+        x.y += dy * inv;
+        x.z += dz * inv;
+        const float rb = P.RV0[v].w;  // the radius change back to a scale change
+        if (rb > 0.f) x.w += (dr / rb) * inv;
+        a[0] = a[1] = 0ull;
         P.cnt[v] = 0;
     }
     return x;
@@ -1369,13 +1374,12 @@ __device__ __forceinline__ void emit_chunk_all(const Params &P, const Grid &G, i
 }
 
 // ================================================================ contacts
-__device__ __forceinline__ void acc_add(const Params &P, int v, V3 d, float ds)
+// Correction of vertex v: position d, radius dr (= scale change x rest radius).
+__device__ __forceinline__ void acc_add(const Params &P, int v, V3 d, float dr)
 {
-    unsigned long long *a = P.acc + 4 * (size_t)v;
-    atomicAdd(a + 0, to_fix(d.x));
-    atomicAdd(a + 1, to_fix(d.y));
-    atomicAdd(a + 2, to_fix(d.z));
-    atomicAdd(a + 3, to_fix(ds));
+    unsigned long long *a = P.acc + 2 * (size_t)v;
+    atomicAdd(a + 0, fix_pack(d.x, d.y, P.fix_scale));
+    atomicAdd(a + 1, fix_pack(d.z, dr, P.fix_scale));
     atomicAdd(P.cnt + v, 1);
 }
 
@@ -1429,8 +1433,28 @@ __device__ __forceinline__ void contact_load(const Params &P, int i, ContactPair
 // of the four are accumulated by this thread, and the multiplier is stored if
 // write_lam.  With `warp` all 32 lanes handle the same pair (the early return
 // is uniform) and the multiplier is written only after every lane has read it.
+// What the update of pair i reads besides the pair's geometry: the four
+// vertices' rest radii, inverse masses and scale weights, and its multiplier.
+struct ApplyData {
+    float rbar[4], wx[4], wsv[4], lam;
+};
+
+__device__ __forceinline__ void apply_data(const Params &P, int i, const ContactPair &c, ApplyData &D)
+{
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        D.rbar[t] = P.XW ? P.RV0[c.vs[t]].w : c.rbar[t];
+        const float4 m = P.RV1[c.vs[t]];
+        D.wx[t] = inv_mass(m);
+        D.wsv[t] = m.y;
+    }
+    D.lam = P.lam_pair[i];
+}
+
+// pre: the pair's ApplyData loaded ahead (before the search, so that its
+// latency overlaps the search's arithmetic), or null to load it here.
 __device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
-                                              int tstep, bool write_lam, bool warp)
+                                              int tstep, bool write_lam, bool warp, const ApplyData *pre = nullptr)
 {
     float be;
     const float C = coll_f(c.Q, al, be);
@@ -1438,24 +1462,23 @@ __device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, 
     float dist = sqrtf(dot(d, d));
     if (!(C < 0.f) || dist < 1e-12f) return false;
     V3 n = (1.f / dist) * d;
-    float rbar[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) rbar[t] = P.XW ? P.RV0[c.vs[t]].w : c.rbar[t];
-    const float4 m1 = P.RV1[c.vs[0]], m2 = P.RV1[c.vs[1]], m3 = P.RV1[c.vs[2]], m4 = P.RV1[c.vs[3]];
+    ApplyData D;
+    if (pre)
+        D = *pre;
+    else
+        apply_data(P, i, c, D);
     const float wt[4] = {1.f - al, al, -(1.f - be), -be};
-    const float wx[4] = {inv_mass(m1), inv_mass(m2), inv_mass(m3), inv_mass(m4)};
-    const float wsv[4] = {m1.y, m2.y, m3.y, m4.y};
     float den = at;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) den += wx[t] * wt[t] * wt[t] + wsv[t] * wt[t] * wt[t] * rbar[t] * rbar[t];
-    const float lam = P.lam_pair[i];
-    const float dl = (-C - at * lam) / den;
+    for (int t = 0; t < 4; ++t)
+        den += D.wx[t] * wt[t] * wt[t] + D.wsv[t] * wt[t] * wt[t] * D.rbar[t] * D.rbar[t];
+    const float dl = (-C - at * D.lam) / den;
     if (warp) __syncwarp();
-    if (write_lam) P.lam_pair[i] = lam + dl;
+    if (write_lam) P.lam_pair[i] = D.lam + dl;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
         if (t >= t0 && (t - t0) % tstep == 0)
-            acc_add(P, c.vs[t], (wx[t] * wt[t] * dl) * n, -wsv[t] * fabsf(wt[t]) * rbar[t] * dl);
+            acc_add(P, c.vs[t], (D.wx[t] * wt[t] * dl) * n, -D.wsv[t] * fabsf(wt[t]) * D.rbar[t] * dl * D.rbar[t]);
     return true;
 }
 
@@ -1556,8 +1579,10 @@ __device__ __forceinline__ int2 contact_pairs_compacted(const Params &P, int np,
             const int j = q[lane];
             ContactPair c;
             contact_load(P, j, c);
+            ApplyData D;
+            apply_data(P, j, c, D);
             pill_pair_axis(c.Q);
-            const bool act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+            const bool act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false, &D);
             counts.x += 32;
             counts.y += __popc(__ballot_sync(full, act));
             __syncwarp();
@@ -1571,8 +1596,10 @@ __device__ __forceinline__ int2 contact_pairs_compacted(const Params &P, int np,
         const int j = q[lane];
         ContactPair c;
         contact_load(P, j, c);
+        ApplyData D;
+        apply_data(P, j, c, D);
         pill_pair_axis(c.Q);
-        act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
+        act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false, &D);
     }
     counts.x += qn;
     counts.y += __popc(__ballot_sync(full, act));
@@ -1595,7 +1622,7 @@ __device__ __forceinline__ void contact_planes(const Params &P, int v, float at)
         const float den = w + m.y * rbar * rbar + at;
         const float dl = (-C - at * *lp) / den;
         *lp += dl;
-        acc_add(P, v, (w * dl) * v3(pl.x, pl.y, pl.z), -m.y * rbar * dl);
+        acc_add(P, v, (w * dl) * v3(pl.x, pl.y, pl.z), -m.y * rbar * dl * rbar);
     }
 }
 

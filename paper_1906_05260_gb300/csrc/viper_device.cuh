@@ -571,6 +571,57 @@ __device__ __forceinline__ float coll_f(const PillPair &P, float al, float &be)
     return sqrt_approx(dot(d, d)) - ra - lerpf(P.rb1, P.rb2, be);
 }
 
+// The probe of the search in scalar form.  Along pill a, pa(x) = a1 + x da, so
+// with r0 = a1 - b1 and e = b2 - b1 = l u every quantity the probe needs is a
+// polynomial in x with per-pair coefficients: a = (pa - b1).u = A0 + x A1,
+// |pa - b1|^2 = R0 + x (R1 + x R2), (pa - b1).e = E0 + x E1, and the squared
+// distance to pb(t) = b1 + t e is |pa - b1|^2 - t (2 (pa - b1).e - t |e|^2).
+// The coefficients come from coordinate differences, so a probe costs about
+// fifteen operations and two square roots instead of the vector form's
+// fifty, and never forms a point in world coordinates (whose FP32 rounding is
+// the larger error of the vector form).  Same function as coll_f.
+struct PillSearch {
+    float A0, A1, R0, R1, R2, E0, E1, L2;
+    float ra1, dra, rb1, drb;
+    float tn, inv_l, fixed;
+};
+
+__device__ __forceinline__ PillSearch pill_search(const PillPair &P)
+{
+    PillSearch S;
+    const V3 r0 = P.a1 - P.b1, da = P.a2 - P.a1, e = P.b2 - P.b1;
+    S.A0 = dot(r0, P.axb.u);
+    S.A1 = dot(da, P.axb.u);
+    S.R0 = dot(r0, r0);
+    S.R1 = 2.f * dot(r0, da);
+    S.R2 = dot(da, da);
+    S.E0 = dot(r0, e);
+    S.E1 = dot(da, e);
+    S.L2 = dot(e, e);
+    S.ra1 = P.ra1;
+    S.dra = P.ra2 - P.ra1;
+    S.rb1 = P.rb1;
+    S.drb = P.rb2 - P.rb1;
+    S.tn = P.axb.tn;
+    S.inv_l = P.axb.inv_l;
+    S.fixed = P.axb.fixed;
+    return S;
+}
+
+__device__ __forceinline__ float search_f(const PillSearch &S, float x)
+{
+    const float a = fmaf(x, S.A1, S.A0);
+    const float rel2 = fmaf(x, fmaf(x, S.R2, S.R1), S.R0);
+    float t = S.fixed;
+    if (!(t >= 0.f)) {
+        const float hh = sqrt_approx(fmaxf(fmaf(-a, a, rel2), 0.f));
+        t = fminf(fmaxf(fmaf(-hh, S.tn, a) * S.inv_l, 0.f), 1.f);
+    }
+    const float re = fmaf(x, S.E1, S.E0);
+    const float d2 = fmaxf(fmaf(-t, fmaf(-t, S.L2, 2.f * re), rel2), 0.f);
+    return sqrt_approx(d2) - fmaf(x, S.dra, S.ra1) - fmaf(t, S.drb, S.rb1);
+}
+
 // Dichotomous search, 10 iterations (Sec. 7.2): probes mid -+ eps/2 with
 // eps = 1e-3 of the current bracket; keep the side of the smaller probe.
 constexpr int kDichoSteps = 10;
@@ -591,12 +642,13 @@ __device__ __forceinline__ void dicho_keep(float &lo, float &hi, float x1, float
 
 __device__ __forceinline__ float dichotomous(const PillPair &P)
 {
-    float lo = 0.f, hi = 1.f, be;
+    const PillSearch S = pill_search(P);
+    float lo = 0.f, hi = 1.f;
 #pragma unroll 1
     for (int it = 0; it < kDichoSteps; ++it) {
         float x1, x2;
         dicho_probes(lo, hi, x1, x2);
-        dicho_keep(lo, hi, x1, x2, coll_f(P, x1, be) < coll_f(P, x2, be));
+        dicho_keep(lo, hi, x1, x2, search_f(S, x1) < search_f(S, x2));
     }
     return 0.5f * (lo + hi);
 }
@@ -613,6 +665,7 @@ __device__ __forceinline__ float dichotomous_warp(const PillPair &P, int lane)
     const int j = 31 - __clz((lane >> 1) + 1);  // depth of this lane's node (4 for lanes 30, 31)
     const int b = (lane - 2 * ((1 << j) - 1)) >> 1;
     const int side = lane & 1;
+    const PillSearch S = pill_search(P);
     float lo = 0.f, hi = 1.f;
 #pragma unroll
     for (int k0 = 0; k0 < kDichoSteps; k0 += 4) {
@@ -627,8 +680,7 @@ __device__ __forceinline__ float dichotomous_warp(const PillPair &P, int lane)
                     dicho_keep(l, h, x1, x2, (b >> t) & 1);
                 }
             dicho_probes(l, h, x1, x2);
-            float be;
-            f = coll_f(P, side ? x2 : x1, be);
+            f = search_f(S, side ? x2 : x1);
         }
         int node = 0;
 #pragma unroll
@@ -673,15 +725,32 @@ __device__ __forceinline__ bool spheres_overlap(float4 a, float4 b)
 }
 
 // ---------------------------------------------------------------- fixed point
-// Contact corrections are summed as 64-bit fixed point (2^-40 units) so that the
-// per-vertex sums do not depend on the order of the atomic additions.
-constexpr float kFixScale = 1099511627776.0f;  // 2^40
-constexpr float kFixInv = 1.0f / 1099511627776.0f;
-__device__ __forceinline__ unsigned long long to_fix(float v)
+// Contact corrections are summed per vertex as integers, so that the sums do
+// not depend on the order of the atomic additions.  Two signed 32-bit
+// fixed-point fields share one 64-bit word (x with y; z with the radius change
+// s rbar), added as the integer hi 2^32 + lo: the sum of such words is
+// (sum hi) 2^32 + (sum lo), from which both field sums are read back exactly
+// while each stays inside 32 bits.  Units are 1 / fix_scale, fix_scale =
+// 2^19 / (the scene's largest rest radius); a contribution is clamped to
+// +-2^23 units (16 largest radii, far beyond any penetration), so up to
+// kFixMaxCount contributions per vertex cannot leave a field.
+constexpr float kFixField = 8388608.0f;  // 2^23
+constexpr int kFixMaxCount = 255;
+constexpr float kFixUnitsPerRadius = 524288.0f;  // 2^19
+__device__ __forceinline__ long long fix_field(float v, float scale)
 {
-    float c = fminf(fmaxf(v * kFixScale, -9.0e18f), 9.0e18f);
-    return (unsigned long long)__float2ll_rn(c);
+    return (long long)__float2int_rn(fminf(fmaxf(v * scale, -kFixField), kFixField));
 }
-__device__ __forceinline__ float from_fix(unsigned long long v) { return __ll2float_rn((long long)v) * kFixInv; }
+__device__ __forceinline__ unsigned long long fix_pack(float lo, float hi, float scale)
+{
+    return (unsigned long long)(fix_field(hi, scale) * 4294967296LL + fix_field(lo, scale));
+}
+__device__ __forceinline__ void fix_unpack(unsigned long long w, float inv, float &lo, float &hi)
+{
+    const int l = (int)(unsigned int)(w & 0xffffffffull);
+    const long long h = ((long long)w - (long long)l) >> 32;
+    lo = (float)l * inv;
+    hi = (float)(int)h * inv;
+}
 
 }  // namespace viper

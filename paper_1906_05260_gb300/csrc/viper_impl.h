@@ -95,8 +95,9 @@ struct Params {
     int2 *pair_v;  // per pair: the first vertices of its two segments, written with it (NULL: looked up)
     int *npairs;
     float *lam_pair, *lam_plane;
-    unsigned long long *acc;
+    unsigned long long *acc;  // per vertex two words of packed fixed-point corrections (fix_pack)
     int *cnt;
+    float fix_scale, fix_inv;  // fixed-point units per length unit and back
     // world position and radius per vertex (x + rod origin, s rbar), written by the
     // shared-memory sweep before each contact pass and read by it; null: not used
     float4 *XW;
