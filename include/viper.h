@@ -50,6 +50,8 @@ extern "C" {
 #define VIPER_ETIMEOUT -6    /* a bounded device wait expired                     */
 #define VIPER_EBUDGET -7     /* admission refused: memory budget exceeded         */
 #define VIPER_ENOCONV -8     /* a bundle's rotation extraction did not converge   */
+#define VIPER_ECONTACTS -9   /* over 2047 contact corrections on one vertex in one */
+                             /* contact pass (its fixed-point sums could wrap)    */
 
 #define VIPER_FLAG_CONTACTS 1 /* pill-pill contacts (Sec. 7.1, 7.2)                */
 #define VIPER_FLAG_VOLUME 2   /* volume constraints (Sec. 5 "Volume potential")    */

@@ -586,6 +586,7 @@ int decode_err(int e)
     if (e & ERR_OVERFLOW) return VIPER_EOVERFLOW;
     if (e & ERR_TIMEOUT) return VIPER_ETIMEOUT;
     if (e & ERR_NOCONV) return VIPER_ENOCONV;
+    if (e & ERR_CONTACTS) return VIPER_ECONTACTS;
     return VIPER_OK;
 }
 
@@ -668,6 +669,7 @@ const char *viper_error_string(int code)
     case VIPER_ETIMEOUT: return "bounded device wait expired";
     case VIPER_EBUDGET: return "memory budget exceeded";
     case VIPER_ENOCONV: return "rotation extraction of a bundle did not converge";
+    case VIPER_ECONTACTS: return "over 2047 contact corrections on one vertex in one pass";
     default: return "unknown error";
     }
 }

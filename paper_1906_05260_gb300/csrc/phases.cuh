@@ -155,7 +155,7 @@ __device__ __forceinline__ float4 apply_pending(const Params &P, int v, float4 x
 {
     int c = P.cnt[v];
     if (c) {
-        if (c > kFixMaxCount) atomicOr(P.err, ERR_OVERFLOW);  // the field sums may have wrapped
+        if (c > kFixMaxCount) atomicOr(P.err, ERR_CONTACTS);  // the field sums may have wrapped
         const float inv = 1.f / (float)c;
         unsigned long long *a = P.acc + 2 * (size_t)v;
         float dx, dy, dz, dr;

@@ -731,12 +731,13 @@ __device__ __forceinline__ bool spheres_overlap(float4 a, float4 b)
 // s rbar), added as the integer hi 2^32 + lo: the sum of such words is
 // (sum hi) 2^32 + (sum lo), from which both field sums are read back exactly
 // while each stays inside 32 bits.  Units are 1 / fix_scale, fix_scale =
-// 2^19 / (the scene's largest rest radius); a contribution is clamped to
-// +-2^23 units (16 largest radii, far beyond any penetration), so up to
-// kFixMaxCount contributions per vertex cannot leave a field.
-constexpr float kFixField = 8388608.0f;  // 2^23
-constexpr int kFixMaxCount = 255;
-constexpr float kFixUnitsPerRadius = 524288.0f;  // 2^19
+// 2^16 / (the scene's largest rest radius); a contribution is clamped to
+// +-2^20 units (16 largest radii, beyond any penetration), so up to
+// kFixMaxCount contributions per vertex cannot leave a field (more raise
+// ERR_CONTACTS).
+constexpr float kFixField = 1048576.0f;  // 2^20
+constexpr int kFixMaxCount = 2047;
+constexpr float kFixUnitsPerRadius = 65536.0f;  // 2^16
 __device__ __forceinline__ long long fix_field(float v, float scale)
 {
     return (long long)__float2int_rn(fminf(fmaxf(v * scale, -kFixField), kFixField));

@@ -9,7 +9,7 @@
 
 namespace viper {
 
-enum : int { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_NOCONV = 8 };
+enum : int { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_NOCONV = 8, ERR_CONTACTS = 16 };
 
 // Work item of the shared-memory rod kernel: a packed group of whole rods.
 //   x = first internal vertex, y = vertex count, z = first internal segment, w = segment count

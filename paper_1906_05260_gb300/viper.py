@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libviper.so")
 
 OK = 0
-EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET, ENOCONV = -1, -2, -3, -4, -5, -6, -7, -8
+EINVAL, ENOMEM, ECUDA, ENONFINITE, EOVERFLOW, ETIMEOUT, EBUDGET, ENOCONV, ECONTACTS = -1, -2, -3, -4, -5, -6, -7, -8, -9
 FLAG_CONTACTS, FLAG_VOLUME, FLAG_SURFACE_BENDING, FLAG_JACOBI, FLAG_WARM_START = 1, 2, 4, 8, 16
 FLAG_VOLUME_VECTOR = 32
 FLAG_CONTACT_THREADS = 64  # contact pass with one thread per pair always (timing only)
