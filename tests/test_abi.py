@@ -39,6 +39,16 @@ def test_library_builds_and_exports_every_declared_symbol():
     lib.viper_error_string.restype = ctypes.c_char_p
     assert lib.viper_error_string(0) == b"ok"
     assert lib.viper_error_string(-4) == b"state became non-finite"
+    # every code the header defines has its own message
+    codes = {}
+    for line in open(os.path.join(ROOT, "include", "viper.h")):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == "#define" and parts[1].startswith("VIPER_E"):
+            codes[parts[1]] = int(parts[2])
+    msgs = {name: lib.viper_error_string(code) for name, code in codes.items()}
+    assert all(m != b"unknown error" for m in msgs.values()), msgs
+    assert len(set(msgs.values())) == len(msgs)
+    assert codes["VIPER_ECONTACTS"] == -9
 
 
 def test_oracle_and_library_share_no_code():
