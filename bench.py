@@ -46,11 +46,11 @@ MUSCLE_DESC = ("muscle_rig: 200 tapered rods of 8-64 vertices pinned to 20 anima
 HAIR_PAIRS_PER_PILL = 64  # pair-list capacity of the hair scene (peak use about 36 per pill)
 
 # FP32 work per unit of the contact pass (ncu SASS counts of FADD + FMUL + 2 FFMA of one
-# pass at frames 5 and 55 of the hair scene, solved for the two figures; frame 18 is
-# predicted within 0.2 %): the two-direction early-out test per candidate pair, and the
-# dichotomous search + constraint update per searched pair
-CONTACT_FLOP_PER_CANDIDATE = 78.5
-CONTACT_FLOP_PER_SEARCHED = 1503.0
+# pass at frames 5, 18 and 55 of the hair scene, least-squares fit of the two figures,
+# each state predicted within 2.5 %): the two-direction early-out test per candidate
+# pair, and the dichotomous search + constraint update per searched pair
+CONTACT_FLOP_PER_CANDIDATE = 76.4
+CONTACT_FLOP_PER_SEARCHED = 1199.6
 # FP32 work of the shared-memory rod kernel per vertex per colour sweep (ncu SASS
 # counts on the batching workload: 2.133 GFLOP per launch over 250,612 vertices x 8
 # sweeps, prediction and velocity update included)
