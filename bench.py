@@ -49,8 +49,8 @@ HAIR_PAIRS_PER_PILL = 64  # pair-list capacity of the hair scene (peak use about
 # pass at frames 5, 18 and 55 of the hair scene, least-squares fit of the two figures,
 # each state predicted within 2.5 %): the two-direction early-out test per candidate
 # pair, and the dichotomous search + constraint update per searched pair
-CONTACT_FLOP_PER_CANDIDATE = 76.4
-CONTACT_FLOP_PER_SEARCHED = 1199.6
+CONTACT_FLOP_PER_CANDIDATE = 78.1
+CONTACT_FLOP_PER_SEARCHED = 894.6
 # FP32 work of the shared-memory rod kernel per vertex per colour sweep (ncu SASS
 # counts on the batching workload: 2.133 GFLOP per launch over 250,612 vertices x 8
 # sweeps, prediction and velocity update included)
@@ -266,6 +266,29 @@ def cpu_baseline(scene):
                         "kind": "oracle",
                         "sample": f"the same substep with OpenMP over the constraints of each colour and the "
                                   f"pairs of each contact pass, {tn:.2f} s on {cores} threads"}}
+
+
+def run_at_frame(frames):
+    """The hair scene after `frames` frames, then one substep with one iteration:
+    a single pair search and a single contact pass at that state (for ncu:
+    contact_kernel launch 40 x frames, bp_emit_kernel launch 10 x frames).
+    Prints the pass's candidate, searched and active pair counts."""
+    import torch
+    from paper_1906_05260_gb300 import build as B
+    B.build()
+    from paper_1906_05260_gb300 import viper as V
+    torch.cuda.set_device(0)
+    sc = hair_scene(0)
+    g = V.Scene(sc, max_pairs=HAIR_PAIRS_PER_PILL * sc.ns)
+    for _ in range(frames):
+        g.step()
+    g.contact_stats()
+    g.step(dt=sc.dt / sc.substeps, substeps=1, iterations=1)
+    cand, searched, active = g.contact_stats()
+    rc = g.sync()
+    g.close()
+    print(json.dumps({"at_frame": frames, "candidates": cand, "searched": searched, "active": active, "rc": rc}))
+    return 0 if rc == 0 else 1
 
 
 def run_reference(args):
@@ -888,6 +911,10 @@ def main():
     ap.add_argument("--no-lbs", action="store_true")
     ap.add_argument("--serving", type=float, default=60.0,
                     help="seconds of the real-time serving load (0 disables)")
+    ap.add_argument("--at-frame", type=int, default=-1,
+                    help="profiling aid: step the hair scene this many frames, then run one substep of "
+                         "one iteration (its contact pass is contact_kernel launch 40 x F) and print "
+                         "that pass's contact counters; no timing")
     ap.add_argument("--serving-serial", type=float, default=10.0,
                     help="seconds of the same load served one scene per step")
     args = ap.parse_args()
@@ -895,6 +922,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.at_frame >= 0:
+        return run_at_frame(args.at_frame)
 
     import ctypes as C
     import torch

@@ -248,7 +248,7 @@ void launch_broadphase(viper_scene *s) { broadphase_enqueue(s->P, s->ls, s->d_sc
 
 // ---------------------------------------------------------------- contact pass
 constexpr int kContactThreads = 256;
-__global__ void __launch_bounds__(kContactThreads, 3) contact_kernel(Params P)
+__global__ void __launch_bounds__(kContactThreads, 4) contact_kernel(Params P)
 {
     __shared__ int queue[kContactThreads / 32][64];
     __shared__ unsigned long long stats[2];

@@ -1451,10 +1451,8 @@ __device__ __forceinline__ void apply_data(const Params &P, int i, const Contact
     D.lam = P.lam_pair[i];
 }
 
-// pre: the pair's ApplyData loaded ahead (before the search, so that its
-// latency overlaps the search's arithmetic), or null to load it here.
 __device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, const ContactPair &c, float al, int t0,
-                                              int tstep, bool write_lam, bool warp, const ApplyData *pre = nullptr)
+                                              int tstep, bool write_lam, bool warp)
 {
     float be;
     const float C = coll_f(c.Q, al, be);
@@ -1462,11 +1460,8 @@ __device__ __forceinline__ bool contact_apply(const Params &P, int i, float at, 
     float dist = sqrtf(dot(d, d));
     if (!(C < 0.f) || dist < 1e-12f) return false;
     V3 n = (1.f / dist) * d;
-    ApplyData D;
-    if (pre)
-        D = *pre;
-    else
-        apply_data(P, i, c, D);
+    ApplyData D;  // loaded only for an active pair
+    apply_data(P, i, c, D);
     const float wt[4] = {1.f - al, al, -(1.f - be), -be};
     float den = at;
 #pragma unroll
@@ -1579,10 +1574,8 @@ __device__ __forceinline__ int2 contact_pairs_compacted(const Params &P, int np,
             const int j = q[lane];
             ContactPair c;
             contact_load(P, j, c);
-            ApplyData D;
-            apply_data(P, j, c, D);
             pill_pair_axis(c.Q);
-            const bool act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false, &D);
+            const bool act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
             counts.x += 32;
             counts.y += __popc(__ballot_sync(full, act));
             __syncwarp();
@@ -1596,10 +1589,8 @@ __device__ __forceinline__ int2 contact_pairs_compacted(const Params &P, int np,
         const int j = q[lane];
         ContactPair c;
         contact_load(P, j, c);
-        ApplyData D;
-        apply_data(P, j, c, D);
         pill_pair_axis(c.Q);
-        act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false, &D);
+        act = contact_apply(P, j, at, c, dichotomous(c.Q), 0, 1, true, false);
     }
     counts.x += qn;
     counts.y += __popc(__ballot_sync(full, act));
