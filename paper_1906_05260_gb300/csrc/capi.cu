@@ -274,13 +274,15 @@ static void rest_tables(viper_scene *s)
 static int upload_rest(viper_scene *s)
 {
     const int nv = s->nv, ns = s->ns;
-    std::vector<float4> RV0(nv), RV1(nv), RV2(nv), RS0(ns), WS;
+    std::vector<float4> RV0(nv), RV1(nv), RV2(nv), CM(nv), RS0(ns), WS;
     std::vector<float2> RS1(ns);
     for (int vi = 0; vi < nv; ++vi) {
         const int vu = s->h_vperm[vi];
         RV0[vi] = s->u_RV0[vu];
         RV1[vi] = s->u_RV1[vu];
         RV2[vi] = s->u_RV2[vu];
+        // the inverse mass as inv_mass() reads it: negative x marks a pinned vertex
+        CM[vi] = make_float4(RV0[vi].w, std::max(RV1[vi].x, 0.f), RV1[vi].y, 0.f);
     }
     for (int gi = 0; gi < ns; ++gi) {
         const int gu = s->h_sperm[gi];
@@ -293,6 +295,7 @@ static int upload_rest(viper_scene *s)
     P.bp_rbar = reinterpret_cast<const float *>(P.RV0) + 3;  // RV0[v].w = rest radius
     if ((rc = upload(s, const_cast<float4 *>(P.RV1), RV1))) return rc;
     if ((rc = upload(s, const_cast<float4 *>(P.RV2), RV2))) return rc;
+    if ((rc = upload(s, const_cast<float4 *>(P.CM), CM))) return rc;
     if ((rc = upload(s, const_cast<float4 *>(P.RS0), RS0))) return rc;
     if ((rc = upload(s, const_cast<float2 *>(P.RS1), RS1))) return rc;
     if (P.warm) {
@@ -899,7 +902,7 @@ int viper_scene_create(const viper_scene_desc *d, viper_scene **out)
     if ((rc = dalloc(s, const_cast<type **>(&(ptr)), (size_t)(n)))) return fail(rc)
     A(P.X, nv); A(P.V, nv); A(P.Xp, nv); A(P.Xpred, nv);
     A(P.Q, ns); A(P.W, ns); A(P.Qp, ns);
-    AC(P.RV0, float4, nv); AC(P.RV1, float4, nv); AC(P.RV2, float4, nv);
+    AC(P.RV0, float4, nv); AC(P.RV1, float4, nv); AC(P.RV2, float4, nv); AC(P.CM, float4, nv);
     AC(P.RS0, float4, ns); AC(P.RS1, float2, ns);
     if (!s->u_warm.empty()) AC(P.warm, float4, nv);
     AC(P.seg_v0, int, ns); AC(P.vtx_seg, int, nv); AC(P.seg_group, int, ns);

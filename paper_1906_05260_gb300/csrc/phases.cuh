@@ -1443,10 +1443,10 @@ __device__ __forceinline__ void apply_data(const Params &P, int i, const Contact
 {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        D.rbar[t] = P.XW ? P.RV0[c.vs[t]].w : c.rbar[t];
-        const float4 m = P.RV1[c.vs[t]];
-        D.wx[t] = inv_mass(m);
-        D.wsv[t] = m.y;
+        const float4 m = P.CM[c.vs[t]];  // rest radius, inverse mass, scale weight
+        D.rbar[t] = P.XW ? m.x : c.rbar[t];
+        D.wx[t] = m.y;
+        D.wsv[t] = m.z;
     }
     D.lam = P.lam_pair[i];
 }

@@ -50,6 +50,9 @@ struct Params {
     const float4 *RV0, *RV1, *RS0;
     // surface bending per vertex: (1/(l_a lv), 1/(l_b lv), compliance, 0), zero at rod ends
     const float4 *RV2;
+    // per vertex (rest radius, inverse mass, scale weight, 0): what a contact
+    // update reads of RV0 and RV1, in one 16-byte gather (written with them)
+    const float4 *CM;
     int surface;
     int jacobi;  // rod constraints by Jacobi with averaging instead of four-colour Gauss-Seidel
     int vvec;    // volume constraint in the printed vector form (plain path; multipliers in lamV2)
