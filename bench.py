@@ -47,10 +47,10 @@ HAIR_PAIRS_PER_PILL = 64  # pair-list capacity of the hair scene (peak use about
 
 # FP32 work per unit of the contact pass (ncu SASS counts of FADD + FMUL + 2 FFMA of one
 # pass at frames 5, 18 and 55 of the hair scene, least-squares fit of the two figures,
-# each state predicted within 2.5 %): the two-direction early-out test per candidate
+# each state predicted within 1.5 %): the two-direction early-out test per candidate
 # pair, and the dichotomous search + constraint update per searched pair
-CONTACT_FLOP_PER_CANDIDATE = 78.1
-CONTACT_FLOP_PER_SEARCHED = 894.6
+CONTACT_FLOP_PER_CANDIDATE = 77.5
+CONTACT_FLOP_PER_SEARCHED = 892.5
 # FP32 work of the shared-memory rod kernel per vertex per colour sweep (ncu SASS
 # counts on the batching workload: 2.133 GFLOP per launch over 250,612 vertices x 8
 # sweeps, prediction and velocity update included)
