@@ -1073,7 +1073,9 @@ __device__ __forceinline__ void emit_warp_hits(const Params &P, bool hit, int a,
 // Each list is walked for the warp's longest length (shorter lanes idle), so
 // that every step ends with one ballot: hits go to the warp's shared buffer
 // buf (kPairBuf pairs), which is flushed to the pair list with one atomic.
-constexpr int kPairBuf = 160;  // after a flush it holds one step's hits (at most 4 x 32)
+// 480 pairs (3.75 KB per warp): one flush atomic per 480 pairs, measured 2 % faster than 160
+// on the hair; after a flush it holds one step's hits (at most 4 x 32)
+constexpr int kPairBuf = 480;
 
 __device__ __forceinline__ void flush_pairs(const Params &P, const int2 *buf, int cnt, int lane)
 {
