@@ -73,24 +73,38 @@ def hair_octant(sc):
     return dc.replace(sub, name="hair_octant", group=np.arange(len(keep), dtype=np.int32))
 
 
-def kernel_source_hash():
-    """sha256 of the CUDA sources (csrc/*.cu, *.cuh, *.h, sorted by name): the
-    build an ncu summary under profiles/ was captured from."""
+def kernel_source_hash(unit="contact.cu"):
+    """sha256 of one CUDA translation unit as the build compiles it: the file
+    csrc/<unit>, every header of the repository it includes (#include "...",
+    followed transitively, in the order met) and the nvcc flags.  A kernel's
+    code is fixed by exactly these, so an ncu summary under profiles/ names the
+    hash of the unit its kernels were captured from."""
     import hashlib
+    import re
+    from paper_1906_05260_gb300 import build as B
     d = os.path.join(ROOT, "paper_1906_05260_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    h.update(" ".join([*B.ARCH, *B.NVCC_FLAGS]).encode() + b"\0")
+    seen, todo = set(), [os.path.join(d, unit)]
+    while todo:
+        path = os.path.normpath(todo.pop(0))
+        if path in seen or not os.path.exists(path):
+            continue
+        seen.add(path)
+        with open(path, "rb") as f:
+            text = f.read()
+        h.update(os.path.relpath(path, ROOT).encode() + b"\0" + text)
+        for inc in re.findall(rb'#include "([^"]+)"', text):
+            todo.append(os.path.join(os.path.dirname(path), inc.decode()))
     return h.hexdigest()
 
 
 def profile_traffic(summary, key):
     """DRAM bytes per unit of one kernel from a committed ncu summary
     (profiles/<summary>): the line 'traffic <key>: <bytes> bytes per <unit>',
-    used only while the summary's 'csrc sha256:' line matches the sources of
-    this build; else None (the kernel changed since the counters were taken)."""
+    used only while the summary's 'csrc sha256:' line matches this build's
+    hash of the kernel's translation unit (contact.cu for the contact pass);
+    else None (the kernel changed since the counters were taken)."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
